@@ -1,0 +1,213 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Thin ctypes access to ``adgb_oracle.c``, the plain double-precision
+reference for the AutoDock4 scoring function, its gene gradient and the
+ADADELTA local search (arxiv 2410.10447, Sec. 2.1).  Only the tests, the
+smoke check and the benchmark's CPU-baseline leg use it; the CUDA library
+never does.  ``build()`` compiles the C file with gcc next to this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "adgb_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class _Receptor(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("n_type_maps", C.c_int), ("spacing", C.c_double),
+                ("origin", C.c_double * 3), ("maps", _dp)]
+
+
+class _Ligand(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("n_tors", C.c_int), ("n_pairs", C.c_int),
+                ("n_types", C.c_int), ("type", _ip), ("charge", _dp), ("xyz", _dp),
+                ("tors_bond", _ip), ("mov_off", _ip), ("mov_atoms", _ip),
+                ("pairs", _ip), ("R", _dp), ("eps", _dp), ("vol", _dp),
+                ("solpar", _dp), ("hb_role", _ip), ("hb_R", C.c_double),
+                ("hb_eps", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, IEEE arithmetic, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.orc_sum_naive.restype = C.c_double
+        L.orc_sum_neumaier.restype = C.c_double
+        L.orc_sum_naive.argtypes = [_dp, C.c_long, C.c_long]
+        L.orc_sum_neumaier.argtypes = [_dp, C.c_long, C.c_long]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _pd(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _pi(a):
+    return a.ctypes.data_as(_ip)
+
+
+class Receptor:
+    """Receptor grid as the oracle sees it (float32 inputs widened to float64)."""
+
+    def __init__(self, rec: dict):
+        self.maps = _d(rec["maps"])
+        self.c = _Receptor(int(rec["nx"]), int(rec["ny"]), int(rec["nz"]),
+                           int(rec["n_type_maps"]), float(np.float32(rec["spacing"])),
+                           (C.c_double * 3)(*[float(v) for v in np.asarray(rec["origin"], np.float32)]),
+                           _pd(self.maps))
+
+
+class Ligand:
+    def __init__(self, lig: dict):
+        self.arrs = dict(
+            type=_i(lig["type"]), charge=_d(lig["charge"]), xyz=_d(lig["xyz"]),
+            tors_bond=_i(lig["tors_bond"]).reshape(-1), mov_off=_i(lig["mov_off"]),
+            mov_atoms=_i(lig["mov_atoms"]), pairs=_i(lig["pairs"]).reshape(-1),
+            R=_d(lig["R"]), eps=_d(lig["eps"]), vol=_d(lig["vol"]),
+            solpar=_d(lig["solpar"]), hb_role=_i(lig["hb_role"]))
+        if len(self.arrs["mov_atoms"]) == 0:
+            self.arrs["mov_atoms"] = np.zeros(1, np.int32)
+        if len(self.arrs["pairs"]) == 0:
+            self.arrs["pairs"] = np.zeros(2, np.int32)
+        a = self.arrs
+        self.n_atoms = int(lig["n_atoms"])
+        self.n_tors = int(lig["n_tors"])
+        self.G = 6 + self.n_tors
+        self.c = _Ligand(self.n_atoms, self.n_tors, int(len(lig["pairs"])), int(lig["n_types"]),
+                         _pi(a["type"]), _pd(a["charge"]), _pd(a["xyz"]), _pi(a["tors_bond"]),
+                         _pi(a["mov_off"]), _pi(a["mov_atoms"]), _pi(a["pairs"]),
+                         _pd(a["R"]), _pd(a["eps"]), _pd(a["vol"]), _pd(a["solpar"]),
+                         _pi(a["hb_role"]), float(np.float32(lig["hb_R"])),
+                         float(np.float32(lig["hb_eps"])))
+
+
+def _lig(x):
+    return x if isinstance(x, Ligand) else Ligand(x)
+
+
+def _rec(x):
+    return x if isinstance(x, Receptor) else Receptor(x)
+
+
+def pose_coords(lig, genes) -> np.ndarray:
+    L = _lig(lig)
+    g = _d(genes)
+    out = np.zeros((L.n_atoms, 3))
+    rc = lib().orc_pose_coords(C.byref(L.c), _pd(g), _pd(out))
+    if rc:
+        raise ValueError("orc_pose_coords failed (%d)" % rc)
+    return out
+
+
+def energy(rec, lig, xyz):
+    """(E_inter, E_intra, dE/dx [N][3]) of explicit coordinates."""
+    R, L = _rec(rec), _lig(lig)
+    x = _d(xyz)
+    g = np.zeros((L.n_atoms, 3))
+    ei, ea = C.c_double(), C.c_double()
+    lib().orc_energy(C.byref(R.c), C.byref(L.c), _pd(x), C.byref(ei), C.byref(ea), _pd(g))
+    return ei.value, ea.value, g
+
+
+def score(rec, lig, genes):
+    """(E, dE/dgenes [G], coords [N][3], dE/dx [N][3]) of one genotype."""
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes)
+    e = C.c_double()
+    gg = np.zeros(L.G)
+    x = np.zeros((L.n_atoms, 3))
+    ag = np.zeros((L.n_atoms, 3))
+    rc = lib().orc_score(C.byref(R.c), C.byref(L.c), _pd(g), C.byref(e), _pd(gg), _pd(x), _pd(ag))
+    if rc:
+        raise ValueError("orc_score failed (%d)" % rc)
+    return e.value, gg, x, ag
+
+
+def adadelta_step(grad, genes, eg2, ed2, rho=0.8, eps=1e-2):
+    """One ADADELTA update; returns new (genes, eg2, ed2)."""
+    grad = _d(grad)
+    g, a, b = _d(genes).copy(), _d(eg2).copy(), _d(ed2).copy()
+    lib().orc_adadelta_step(C.c_int(len(g)), _pd(grad), C.c_double(rho), C.c_double(eps),
+                            _pd(g), _pd(a), _pd(b))
+    return g, a, b
+
+
+def local_search(rec, lig, genes, iters, rho=0.8, eps=1e-2, state=None):
+    """Returns (best_E, best_genes, final_state [3][G]); resumes from state if given."""
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes).copy()
+    st = np.zeros((3, L.G)) if state is None else _d(state).reshape(3, L.G).copy()
+    be = C.c_double()
+    rc = lib().orc_local_search(C.byref(R.c), C.byref(L.c), _pd(g), C.c_int(iters),
+                                C.c_double(rho), C.c_double(eps),
+                                C.c_int(0 if state is None else 1), _pd(st), C.byref(be))
+    if rc:
+        raise ValueError("orc_local_search failed (%d)" % rc)
+    return be.value, g, st
+
+
+def local_search_batch(rec, lig, genes, iters, rho=0.8, eps=1e-2, nthreads=0):
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes).copy()
+    n = g.shape[0]
+    be = np.zeros(n)
+    rc = lib().orc_local_search_batch(C.byref(R.c), C.byref(L.c), C.c_int(n), _pd(g),
+                                      C.c_int(iters), C.c_double(rho), C.c_double(eps),
+                                      _pd(be), C.c_int(nthreads))
+    if rc:
+        raise ValueError("orc_local_search_batch failed")
+    return be, g
+
+
+def score_batch(rec, lig, genes, nthreads=0):
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes)
+    n = g.shape[0]
+    e = np.zeros(n)
+    gg = np.zeros((n, L.G))
+    rc = lib().orc_score_batch(C.byref(R.c), C.byref(L.c), C.c_int(n), _pd(g), _pd(e),
+                               _pd(gg), C.c_int(nthreads))
+    if rc:
+        raise ValueError("orc_score_batch failed")
+    return e, gg
+
+
+def sum_naive(x) -> float:
+    x = _d(x).reshape(-1)
+    return lib().orc_sum_naive(_pd(x), len(x), 1)
+
+
+def sum_neumaier(x) -> float:
+    x = _d(x).reshape(-1)
+    return lib().orc_sum_neumaier(_pd(x), len(x), 1)

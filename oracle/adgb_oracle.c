@@ -1,0 +1,468 @@
+/*
+ * FP64 CPU oracle: AutoDock4 scoring function, gradient and ADADELTA local
+ * search, written step by step from the definitions (arxiv 2410.10447,
+ * Sec. 2.1, and the force field it names: AutoDock4, Morris et al. 1998;
+ * ADADELTA, Zeiler 2012).
+ *
+ * TEST INFRASTRUCTURE ONLY: the reference the CUDA library is compared with.
+ * Nothing here is tuned; every sum is a plain left-to-right loop in double
+ * precision.  See adgb_oracle.h for the data layout.
+ *
+ * Readings of points the paper leaves open (the paper names the force field
+ * but prints none of its formulas):
+ *  - genotype (Sec. 2.1): x,y,z translation (A), rotation axis given by the
+ *    azimuth phi and polar angle theta, rotation angle alpha, then one
+ *    torsion angle per rotatable bond; 6+T genes;
+ *  - every rotation is applied in increment form
+ *    r' = r + sin(a) (k x v) + (1 - cos(a)) (k x (k x v)), so a zero angle
+ *    leaves a coordinate bit-for-bit unchanged;
+ *  - intermolecular energy: trilinear interpolation of the atom type's map,
+ *    plus q times the electrostatic map, plus |q| times the desolvation map;
+ *    a point outside the grid is clamped onto it and pays 10 kcal/mol/A^2
+ *    times its squared distance to the grid;
+ *  - intramolecular energy: 12-6 van der Waals (12-10 for donor-acceptor
+ *    pairs), Coulomb with the Mehler-Solmajer distance-dependent dielectric,
+ *    and the AutoDock4 desolvation term; the singular terms use
+ *    max(r, 0.5 A), below which their gradient is zero;
+ *  - ADADELTA (Zeiler 2012) moves against the gradient; the best (lowest)
+ *    energy seen and its genotype are kept, ties keep the earlier one;
+ *    torsion genes are wrapped to [-pi, pi) after each update.
+ */
+#include "adgb_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI 3.14159265358979323846
+
+static void cross(const double a[3], const double b[3], double c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* r += sin(ang) (k x v) + (1 - cos(ang)) (k x (k x v)), v = r - centre */
+static void rotate_increment(double r[3], const double centre[3],
+                             const double k[3], double s, double omc) {
+    double v[3] = {r[0] - centre[0], r[1] - centre[1], r[2] - centre[2]};
+    double kv[3], kkv[3];
+    cross(k, v, kv);
+    cross(k, kv, kkv);
+    for (int d = 0; d < 3; d++) r[d] += s * kv[d] + omc * kkv[d];
+}
+
+static void axis_from_angles(double phi, double theta, double u[3]) {
+    u[0] = sin(theta) * cos(phi);
+    u[1] = sin(theta) * sin(phi);
+    u[2] = cos(theta);
+}
+
+/*
+ * Torsioned conformation (Sec. 2.1 genotype, torsion genes psi_k).
+ * Torsions are applied root to leaf, each about the CURRENT position of its
+ * bond (a->b), so that a later (deeper) torsion turns about an axis already
+ * moved by its ancestors.
+ */
+static int torsion_coords(const orc_ligand *L, const double *genes, double *p) {
+    const int N = L->n_atoms, T = L->n_tors;
+    memcpy(p, L->xyz, sizeof(double) * 3 * (size_t)N);
+    for (int k = 0; k < T; k++) {
+        const double *pa = p + 3 * L->tors_bond[2 * k];
+        const double *pb = p + 3 * L->tors_bond[2 * k + 1];
+        double b[3] = {pb[0], pb[1], pb[2]};
+        double ax[3] = {pb[0] - pa[0], pb[1] - pa[1], pb[2] - pa[2]};
+        double len = sqrt(dot(ax, ax));
+        if (!(len > 0)) return -1;
+        for (int d = 0; d < 3; d++) ax[d] /= len;
+        double psi = genes[6 + k];
+        double s = sin(psi), omc = 1.0 - cos(psi);
+        for (int m = L->mov_off[k]; m < L->mov_off[k + 1]; m++)
+            rotate_increment(p + 3 * L->mov_atoms[m], b, ax, s, omc);
+    }
+    return 0;
+}
+
+/* Rigid motion: rotation (phi, theta, alpha) about the frame origin, then t. */
+static void rigid_motion(int N, const double *genes, const double *p, double *x) {
+    double u[3];
+    axis_from_angles(genes[3], genes[4], u);
+    double s = sin(genes[5]), omc = 1.0 - cos(genes[5]);
+    const double zero[3] = {0, 0, 0};
+    memcpy(x, p, sizeof(double) * 3 * (size_t)N);
+    for (int i = 0; i < N; i++) {
+        rotate_increment(x + 3 * i, zero, u, s, omc);
+        for (int d = 0; d < 3; d++) x[3 * i + d] += genes[d];
+    }
+}
+
+/* Pose -> coordinates: torsions, then rotation about the centre, then translation. */
+int orc_pose_coords(const orc_ligand *L, const double *genes, double *x) {
+    double *p = (double *)malloc(sizeof(double) * 3 * (size_t)L->n_atoms);
+    if (!p) return -2;
+    int rc = torsion_coords(L, genes, p);
+    if (!rc) rigid_motion(L->n_atoms, genes, p, x);
+    free(p);
+    return rc;
+}
+
+/*
+ * Trilinear interpolation of map m at the (already clamped) point p, and its
+ * gradient with respect to p.  The 8 corner weights are written out as
+ * products of (f) and (1-f) per axis.
+ */
+static double trilinear(const orc_receptor *R, int m, const double p[3],
+                        double grad[3]) {
+    const int n[3] = {R->nx, R->ny, R->nz};
+    int i0[3];
+    double f[3];
+    for (int d = 0; d < 3; d++) {
+        double u = (p[d] - R->origin[d]) / R->spacing;
+        int c = (int)floor(u);
+        if (c < 0) c = 0;
+        if (c > n[d] - 2) c = n[d] - 2;
+        i0[d] = c;
+        f[d] = u - c;
+    }
+    const double *map = R->maps + (size_t)m * R->nx * R->ny * R->nz;
+    double val = 0, g[3] = {0, 0, 0};
+    for (int cz = 0; cz < 2; cz++)
+        for (int cy = 0; cy < 2; cy++)
+            for (int cx = 0; cx < 2; cx++) {
+                size_t idx = ((size_t)(i0[2] + cz) * R->ny + (i0[1] + cy)) * R->nx
+                             + (i0[0] + cx);
+                double v = map[idx];
+                double wx = cx ? f[0] : 1 - f[0];
+                double wy = cy ? f[1] : 1 - f[1];
+                double wz = cz ? f[2] : 1 - f[2];
+                double sx = cx ? 1.0 : -1.0, sy = cy ? 1.0 : -1.0, sz = cz ? 1.0 : -1.0;
+                val += wx * wy * wz * v;
+                g[0] += sx * wy * wz * v;
+                g[1] += wx * sy * wz * v;
+                g[2] += wx * wy * sz * v;
+            }
+    for (int d = 0; d < 3; d++) grad[d] = g[d] / R->spacing;
+    return val;
+}
+
+/* Intermolecular energy of one atom and its gradient (reading above). */
+static double atom_inter(const orc_receptor *R, int type, double q,
+                         const double r[3], double g[3]) {
+    const int n[3] = {R->nx, R->ny, R->nz};
+    double p[3], pen = 0;
+    int inside[3];
+    for (int d = 0; d < 3; d++) {
+        double lo = R->origin[d], hi = R->origin[d] + (n[d] - 1) * R->spacing;
+        p[d] = r[d] < lo ? lo : (r[d] > hi ? hi : r[d]);
+        inside[d] = (r[d] >= lo && r[d] <= hi);
+        pen += (r[d] - p[d]) * (r[d] - p[d]);
+    }
+    double gt[3], ge[3], gd[3];
+    double vt = trilinear(R, type, p, gt);
+    double ve = trilinear(R, R->n_type_maps, p, ge);
+    double vd = trilinear(R, R->n_type_maps + 1, p, gd);
+    double aq = fabs(q);
+    for (int d = 0; d < 3; d++) {
+        double gi = inside[d] ? gt[d] + q * ge[d] + aq * gd[d] : 0.0;
+        g[d] = gi + 2.0 * ORC_W_OUT * (r[d] - p[d]);
+    }
+    return vt + q * ve + aq * vd + ORC_W_OUT * pen;
+}
+
+/* Mehler-Solmajer distance-dependent dielectric and its derivative. */
+static double dielectric(double r, double *deps_dr) {
+    const double A = -8.5525, eps0 = 78.4, lam = 0.003627, k = 7.7839;
+    const double B = eps0 - A;
+    double ex = exp(-lam * B * r);
+    double den = 1.0 + k * ex;
+    *deps_dr = B * k * lam * B * ex / (den * den);
+    return A + B / den;
+}
+
+/*
+ * Energy of one intramolecular pair at separation vector rv = x_i - x_j,
+ * and the gradient with respect to x_i (x_j receives the negative).
+ */
+static double pair_energy(const orc_ligand *L, int i, int j, const double rv[3],
+                          double gi[3]) {
+    int ti = L->type[i], tj = L->type[j];
+    double r = sqrt(dot(rv, rv));
+    double rc = r > ORC_R_MIN ? r : ORC_R_MIN;
+    int live = r >= ORC_R_MIN;        /* clamped terms have zero gradient below */
+    double e = 0, dedr = 0;
+    int hb = (L->hb_role[ti] == 1 && L->hb_role[tj] == 2) ||
+             (L->hb_role[ti] == 2 && L->hb_role[tj] == 1);
+    if (hb) {
+        /* 12-10 hydrogen bond: eps [5 (R/r)^12 - 6 (R/r)^10] */
+        double Rh = L->hb_R, eh = L->hb_eps;
+        e += ORC_W_HB * eh * (5.0 * pow(Rh / rc, 12) - 6.0 * pow(Rh / rc, 10));
+        dedr += ORC_W_HB * eh * (-60.0 * pow(Rh / rc, 12) / rc + 60.0 * pow(Rh / rc, 10) / rc);
+    } else {
+        /* 12-6 van der Waals, Lorentz-Berthelot mixed: eps [(R/r)^12 - 2 (R/r)^6] */
+        double Rij = 0.5 * (L->R[ti] + L->R[tj]);
+        double eij = sqrt(L->eps[ti] * L->eps[tj]);
+        e += ORC_W_VDW * eij * (pow(Rij / rc, 12) - 2.0 * pow(Rij / rc, 6));
+        dedr += ORC_W_VDW * eij * (-12.0 * pow(Rij / rc, 12) / rc + 12.0 * pow(Rij / rc, 6) / rc);
+    }
+    /* Coulomb with eps(r): C / (r eps(r)) */
+    double deps;
+    double epsr = dielectric(rc, &deps);
+    double C = ORC_W_EL * ORC_ELEC * L->charge[i] * L->charge[j];
+    e += C / (rc * epsr);
+    dedr += -C * (epsr + rc * deps) / ((rc * epsr) * (rc * epsr));
+    if (!live) dedr = 0.0;
+    /* desolvation: (S_i V_j + S_j V_i) exp(-r^2 / (2 sigma^2)) */
+    double Si = L->solpar[ti] + ORC_QSOL * fabs(L->charge[i]);
+    double Sj = L->solpar[tj] + ORC_QSOL * fabs(L->charge[j]);
+    double s2 = 2.0 * ORC_DS_SIGMA * ORC_DS_SIGMA;
+    double eds = ORC_W_DS * (Si * L->vol[tj] + Sj * L->vol[ti]) * exp(-r * r / s2);
+    e += eds;
+    for (int d = 0; d < 3; d++) {
+        double g = 0;
+        if (live) g += dedr * rv[d] / r;
+        g += -eds * rv[d] / (ORC_DS_SIGMA * ORC_DS_SIGMA);  /* d/dx_i of exp(-r^2/2s^2) */
+        gi[d] = g;
+    }
+    return e;
+}
+
+/* Inter + intra energy of a conformation and dE/dx per atom. */
+int orc_energy(const orc_receptor *R, const orc_ligand *L, const double *x,
+               double *e_inter, double *e_intra, double *atom_grad) {
+    const int N = L->n_atoms;
+    double ei = 0, ea = 0;
+    for (int i = 0; i < 3 * N; i++) atom_grad[i] = 0;
+    for (int i = 0; i < N; i++) {
+        double g[3];
+        ei += atom_inter(R, L->type[i], L->charge[i], x + 3 * i, g);
+        for (int d = 0; d < 3; d++) atom_grad[3 * i + d] += g[d];
+    }
+    for (int p = 0; p < L->n_pairs; p++) {
+        int i = L->pairs[2 * p], j = L->pairs[2 * p + 1];
+        double rv[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1],
+                        x[3 * i + 2] - x[3 * j + 2]};
+        double g[3];
+        ea += pair_energy(L, i, j, rv, g);
+        for (int d = 0; d < 3; d++) {
+            atom_grad[3 * i + d] += g[d];
+            atom_grad[3 * j + d] -= g[d];
+        }
+    }
+    *e_inter = ei;
+    *e_intra = ea;
+    return 0;
+}
+
+/*
+ * Energy and gradient with respect to the genes (Sec. 2.1: translation,
+ * rotation and torsion genes).  Chain rule written out per gene:
+ *  - translation: sum of atom gradients;
+ *  - rotation genes: sum_i g_i . (dR/dgene) p_i with p_i the torsioned
+ *    coordinates and R the increment-form rotation written as a function of
+ *    (phi, theta, alpha);
+ *  - torsion k: sum over its moving atoms of g_i . (a_k x (x_i - x_b)), the
+ *    velocity of atom i when the bond turns, a_k the bond's unit vector in
+ *    the final pose.
+ */
+int orc_score(const orc_receptor *R, const orc_ligand *L, const double *genes,
+              double *energy, double *gene_grad, double *xyz_out,
+              double *atom_grad) {
+    const int N = L->n_atoms, T = L->n_tors;
+    double *x = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *g = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    if (!x || !g || !p) { free(x); free(g); free(p); return -2; }
+    if (torsion_coords(L, genes, p)) { free(x); free(g); free(p); return -1; }
+    rigid_motion(N, genes, p, x);
+    double ei, ea;
+    orc_energy(R, L, x, &ei, &ea, g);
+    *energy = ei + ea;
+    if (gene_grad) {
+        double u[3];
+        axis_from_angles(genes[3], genes[4], u);
+        double al = genes[5];
+        double up[3] = {-sin(genes[4]) * sin(genes[3]), sin(genes[4]) * cos(genes[3]), 0.0};
+        double ut[3] = {cos(genes[4]) * cos(genes[3]), cos(genes[4]) * sin(genes[3]), -sin(genes[4])};
+        double sa = sin(al), omc = 1.0 - cos(al), ca = cos(al);
+        for (int k = 0; k < 6 + T; k++) gene_grad[k] = 0.0;
+        for (int i = 0; i < N; i++) {
+            const double *pi = p + 3 * i, *gi = g + 3 * i;
+            for (int d = 0; d < 3; d++) gene_grad[d] += gi[d];
+            /* dR/dphi p = sin a (u_phi x p) + (1-cos a)(u_phi x (u x p) + u x (u_phi x p)) */
+            double t1[3], t2[3], t3[3], t4[3], v[3];
+            cross(up, pi, t1);
+            cross(u, pi, t2);
+            cross(up, t2, t3);
+            cross(u, t1, t4);
+            for (int d = 0; d < 3; d++) v[d] = sa * t1[d] + omc * (t3[d] + t4[d]);
+            gene_grad[3] += dot(gi, v);
+            cross(ut, pi, t1);
+            cross(ut, t2, t3);
+            cross(u, t1, t4);
+            for (int d = 0; d < 3; d++) v[d] = sa * t1[d] + omc * (t3[d] + t4[d]);
+            gene_grad[4] += dot(gi, v);
+            /* dR/dalpha p = cos a (u x p) + sin a (u x (u x p)) */
+            cross(u, t2, t3);
+            for (int d = 0; d < 3; d++) v[d] = ca * t2[d] + sa * t3[d];
+            gene_grad[5] += dot(gi, v);
+        }
+        for (int k = 0; k < T; k++) {
+            const double *xa = x + 3 * L->tors_bond[2 * k];
+            const double *xb = x + 3 * L->tors_bond[2 * k + 1];
+            double ax[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+            double len = sqrt(dot(ax, ax));
+            for (int d = 0; d < 3; d++) ax[d] /= len;
+            double acc = 0;
+            for (int m = L->mov_off[k]; m < L->mov_off[k + 1]; m++) {
+                int i = L->mov_atoms[m];
+                double v[3] = {x[3 * i] - xb[0], x[3 * i + 1] - xb[1], x[3 * i + 2] - xb[2]};
+                double vel[3];
+                cross(ax, v, vel);
+                acc += dot(g + 3 * i, vel);
+            }
+            gene_grad[6 + k] = acc;
+        }
+    }
+    if (xyz_out) memcpy(xyz_out, x, sizeof(double) * 3 * (size_t)N);
+    if (atom_grad) memcpy(atom_grad, g, sizeof(double) * 3 * (size_t)N);
+    free(x);
+    free(g);
+    free(p);
+    return 0;
+}
+
+static double wrap_angle(double a) {
+    return a - 2.0 * PI * floor((a + PI) / (2.0 * PI));
+}
+
+/*
+ * One ADADELTA update (Zeiler 2012, Algorithm 1; Sec. 2.1 writes it as
+ * Omega_{t+1} = Omega_t + eta_t g_t).  The step is taken against the
+ * gradient:
+ *   E[g^2]  <- rho E[g^2]  + (1-rho) g^2
+ *   d       <- -sqrt(E[d^2] + eps) / sqrt(E[g^2] + eps) * g
+ *   E[d^2]  <- rho E[d^2]  + (1-rho) d^2
+ *   Omega   <- Omega + d      (torsion genes wrapped to [-pi, pi))
+ */
+int orc_adadelta_step(int G, const double *grad, double rho, double eps,
+                      double *genes, double *eg2, double *ed2) {
+    for (int j = 0; j < G; j++) {
+        eg2[j] = rho * eg2[j] + (1.0 - rho) * grad[j] * grad[j];
+        double d = -sqrt(ed2[j] + eps) / sqrt(eg2[j] + eps) * grad[j];
+        ed2[j] = rho * ed2[j] + (1.0 - rho) * d * d;
+        genes[j] += d;
+        if (j >= 6) genes[j] = wrap_angle(genes[j]);
+    }
+    return 0;
+}
+
+/*
+ * ADADELTA local search of one genotype: `iters` energy+gradient
+ * evaluations, each followed by one update; the lowest energy seen and the
+ * genotype it was seen at are returned (genes is overwritten with it).
+ * state, if given, is [3][G] = (Omega, E[g^2], E[d^2]) after the last update;
+ * with resume != 0 the search starts from state instead of (genes, 0, 0).
+ */
+int orc_local_search(const orc_receptor *R, const orc_ligand *L, double *genes,
+                     int iters, double rho, double eps, int resume,
+                     double *state, double *best_energy) {
+    const int G = 6 + L->n_tors;
+    double *om = (double *)calloc((size_t)G * 5, sizeof(double));
+    if (!om) return -2;
+    double *eg2 = om + G, *ed2 = om + 2 * G, *grad = om + 3 * G, *best = om + 4 * G;
+    if (resume && state) {
+        memcpy(om, state, sizeof(double) * G);
+        memcpy(eg2, state + G, sizeof(double) * G);
+        memcpy(ed2, state + 2 * G, sizeof(double) * G);
+    } else {
+        memcpy(om, genes, sizeof(double) * G);
+    }
+    memcpy(best, om, sizeof(double) * G);
+    double best_e = INFINITY;
+    int rc = 0;
+    for (int t = 0; t < iters; t++) {
+        double e;
+        rc = orc_score(R, L, om, &e, grad, NULL, NULL);
+        if (rc) break;
+        if (e < best_e) {
+            best_e = e;
+            memcpy(best, om, sizeof(double) * G);
+        }
+        orc_adadelta_step(G, grad, rho, eps, om, eg2, ed2);
+    }
+    memcpy(genes, best, sizeof(double) * G);
+    if (state) {
+        memcpy(state, om, sizeof(double) * G);
+        memcpy(state + G, eg2, sizeof(double) * G);
+        memcpy(state + 2 * G, ed2, sizeof(double) * G);
+    }
+    *best_energy = best_e;
+    free(om);
+    return rc;
+}
+
+/* Independent local searches over n genotypes ([n][G]), spread over threads. */
+int orc_local_search_batch(const orc_receptor *R, const orc_ligand *L, int n,
+                           double *genes, int iters, double rho, double eps,
+                           double *best_energy, int nthreads) {
+    const int G = 6 + L->n_tors;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (int p = 0; p < n; p++)
+        bad |= orc_local_search(R, L, genes + (size_t)p * G, iters, rho, eps, 0,
+                                NULL, best_energy + p) != 0;
+    (void)nthreads;
+    return bad ? -1 : 0;
+}
+
+int orc_score_batch(const orc_receptor *R, const orc_ligand *L, int n,
+                    const double *genes, double *energy, double *gene_grad,
+                    int nthreads) {
+    const int G = 6 + L->n_tors;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : bad)
+#endif
+    for (int p = 0; p < n; p++)
+        bad |= orc_score(R, L, genes + (size_t)p * G, energy + p,
+                         gene_grad ? gene_grad + (size_t)p * G : NULL, NULL, NULL) != 0;
+    (void)nthreads;
+    return bad ? -1 : 0;
+}
+
+/* Plain left-to-right sum (the definition of the reduction, Sec. 4.2). */
+double orc_sum_naive(const double *x, long n, long stride) {
+    double s = 0;
+    for (long i = 0; i < n; i++) s += x[i * stride];
+    return s;
+}
+
+/*
+ * Neumaier's compensated summation (Neumaier 1974): carries the rounding
+ * error of every addition in a second accumulator; the result is the exact
+ * sum rounded once, up to O(n u^2) effects.
+ */
+double orc_sum_neumaier(const double *x, long n, long stride) {
+    double s = 0, c = 0;
+    for (long i = 0; i < n; i++) {
+        double v = x[i * stride];
+        double t = s + v;
+        if (fabs(s) >= fabs(v))
+            c += (s - t) + v;
+        else
+            c += (v - t) + s;
+        s = t;
+    }
+    return s + c;
+}

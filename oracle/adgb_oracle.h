@@ -1,0 +1,78 @@
+/*
+ * FP64 CPU oracle for the AutoDock4 scoring function, its gradient and the
+ * ADADELTA local search (arxiv 2410.10447, Sec. 2.1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the slow, plain reference that the CUDA
+ * library is checked against.  It shares no code, header, table or helper
+ * with the CUDA path, and only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it.
+ *
+ * Parity status: every function below is pinned by tests that do not go
+ * through the oracle's own formulas (finite differences, closed forms,
+ * invariants, brute force).  The GA, serving and rescoring parts are not
+ * here: they are built from the same scoring call.
+ */
+#ifndef ADGB_ORACLE_H
+#define ADGB_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int nx, ny, nz;          /* grid points per axis (>= 2) */
+    int n_type_maps;         /* affinity maps; map n_type_maps = e, +1 = d */
+    double spacing;          /* A between grid points */
+    double origin[3];        /* position of grid point (0,0,0) */
+    const double *maps;      /* [n_type_maps+2][nz][ny][nx] */
+} orc_receptor;
+
+typedef struct {
+    int n_atoms, n_tors, n_pairs, n_types;
+    const int *type;         /* [N] atom type = affinity map index */
+    const double *charge;    /* [N] partial charge (e) */
+    const double *xyz;       /* [N][3] reference conformation, rotation centre at 0 */
+    const int *tors_bond;    /* [T][2] (a,b): axis a->b, root to leaf order */
+    const int *mov_off;      /* [T+1] offsets into mov_atoms */
+    const int *mov_atoms;    /* atoms moved by torsion k: mov_atoms[mov_off[k]..] */
+    const int *pairs;        /* [n_pairs][2] intramolecular pairs */
+    const double *R, *eps, *vol, *solpar; /* [n_types] force-field parameters */
+    const int *hb_role;      /* [n_types] 0 none, 1 donor, 2 acceptor */
+    double hb_R, hb_eps;     /* 12-10 parameters of donor-acceptor pairs */
+} orc_ligand;
+
+/* force-field constants (AutoDock4.2 free-energy model) */
+#define ORC_W_VDW 0.1662
+#define ORC_W_HB 0.1209
+#define ORC_W_EL 0.1406
+#define ORC_W_DS 0.1322
+#define ORC_ELEC 332.06363
+#define ORC_DS_SIGMA 3.6
+#define ORC_QSOL 0.01097
+#define ORC_R_MIN 0.5
+#define ORC_W_OUT 10.0
+
+int orc_pose_coords(const orc_ligand *L, const double *genes, double *xyz_out);
+int orc_energy(const orc_receptor *R, const orc_ligand *L, const double *xyz,
+               double *e_inter, double *e_intra, double *atom_grad);
+int orc_score(const orc_receptor *R, const orc_ligand *L, const double *genes,
+              double *energy, double *gene_grad, double *xyz_out,
+              double *atom_grad);
+int orc_adadelta_step(int G, const double *grad, double rho, double eps,
+                      double *genes, double *eg2, double *ed2);
+int orc_local_search(const orc_receptor *R, const orc_ligand *L, double *genes,
+                     int iters, double rho, double eps, int resume,
+                     double *state, double *best_energy);
+int orc_local_search_batch(const orc_receptor *R, const orc_ligand *L, int n,
+                           double *genes, int iters, double rho, double eps,
+                           double *best_energy, int nthreads);
+int orc_score_batch(const orc_receptor *R, const orc_ligand *L, int n,
+                    const double *genes, double *energy, double *gene_grad,
+                    int nthreads);
+double orc_sum_naive(const double *x, long n, long stride);
+double orc_sum_neumaier(const double *x, long n, long stride);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
