@@ -1,0 +1,226 @@
+/*
+ * adgb - GB300-native AutoDock4 scoring function, gradient and ADADELTA
+ * local search (the hot path of AutoDock-GPU's Lamarckian GA studied in
+ * arxiv 2410.10447, "Accelerating Drug Discovery in AutoDock-GPU with
+ * Tensor Cores").
+ *
+ * C ABI.  Conventions:
+ *  - Every call returns an int status: ADGB_OK (0) or a negative ADGB_E*
+ *    code.  adgb_last_error(ctx) gives a message for the last failure on
+ *    that context.  Nothing is left half-done on an ADGB_EINVAL return.
+ *  - Pointers named *_dev are device pointers owned by the caller; the call
+ *    enqueues its work on `stream` and returns without synchronising.
+ *    Pointers without the suffix are host pointers owned by the caller; the
+ *    call copies them to the device, runs, copies results back and returns
+ *    when they are in host memory.
+ *  - Receptors and ligands are device objects owned by the library,
+ *    referenced by integer ids, released explicitly or by adgb_destroy.
+ *  - A context is bound to one device.  Calls on one context must not run
+ *    concurrently from several host threads (thread-compatible); the
+ *    library keeps no global state.
+ *  - adgb_stream is the CUDA runtime's cudaStream_t (NULL = legacy default
+ *    stream); it is declared here without the CUDA headers.
+ *
+ * Genotype layout (Sec. 2.1): genes[6+T] = (x, y, z, phi, theta, alpha,
+ * psi_0 .. psi_{T-1}) in Angstrom and radians: translation of the ligand's
+ * rotation centre, rotation axis (azimuth phi, polar angle theta), rotation
+ * angle alpha about that axis, and one angle per rotatable bond.
+ */
+#ifndef ADGB_H
+#define ADGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adgb_ctx adgb_ctx;
+typedef struct CUstream_st *adgb_stream;
+
+enum {
+    ADGB_OK = 0,
+    ADGB_EINVAL = -1,     /* bad argument, size or ligand description */
+    ADGB_ENOMEM = -2,     /* device or host allocation failed */
+    ADGB_ENOTFOUND = -3,  /* unknown receptor / ligand / job id */
+    ADGB_EDEVICE = -4,    /* CUDA error (message in adgb_last_error) */
+    ADGB_ETIMEOUT = -5,   /* a wait ran out of time */
+    ADGB_EREJECTED = -6,  /* a job can never fit the device */
+    ADGB_ECANCELLED = -7  /* the job was cancelled */
+};
+
+/* Block-reduction variants of the (E, dE/dt, torque) vector (Sec. 3-4). */
+enum {
+    ADGB_REDUCE_SHFL = 0,       /* FP32 warp shuffles (reduce-scatter + all-gather) */
+    ADGB_REDUCE_MMA_TF32X2 = 1, /* tensor-core sum, operands split into 2 TF32 terms, FP32 accumulate */
+    ADGB_REDUCE_MMA_BF16X3 = 2, /* tensor-core sum, operands split into 3 BF16 terms, FP32 accumulate */
+    ADGB_REDUCE_N = 3
+};
+
+/* Limits of one ligand. */
+#define ADGB_MAX_ATOMS 256
+#define ADGB_MAX_TORS 40
+#define ADGB_MAX_TYPES 16
+
+/* Force-field constants (AutoDock4.2 free-energy weights; Sec. 2.1 names
+ * the force field without printing it). */
+#define ADGB_W_VDW 0.1662f
+#define ADGB_W_HB 0.1209f
+#define ADGB_W_EL 0.1406f
+#define ADGB_W_DS 0.1322f
+#define ADGB_ELEC_KCAL 332.06363f
+#define ADGB_DS_SIGMA 3.6f
+#define ADGB_QSOL 0.01097f
+#define ADGB_R_MIN 0.5f      /* clash clamp of the singular pair terms (A) */
+#define ADGB_W_OUT 10.0f     /* out-of-grid penalty (kcal/mol/A^2) */
+
+typedef struct {
+    int threads_per_pose;  /* 0 = pick per ligand; else 32, 64, 128 or 256 */
+    int poses_per_block;   /* 0 = pick per ligand; else 1..8 */
+    int reduce_variant;    /* default ADGB_REDUCE_* for calls that do not say */
+} adgb_options;
+
+/* Receptor grid (Sec. 2.1: the receptor is fixed; its interaction with a
+ * ligand atom is read from precomputed maps). */
+typedef struct {
+    int nx, ny, nz;        /* grid points per axis, each >= 2 */
+    float spacing;         /* A between neighbouring points, > 0 */
+    float origin[3];       /* position of point (0,0,0), A */
+    int n_type_maps;       /* affinity maps, one per ligand atom type */
+} adgb_grid_desc;
+
+/* Ligand with its torsion tree (Sec. 2.1: torsion angles of rotatable bonds). */
+typedef struct {
+    int n_atoms;               /* 1..ADGB_MAX_ATOMS */
+    int n_types;               /* 1..ADGB_MAX_TYPES */
+    int n_tors;                /* 0..ADGB_MAX_TORS */
+    int n_pairs;               /* >= 0 */
+    const int32_t *type;       /* [n_atoms] type, also the receptor map index */
+    const float *charge;       /* [n_atoms] partial charge (e) */
+    const float *xyz;          /* [n_atoms][3] reference conformation; the rotation centre is the origin */
+    const int32_t *tors_bond;  /* [n_tors][2] bond (a,b): torsion turns the atoms beyond b about a->b; listed root to leaf */
+    const int32_t *mov_off;    /* [n_tors+1] offsets into mov_atoms */
+    const int32_t *mov_atoms;  /* atoms moved by torsion k: mov_atoms[mov_off[k] .. mov_off[k+1]) (excluding a and b) */
+    const int32_t *pairs;      /* [n_pairs][2] intramolecular pairs (i != j) */
+    const float *R;            /* [n_types] vdW equilibrium distance (A) */
+    const float *eps;          /* [n_types] vdW well depth (kcal/mol) */
+    const float *vol;          /* [n_types] atomic volume (A^3) */
+    const float *solpar;       /* [n_types] atomic solvation parameter */
+    const int32_t *hb_role;    /* [n_types] 0 none, 1 donor, 2 acceptor */
+    float hb_R, hb_eps;        /* 12-10 term of donor-acceptor pairs */
+} adgb_ligand_desc;
+
+/* ADADELTA local search parameters (Sec. 2.1; Zeiler 2012). */
+typedef struct {
+    int iters;             /* energy+gradient evaluations per genotype, >= 0 */
+    float rho;             /* decay of the running averages, 0 < rho < 1 (0.8) */
+    float eps;             /* conditioning constant, > 0 (1e-2) */
+    int reduce_variant;    /* ADGB_REDUCE_*, or -1 for the context default */
+    int flags;             /* ADGB_LS_* */
+} adgb_ls_params;
+
+#define ADGB_LS_RESUME 1   /* start from state (Omega, E[g^2], E[d^2]) instead of (genes, 0, 0) */
+
+/* Context on one CUDA device; opts may be NULL (defaults). */
+int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts);
+int adgb_destroy(adgb_ctx *ctx);
+/* Message of the last failure on ctx ("" if none); valid until the next call. */
+const char *adgb_last_error(const adgb_ctx *ctx);
+
+/*
+ * upload_receptor_grids - copy the receptor's grid maps to the device.
+ * maps: host float32 [n_type_maps+2][nz][ny][nx] (x fastest): the type
+ * affinity maps, then the electrostatic potential map e (kcal/mol/e), then
+ * the desolvation map d.  Maps already carry their force-field weights.
+ * The library stores them cell-major (the 8 corner values of every map of a
+ * grid cell contiguous), so one atom reads 3 x 32 contiguous bytes.
+ * Errors: EINVAL (sizes), ENOMEM, EDEVICE.
+ */
+int upload_receptor_grids(adgb_ctx *ctx, const adgb_grid_desc *grid,
+                          const float *maps, int *receptor_id);
+int release_receptor(adgb_ctx *ctx, int receptor_id);
+
+/*
+ * upload_ligand_torsion_tree - validate and copy a ligand (Sec. 2.1).
+ * The torsion tree must be laminar: two moving sets are disjoint or nested;
+ * a torsion nested in another is listed after it and its bond atoms lie in
+ * the outer moving set (or are its b atom); no torsion moves its own bond
+ * atoms.  Errors: EINVAL (limits, indices, tree, n_types > ADGB_MAX_TYPES),
+ * ENOMEM, EDEVICE.
+ */
+int upload_ligand_torsion_tree(adgb_ctx *ctx, const adgb_ligand_desc *lig,
+                               int *ligand_id);
+int release_ligand(adgb_ctx *ctx, int ligand_id);
+
+/*
+ * validate_ligand_torsion_tree - the checks of upload_ligand_torsion_tree
+ * without a context or a device.  Returns ADGB_OK or ADGB_EINVAL; the
+ * reason is written to msg (NUL-terminated, at most msg_len bytes) if msg
+ * is not NULL.
+ */
+int validate_ligand_torsion_tree(const adgb_ligand_desc *lig, char *msg, int msg_len);
+
+/*
+ * pose_coords - atom coordinates of n genotypes (Sec. 2.1).
+ * genes [n][6+T] -> xyz [n][n_atoms][3], atoms in the caller's order.
+ */
+int pose_coords_dev(adgb_ctx *ctx, int ligand_id, const float *genes_dev, int n,
+                    float *xyz_dev, adgb_stream stream);
+int pose_coords(adgb_ctx *ctx, int ligand_id, const float *genes, int n, float *xyz);
+
+/*
+ * score_poses - energy and gene gradient of n genotypes (Sec. 2.1, the
+ * scoring function evaluated with its gradient; Sec. 3, seven block
+ * reductions per evaluation, here one 8-wide reduction).
+ * genes [n][6+T]; energy [n] (kcal/mol); grad [n][6+T] or NULL.
+ * reduce_variant: ADGB_REDUCE_* or -1 for the context default.
+ * Errors: EINVAL (n < 0, unknown variant, ligand type beyond the receptor's
+ * maps), ENOTFOUND, EDEVICE.
+ */
+int score_poses_dev(adgb_ctx *ctx, int receptor_id, int ligand_id,
+                    const float *genes_dev, int n, float *energy_dev,
+                    float *grad_dev, int reduce_variant, adgb_stream stream);
+int score_poses(adgb_ctx *ctx, int receptor_id, int ligand_id, const float *genes,
+                int n, float *energy, float *grad, int reduce_variant);
+
+/*
+ * local_search - ADADELTA local search of n genotypes (Sec. 2.1).
+ * For each genotype: p->iters evaluations, each followed by one update
+ *   E[g^2] <- rho E[g^2] + (1-rho) g^2
+ *   d      <- -sqrt(E[d^2] + eps) / sqrt(E[g^2] + eps) * g
+ *   E[d^2] <- rho E[d^2] + (1-rho) d^2
+ *   Omega  <- Omega + d   (torsion genes wrapped to [-pi, pi)).
+ * genes [n][6+T] in: the start genotypes; out: the genotype of the lowest
+ * energy seen (ties keep the earlier one).  best_energy [n] out (+inf when
+ * iters == 0).  state [n][3][6+T] or NULL: out, (Omega, E[g^2], E[d^2])
+ * after the last update; with ADGB_LS_RESUME also in, and genes in is then
+ * ignored.  The whole search of every genotype runs in one kernel launch.
+ * Errors: EINVAL, ENOTFOUND, EDEVICE.
+ */
+int local_search_dev(adgb_ctx *ctx, int receptor_id, int ligand_id,
+                     float *genes_dev, int n, const adgb_ls_params *p,
+                     float *best_energy_dev, float *state_dev, adgb_stream stream);
+int local_search(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes,
+                 int n, const adgb_ls_params *p, float *best_energy, float *state);
+
+/*
+ * reduce4_bench_dev - the reduction test kernel of Sec. 5.2: every thread
+ * of a block holds one four-element vector, the block computes the sum and
+ * every thread receives it.  in [n_blocks][threads][4] float32, out the same
+ * shape (each thread's copy of its block's sum).  The reduction is repeated
+ * `reps` times inside the kernel (every repetition reduces the same input),
+ * so that its own cost dominates a timing.  variant: ADGB_REDUCE_* or
+ * ADGB_REDUCE4_PAPER_FS, the per-component shuffle + shared-memory atomic
+ * reduction that Sec. 3 profiles (three barriers per component).
+ * threads: 32..1024, a multiple of 32; reps >= 1.
+ * Errors: EINVAL, EDEVICE.
+ */
+#define ADGB_REDUCE4_PAPER_FS 100
+int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
+                      int threads, int n_blocks, int reps, float *out_dev,
+                      adgb_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADGB_H */

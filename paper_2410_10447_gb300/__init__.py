@@ -1,0 +1,10 @@
+"""GB300-native AutoDock4 scoring, gradient and ADADELTA local search
+(arxiv 2410.10447).  The compute path is libadgb.so (hand-written sm_103a
+CUDA kernels behind a C ABI, include/adgb.h); this package is its ctypes
+binding and build step.
+"""
+from .adgb import (  # noqa: F401
+    EXPORTS, LS_RESUME, REDUCE4_PAPER_FS, REDUCE_MMA_BF16X3, REDUCE_MMA_TF32X2, REDUCE_SHFL,
+    VARIANTS, AdgbError, Context, library_path, load, validate_ligand_torsion_tree,
+)
+from .build import build  # noqa: F401

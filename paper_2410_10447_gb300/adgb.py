@@ -1,0 +1,281 @@
+"""ctypes binding of libadgb (include/adgb.h).  Argument marshalling only:
+every step of scoring and local search runs in the library's CUDA kernels.
+
+Device-pointer calls take torch CUDA tensors and run on the current torch
+stream; host calls take numpy arrays (pinned torch CPU tensors also work).
+Loading fails loudly when the library has not been built or cannot load:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+ADGB_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ENOTFOUND", -4: "EDEVICE", -5: "ETIMEOUT",
+          -6: "EREJECTED", -7: "ECANCELLED"}
+REDUCE_SHFL, REDUCE_MMA_TF32X2, REDUCE_MMA_BF16X3 = 0, 1, 2
+REDUCE4_PAPER_FS = 100
+VARIANTS = {"shfl": REDUCE_SHFL, "mma_tf32x2": REDUCE_MMA_TF32X2, "mma_bf16x3": REDUCE_MMA_BF16X3}
+LS_RESUME = 1
+
+# the C ABI's exported entry points (checked against include/adgb.h by the tests)
+EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_grids",
+           "release_receptor", "upload_ligand_torsion_tree", "release_ligand",
+           "validate_ligand_torsion_tree",
+           "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
+           "local_search_dev", "local_search", "reduce4_bench_dev"]
+
+
+class AdgbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class _Options(C.Structure):
+    _fields_ = [("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
+                ("reduce_variant", C.c_int)]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("spacing", C.c_float),
+                ("origin", C.c_float * 3), ("n_type_maps", C.c_int)]
+
+
+_i32p = C.POINTER(C.c_int32)
+_f32p = C.POINTER(C.c_float)
+
+
+class _Ligand(C.Structure):
+    _fields_ = [("n_atoms", C.c_int), ("n_types", C.c_int), ("n_tors", C.c_int),
+                ("n_pairs", C.c_int), ("type", _i32p), ("charge", _f32p), ("xyz", _f32p),
+                ("tors_bond", _i32p), ("mov_off", _i32p), ("mov_atoms", _i32p),
+                ("pairs", _i32p), ("R", _f32p), ("eps", _f32p), ("vol", _f32p),
+                ("solpar", _f32p), ("hb_role", _i32p), ("hb_R", C.c_float),
+                ("hb_eps", C.c_float)]
+
+
+class _LSParams(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rho", C.c_float), ("eps", C.c_float),
+                ("reduce_variant", C.c_int), ("flags", C.c_int)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = False):
+    """Loads libadgb.so (building it first if asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libadgb.so is not built; run paper_2410_10447_gb300.build.build()")
+    L = C.CDLL(_build.LIB)
+    vp = C.c_void_p
+    L.adgb_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(_Options)]
+    L.adgb_destroy.argtypes = [vp]
+    L.adgb_last_error.argtypes = [vp]
+    L.adgb_last_error.restype = C.c_char_p
+    L.upload_receptor_grids.argtypes = [vp, C.POINTER(_Grid), vp, C.POINTER(C.c_int)]
+    L.release_receptor.argtypes = [vp, C.c_int]
+    L.upload_ligand_torsion_tree.argtypes = [vp, C.POINTER(_Ligand), C.POINTER(C.c_int)]
+    L.release_ligand.argtypes = [vp, C.c_int]
+    L.validate_ligand_torsion_tree.argtypes = [C.POINTER(_Ligand), C.c_char_p, C.c_int]
+    L.pose_coords_dev.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
+    L.pose_coords.argtypes = [vp, C.c_int, vp, C.c_int, vp]
+    L.score_poses_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp, C.c_int, vp]
+    L.score_poses.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp, C.c_int]
+    L.local_search_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_LSParams),
+                                   vp, vp, vp]
+    L.local_search.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_LSParams), vp, vp]
+    L.reduce4_bench_dev.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp]
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array, a torch tensor, or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _check_dev(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+            and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+
+
+def _ligand_desc(lig: dict):
+    """adgb_ligand_desc over numpy copies of the ligand's arrays; the arrays
+    are returned too and must outlive the descriptor."""
+    arr = dict(type=_i32(lig["type"]), charge=_f32(lig["charge"]), xyz=_f32(lig["xyz"]),
+               tors_bond=_i32(lig["tors_bond"]), mov_off=_i32(lig["mov_off"]),
+               mov_atoms=_i32(lig["mov_atoms"]), pairs=_i32(lig["pairs"]),
+               R=_f32(lig["R"]), eps=_f32(lig["eps"]), vol=_f32(lig["vol"]),
+               solpar=_f32(lig["solpar"]), hb_role=_i32(lig["hb_role"]))
+    P = lambda a, t: a.ctypes.data_as(t) if a.size else None
+    d = _Ligand(int(lig["n_atoms"]), int(lig["n_types"]), int(lig["n_tors"]),
+                int(arr["pairs"].size // 2), P(arr["type"], _i32p), P(arr["charge"], _f32p),
+                P(arr["xyz"], _f32p), P(arr["tors_bond"], _i32p), P(arr["mov_off"], _i32p),
+                P(arr["mov_atoms"], _i32p), P(arr["pairs"], _i32p), P(arr["R"], _f32p),
+                P(arr["eps"], _f32p), P(arr["vol"], _f32p), P(arr["solpar"], _f32p),
+                P(arr["hb_role"], _i32p), float(lig["hb_R"]), float(lig["hb_eps"]))
+    return d, arr
+
+
+def validate_ligand_torsion_tree(lig: dict):
+    """(status, message) of the library's ligand checks; needs no GPU."""
+    d, _keep = _ligand_desc(lig)
+    buf = C.create_string_buffer(512)
+    rc = load().validate_ligand_torsion_tree(C.byref(d), buf, 512)
+    return rc, buf.value.decode()
+
+
+class Context:
+    """One adgb context on one CUDA device."""
+
+    def __init__(self, device: int = 0, threads_per_pose: int = 0, poses_per_block: int = 0,
+                 reduce_variant: int = REDUCE_SHFL):
+        self.lib = load()
+        self.h = C.c_void_p()
+        opts = _Options(threads_per_pose, poses_per_block, reduce_variant)
+        rc = self.lib.adgb_create(C.byref(self.h), device, C.byref(opts))
+        if rc != ADGB_OK:
+            raise AdgbError(rc, "adgb_create(device=%d)" % device)
+        self._keep = {}
+
+    def close(self):
+        if self.h:
+            self.lib.adgb_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc != ADGB_OK:
+            raise AdgbError(rc, self.lib.adgb_last_error(self.h).decode())
+
+    # ------------------------------------------------------------ uploads
+    def upload_receptor_grids(self, rec: dict) -> int:
+        g = _Grid(int(rec["nx"]), int(rec["ny"]), int(rec["nz"]), float(rec["spacing"]),
+                  (C.c_float * 3)(*[float(v) for v in rec["origin"]]), int(rec["n_type_maps"]))
+        maps = _f32(rec["maps"])
+        rid = C.c_int()
+        self._chk(self.lib.upload_receptor_grids(self.h, C.byref(g), maps.ctypes.data, C.byref(rid)))
+        return rid.value
+
+    def release_receptor(self, rid: int):
+        self._chk(self.lib.release_receptor(self.h, rid))
+
+    def upload_ligand_torsion_tree(self, lig: dict) -> int:
+        d, keep = _ligand_desc(lig)
+        lid = C.c_int()
+        self._chk(self.lib.upload_ligand_torsion_tree(self.h, C.byref(d), C.byref(lid)))
+        return lid.value
+
+    def release_ligand(self, lid: int):
+        self._chk(self.lib.release_ligand(self.h, lid))
+
+    # ------------------------------------------------------ device calls
+    def pose_coords_dev(self, lid, genes, xyz):
+        _check_dev(genes, "genes")
+        _check_dev(xyz, "xyz")
+        self._chk(self.lib.pose_coords_dev(self.h, lid, _ptr(genes), genes.shape[0], _ptr(xyz),
+                                           _stream()))
+
+    def score_poses_dev(self, rid, lid, genes, energy, grad=None, variant=-1):
+        _check_dev(genes, "genes")
+        _check_dev(energy, "energy")
+        if grad is not None:
+            _check_dev(grad, "grad")
+        self._chk(self.lib.score_poses_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
+                                           _ptr(energy), _ptr(grad), variant, _stream()))
+
+    def local_search_dev(self, rid, lid, genes, best_energy, iters, rho=0.8, eps=1e-2,
+                         variant=-1, state=None, resume=False):
+        _check_dev(genes, "genes")
+        _check_dev(best_energy, "best_energy")
+        if state is not None:
+            _check_dev(state, "state")
+        p = _LSParams(int(iters), float(rho), float(eps), int(variant), LS_RESUME if resume else 0)
+        self._chk(self.lib.local_search_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
+                                            C.byref(p), _ptr(best_energy), _ptr(state),
+                                            _stream()))
+
+    def reduce4_bench_dev(self, variant, x, threads, reps=1, out=None):
+        import torch
+        _check_dev(x, "x")
+        n_blocks = x.numel() // (4 * threads)
+        if out is None:
+            out = torch.empty_like(x)
+        self._chk(self.lib.reduce4_bench_dev(self.h, variant, _ptr(x), threads, n_blocks, reps,
+                                             _ptr(out), _stream()))
+        return out
+
+    # -------------------------------------------------------- host calls
+    def pose_coords(self, lid, genes, n_atoms):
+        g = _f32(genes)
+        out = np.zeros((g.shape[0], n_atoms, 3), np.float32)
+        self._chk(self.lib.pose_coords(self.h, lid, g.ctypes.data, g.shape[0], out.ctypes.data))
+        return out
+
+    def score_poses(self, rid, lid, genes, with_grad=True, variant=-1):
+        g = _f32(genes)
+        e = np.zeros(g.shape[0], np.float32)
+        gr = np.zeros_like(g) if with_grad else None
+        self._chk(self.lib.score_poses(self.h, rid, lid, g.ctypes.data, g.shape[0], e.ctypes.data,
+                                       _ptr(gr), variant))
+        return e, gr
+
+    def local_search(self, rid, lid, genes, iters, rho=0.8, eps=1e-2, variant=-1, state=None,
+                     resume=False, want_state=False):
+        """Host-buffer local search; genes are updated in place when they
+        are a float32 C-contiguous array, and returned either way."""
+        g = genes if (isinstance(genes, np.ndarray) and genes.dtype == np.float32
+                      and genes.flags.c_contiguous) else _f32(genes)
+        n, G = g.shape
+        e = np.zeros(n, np.float32)
+        st = None
+        if resume or want_state:
+            st = _f32(state) if state is not None else np.zeros((n, 3, G), np.float32)
+        p = _LSParams(int(iters), float(rho), float(eps), int(variant), LS_RESUME if resume else 0)
+        self._chk(self.lib.local_search(self.h, rid, lid, g.ctypes.data, n, C.byref(p), e.ctypes.data,
+                                        _ptr(st)))
+        return e, g, st
+
+    def local_search_host_ptr(self, rid, lid, genes_ptr, n, iters, best_ptr, rho=0.8, eps=1e-2,
+                              variant=-1):
+        """Host call on raw host pointers (pinned buffers of the caller)."""
+        p = _LSParams(int(iters), float(rho), float(eps), int(variant), 0)
+        self._chk(self.lib.local_search(self.h, rid, lid, genes_ptr, n, C.byref(p), best_ptr, None))

@@ -1,0 +1,106 @@
+// Internal device layouts of the adgb library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/adgb.h"
+
+namespace adgb {
+
+// Mehler-Solmajer distance-dependent dielectric eps(r) = A + B / (1 + k exp(-lambda B r)).
+constexpr float MS_A = -8.5525f;
+constexpr float MS_EPS0 = 78.4f;
+constexpr float MS_B = MS_EPS0 - MS_A;
+constexpr float MS_LAMBDA = 0.003627f;
+constexpr float MS_K = 7.7839f;
+
+constexpr int MAX_GENES = 6 + ADGB_MAX_TORS;
+constexpr int TYPE_TAB = ADGB_MAX_TYPES * ADGB_MAX_TYPES;
+
+// Receptor as the kernels see it.  cells[((iz*(ny-1)+iy)*(nx-1)+ix)][m][c]
+// holds map m at corner c = cx + 2 cy + 4 cz of cell (ix, iy, iz): one atom
+// reads three 32-byte runs (its type map, then e and d adjacent).
+struct RecDev {
+    int nx, ny, nz, M;      // points per axis, maps (types + e + d)
+    float lo[3], hi[3];     // first and last grid point per axis
+    float inv_h;            // 1 / spacing
+    const float *cells;
+};
+
+// Ligand as the kernels see it.  Atoms are stored in an internal order in
+// which every torsion's moving set is one contiguous range [start, end).
+struct LigDev {
+    int n_atoms, n_tors, n_pairs, n_types;
+    const float4 *ref;        // [N] reference x, y, z and charge q
+    const float2 *sv;         // [N] (w_ds * S_i, V_i), S_i = solpar + QSOL |q_i|
+    const int *type;          // [N] map index
+    const int *frag;          // [N] deepest torsion moving the atom, -1 = root fragment
+    const int *tparent;       // [T] enclosing torsion, -1 = root
+    const int4 *tatoms;       // [T] (a, b, start, end), internal indices
+    const float4 *taxis;      // [T] unit bond axis a->b in the reference conformation
+    const float4 *tbref;      // [T] reference position of b
+    const uint32_t *pairs;    // [Np] i | j << 8 | (ti*16+tj) << 16 | hb << 24
+    const float2 *tptab;      // [256] (A, B): E = A r^-12 - B r^-m, m = 10 if hb else 6
+    const int *perm;          // [N] internal index -> caller's index
+};
+
+// Shared-memory layout of one block of the scoring / local-search kernel:
+// per-ligand constants once, then per-pose working arrays.  All offsets in
+// bytes, 16-byte aligned.
+struct SmemLayout {
+    int ref, sv, type, frag, tparent, tatoms, taxis, tbref, tptab;
+    int pose0, pose_stride;          // first pose block, bytes per pose
+    // offsets inside one pose block
+    int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage;
+    int total;
+
+    static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+    __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose) {
+        int o = 0;
+        ref = o;     o = al16(o + 16 * N);
+        sv = o;      o = al16(o + 8 * N);
+        type = o;    o = al16(o + 4 * N);
+        frag = o;    o = al16(o + 4 * N);
+        tparent = o; o = al16(o + 4 * (T > 0 ? T : 1));
+        tatoms = o;  o = al16(o + 16 * (T > 0 ? T : 1));
+        taxis = o;   o = al16(o + 16 * (T > 0 ? T : 1));
+        tbref = o;   o = al16(o + 16 * (T > 0 ? T : 1));
+        tptab = o;   o = al16(o + 8 * TYPE_TAB);
+        pose0 = o;
+        int q = 0;
+        p_xyz = q;   q = al16(q + 16 * N);
+        p_grad = q;  q = al16(q + 16 * N);
+        p_genes = q; q = al16(q + 4 * MAX_GENES);
+        p_ggrad = q; q = al16(q + 4 * MAX_GENES);
+        p_sc = q;    q = al16(q + 8 * (ADGB_MAX_TORS + 4));
+        p_red = q;   q = al16(q + 4 * 8 * warps_per_pose);
+        p_stage = q; q = al16(q + 4 * 32 * 12 * warps_per_pose);
+        pose_stride = q;
+        total = pose0 + ppb * pose_stride;
+    }
+};
+
+// Launch configuration of the fused kernel.
+struct EvalCfg {
+    int tpp;        // threads per pose (32, 64, 128, 256)
+    int ppb;        // poses per block
+    int variant;    // ADGB_REDUCE_*
+};
+
+// Host-side launchers (eval.cu, reduce_bench.cu).
+cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
+                        int mode, const float *genes_in, float *genes_out, int n,
+                        int iters, float rho, float eps, int resume, float *energy,
+                        float *grad, float *state, cudaStream_t s);
+cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
+                          cudaStream_t s);
+cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M,
+                             float *cells, cudaStream_t s);
+cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int n_blocks,
+                                 int reps, float *out, cudaStream_t s);
+
+enum { MODE_SCORE = 0, MODE_LS = 1 };
+
+}  // namespace adgb

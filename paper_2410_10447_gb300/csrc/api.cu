@@ -1,0 +1,669 @@
+// C ABI of the adgb library: contexts, uploads (with validation and the
+// internal atom order), and the launches behind score_poses / local_search /
+// pose_coords / reduce4_bench.  See include/adgb.h for the contract.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "adgb_internal.cuh"
+
+using namespace adgb;
+
+namespace {
+
+struct Receptor {
+    RecDev dev;
+    float *cells = nullptr;
+    int n_type_maps = 0;
+};
+
+struct Ligand {
+    LigDev dev;
+    void *mem = nullptr;
+    int n_atoms = 0, n_tors = 0, n_types = 0, max_type = 0;
+};
+
+}  // namespace
+
+struct adgb_ctx {
+    int device = 0;
+    adgb_options opts{};
+    std::map<int, Receptor> recs;
+    std::map<int, Ligand> ligs;
+    int next_id = 1;
+    std::string err;
+    cudaStream_t stream = nullptr;  // used by the host-pointer calls
+    void *stage = nullptr;          // device staging for host-pointer calls
+    size_t stage_bytes = 0;
+};
+
+namespace {
+
+int fail(adgb_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int ferr(std::string *err, int code, const char *fmt, ...) {
+    if (err) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        *err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(adgb_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, ADGB_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes ctx's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite(float x) { return isfinite(x); }
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int stage_reserve(adgb_ctx *c, size_t bytes) {
+    if (bytes <= c->stage_bytes) return ADGB_OK;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->stage, bytes);
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "staging allocation of %zu bytes: %s",
+                                      bytes, cudaGetErrorString(e));
+    c->stage_bytes = bytes;
+    return ADGB_OK;
+}
+
+// ------------------------------------------------------------- ligand build
+struct Bits {
+    uint64_t w[4] = {0, 0, 0, 0};
+    void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+    bool has(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+    bool subset_of(const Bits &o) const {
+        for (int k = 0; k < 4; k++)
+            if (w[k] & ~o.w[k]) return false;
+        return true;
+    }
+    bool meets(const Bits &o) const {
+        for (int k = 0; k < 4; k++)
+            if (w[k] & o.w[k]) return true;
+        return false;
+    }
+};
+
+struct HostLigand {
+    int N, T, NP;
+    std::vector<float4> ref;
+    std::vector<float2> sv;
+    std::vector<int> type, frag, tparent, perm;
+    std::vector<int4> tatoms;
+    std::vector<float4> taxis, tbref;
+    std::vector<uint32_t> pairs;
+    std::vector<float2> tptab;
+    int max_type = 0;
+};
+
+int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
+    if (!d) return ferr(err, ADGB_EINVAL, "ligand: null descriptor");
+    const int N = d->n_atoms, T = d->n_tors, NP = d->n_pairs, NT = d->n_types;
+    if (N < 1 || N > ADGB_MAX_ATOMS) return ferr(err, ADGB_EINVAL, "ligand: n_atoms %d not in 1..%d", N, ADGB_MAX_ATOMS);
+    if (NT < 1 || NT > ADGB_MAX_TYPES) return ferr(err, ADGB_EINVAL, "ligand: n_types %d not in 1..%d", NT, ADGB_MAX_TYPES);
+    if (T < 0 || T > ADGB_MAX_TORS) return ferr(err, ADGB_EINVAL, "ligand: n_tors %d not in 0..%d", T, ADGB_MAX_TORS);
+    if (NP < 0) return ferr(err, ADGB_EINVAL, "ligand: n_pairs %d < 0", NP);
+    if (!d->type || !d->charge || !d->xyz || !d->R || !d->eps || !d->vol || !d->solpar || !d->hb_role)
+        return ferr(err, ADGB_EINVAL, "ligand: null per-atom or per-type array");
+    if (T > 0 && (!d->tors_bond || !d->mov_off)) return ferr(err, ADGB_EINVAL, "ligand: null torsion arrays");
+    if (NP > 0 && !d->pairs) return ferr(err, ADGB_EINVAL, "ligand: null pair list");
+    if (!finite(d->hb_R) || d->hb_R <= 0 || !finite(d->hb_eps) || d->hb_eps < 0)
+        return ferr(err, ADGB_EINVAL, "ligand: bad hydrogen-bond parameters");
+    for (int t = 0; t < NT; t++) {
+        if (!finite(d->R[t]) || d->R[t] <= 0 || !finite(d->eps[t]) || d->eps[t] < 0 ||
+            !finite(d->vol[t]) || !finite(d->solpar[t]) || d->hb_role[t] < 0 || d->hb_role[t] > 2)
+            return ferr(err, ADGB_EINVAL, "ligand: bad parameters of type %d", t);
+    }
+    for (int i = 0; i < N; i++) {
+        if (d->type[i] < 0 || d->type[i] >= NT) return ferr(err, ADGB_EINVAL, "ligand: atom %d type %d out of range", i, d->type[i]);
+        if (!finite(d->charge[i]) || !finite(d->xyz[3 * i]) || !finite(d->xyz[3 * i + 1]) || !finite(d->xyz[3 * i + 2]))
+            return ferr(err, ADGB_EINVAL, "ligand: atom %d has a non-finite value", i);
+    }
+    // torsion moving sets
+    std::vector<Bits> S(T);
+    if (T > 0) {
+        if (d->mov_off[0] != 0) return ferr(err, ADGB_EINVAL, "ligand: mov_off[0] != 0");
+        for (int k = 0; k < T; k++)
+            if (d->mov_off[k + 1] < d->mov_off[k]) return ferr(err, ADGB_EINVAL, "ligand: mov_off not monotone");
+        if (d->mov_off[T] > 0 && !d->mov_atoms) return ferr(err, ADGB_EINVAL, "ligand: null mov_atoms");
+    }
+    for (int k = 0; k < T; k++) {
+        const int a = d->tors_bond[2 * k], b = d->tors_bond[2 * k + 1];
+        if (a < 0 || a >= N || b < 0 || b >= N || a == b) return ferr(err, ADGB_EINVAL, "ligand: torsion %d bond (%d,%d) invalid", k, a, b);
+        const double dx = d->xyz[3 * b] - d->xyz[3 * a], dy = d->xyz[3 * b + 1] - d->xyz[3 * a + 1],
+                     dz = d->xyz[3 * b + 2] - d->xyz[3 * a + 2];
+        if (!(dx * dx + dy * dy + dz * dz > 0)) return ferr(err, ADGB_EINVAL, "ligand: torsion %d has a zero-length bond", k);
+        for (int m = d->mov_off[k]; m < d->mov_off[k + 1]; m++) {
+            const int i = d->mov_atoms[m];
+            if (i < 0 || i >= N) return ferr(err, ADGB_EINVAL, "ligand: torsion %d moves atom %d out of range", k, i);
+            if (S[k].has(i)) return ferr(err, ADGB_EINVAL, "ligand: torsion %d lists atom %d twice", k, i);
+            if (i == a || i == b) return ferr(err, ADGB_EINVAL, "ligand: torsion %d moves its own bond atom %d", k, i);
+            S[k].set(i);
+        }
+    }
+    // laminar tree, listed root to leaf
+    for (int k = 0; k < T; k++) {
+        const int ak = d->tors_bond[2 * k], bk = d->tors_bond[2 * k + 1];
+        for (int q = k + 1; q < T; q++) {
+            const int aq = d->tors_bond[2 * q], bq = d->tors_bond[2 * q + 1];
+            const bool inside = S[q].meets(S[k]) || S[k].has(aq) || S[k].has(bq);
+            if (inside) {
+                if (!S[q].subset_of(S[k]) || !S[k].has(bq) || !(S[k].has(aq) || aq == bk))
+                    return ferr(err, ADGB_EINVAL, "ligand: torsions %d and %d are neither nested nor disjoint", k, q);
+            } else if (S[q].has(ak) || S[q].has(bk)) {
+                return ferr(err, ADGB_EINVAL, "ligand: torsion %d encloses %d but is listed after it", q, k);
+            }
+        }
+    }
+    std::vector<int> tparent(T, -1), frag(N, -1);
+    for (int k = 0; k < T; k++) {
+        const int bk = d->tors_bond[2 * k + 1];
+        for (int q = k - 1; q >= 0; q--)
+            if (S[q].has(bk)) { tparent[k] = q; break; }
+    }
+    for (int i = 0; i < N; i++)
+        for (int k = T - 1; k >= 0; k--)
+            if (S[k].has(i)) { frag[i] = k; break; }
+    // depth-first order: a torsion's moving set becomes one contiguous range
+    std::vector<std::vector<int>> kids(T + 1);  // index 0 = root
+    for (int k = 0; k < T; k++) kids[tparent[k] + 1].push_back(k);
+    std::vector<int> perm, start(T, 0), end(T, 0);
+    perm.reserve(N);
+    std::vector<std::pair<int, int>> stack;  // (node, next child)
+    auto emit_own = [&](int node) {
+        for (int i = 0; i < N; i++)
+            if (frag[i] == node) perm.push_back(i);
+    };
+    emit_own(-1);
+    stack.push_back({-1, 0});
+    while (!stack.empty()) {
+        auto &top = stack.back();
+        const auto &ch = kids[top.first + 1];
+        if (top.second < (int)ch.size()) {
+            const int k = ch[top.second++];
+            start[k] = (int)perm.size();
+            emit_own(k);
+            stack.push_back({k, 0});
+        } else {
+            if (top.first >= 0) end[top.first] = (int)perm.size();
+            stack.pop_back();
+        }
+    }
+    if ((int)perm.size() != N) return ferr(err, ADGB_EINVAL, "ligand: torsion tree does not cover the atoms once");
+    std::vector<int> inv(N);
+    for (int n = 0; n < N; n++) inv[perm[n]] = n;
+    for (int k = 0; k < T; k++) {
+        if (end[k] - start[k] != d->mov_off[k + 1] - d->mov_off[k])
+            return ferr(err, ADGB_EINVAL, "ligand: torsion %d moving set is not a subtree", k);
+        for (int m = d->mov_off[k]; m < d->mov_off[k + 1]; m++) {
+            const int n = inv[d->mov_atoms[m]];
+            if (n < start[k] || n >= end[k]) return ferr(err, ADGB_EINVAL, "ligand: torsion %d moving set is not a subtree", k);
+        }
+    }
+    h.N = N;
+    h.T = T;
+    h.NP = NP;
+    h.perm = perm;
+    h.ref.resize(N);
+    h.sv.resize(N);
+    h.type.resize(N);
+    h.frag.resize(N);
+    for (int n = 0; n < N; n++) {
+        const int i = perm[n], t = d->type[i];
+        const float q = d->charge[i];
+        h.ref[n] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], q);
+        const double S_i = (double)d->solpar[t] + (double)ADGB_QSOL * fabs((double)q);
+        h.sv[n] = make_float2((float)((double)ADGB_W_DS * S_i), d->vol[t]);
+        h.type[n] = t;
+        h.frag[n] = frag[i];
+        h.max_type = std::max(h.max_type, t);
+    }
+    h.tparent = tparent;
+    h.tatoms.resize(T);
+    h.taxis.resize(T);
+    h.tbref.resize(T);
+    for (int k = 0; k < T; k++) {
+        const int a = d->tors_bond[2 * k], b = d->tors_bond[2 * k + 1];
+        const double dx = (double)d->xyz[3 * b] - d->xyz[3 * a], dy = (double)d->xyz[3 * b + 1] - d->xyz[3 * a + 1],
+                     dz = (double)d->xyz[3 * b + 2] - d->xyz[3 * a + 2];
+        const double l = sqrt(dx * dx + dy * dy + dz * dz);
+        h.tatoms[k] = make_int4(inv[a], inv[b], start[k], end[k]);
+        h.taxis[k] = make_float4((float)(dx / l), (float)(dy / l), (float)(dz / l), 0.f);
+        h.tbref[k] = make_float4(d->xyz[3 * b], d->xyz[3 * b + 1], d->xyz[3 * b + 2], 0.f);
+    }
+    h.pairs.resize(NP);
+    for (int p = 0; p < NP; p++) {
+        const int i = d->pairs[2 * p], j = d->pairs[2 * p + 1];
+        if (i < 0 || i >= N || j < 0 || j >= N || i == j)
+            return ferr(err, ADGB_EINVAL, "ligand: pair %d (%d,%d) invalid", p, i, j);
+        const int ti = d->type[i], tj = d->type[j];
+        const int ri = d->hb_role[ti], rj = d->hb_role[tj];
+        const uint32_t hb = (ri == 1 && rj == 2) || (ri == 2 && rj == 1);
+        h.pairs[p] = (uint32_t)inv[i] | (uint32_t)inv[j] << 8 |
+                     (uint32_t)(ti * ADGB_MAX_TYPES + tj) << 16 | hb << 24;
+    }
+    h.tptab.assign(TYPE_TAB, make_float2(0.f, 0.f));
+    for (int ti = 0; ti < NT; ti++)
+        for (int tj = 0; tj < NT; tj++) {
+            const int ri = d->hb_role[ti], rj = d->hb_role[tj];
+            const bool hb = (ri == 1 && rj == 2) || (ri == 2 && rj == 1);
+            double A, B;
+            if (hb) {
+                const double R = d->hb_R, e = d->hb_eps;
+                A = ADGB_W_HB * 5.0 * e * pow(R, 12);
+                B = ADGB_W_HB * 6.0 * e * pow(R, 10);
+            } else {
+                const double R = 0.5 * ((double)d->R[ti] + d->R[tj]);
+                const double e = sqrt((double)d->eps[ti] * d->eps[tj]);
+                A = ADGB_W_VDW * e * pow(R, 12);
+                B = ADGB_W_VDW * 2.0 * e * pow(R, 6);
+            }
+            h.tptab[ti * ADGB_MAX_TYPES + tj] = make_float2((float)A, (float)B);
+        }
+    return ADGB_OK;
+}
+
+EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
+    EvalCfg cfg;
+    cfg.variant = variant;
+    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 32;
+    int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 8;
+    while (ppb > 1 && cfg.tpp * ppb > 256) ppb--;
+    SmemLayout lay;
+    for (; ppb > 1; ppb--) {
+        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32);
+        if (lay.total <= 110 * 1024) break;
+    }
+    cfg.ppb = ppb;
+    return cfg;
+}
+
+int check_variant(adgb_ctx *c, int &variant) {
+    if (variant < 0) variant = c->opts.reduce_variant;
+    if (variant < 0 || variant >= ADGB_REDUCE_N) return fail(c, ADGB_EINVAL, "unknown reduce variant %d", variant);
+    return ADGB_OK;
+}
+
+int lookup(adgb_ctx *c, int rid, int lid, Receptor **R, Ligand **L) {
+    if (R) {
+        auto it = c->recs.find(rid);
+        if (it == c->recs.end()) return fail(c, ADGB_ENOTFOUND, "unknown receptor id %d", rid);
+        *R = &it->second;
+    }
+    auto jt = c->ligs.find(lid);
+    if (jt == c->ligs.end()) return fail(c, ADGB_ENOTFOUND, "unknown ligand id %d", lid);
+    *L = &jt->second;
+    if (R && *R && jt->second.max_type >= (*R)->n_type_maps)
+        return fail(c, ADGB_EINVAL, "ligand type %d has no map in receptor %d (%d type maps)",
+                    jt->second.max_type, rid, (*R)->n_type_maps);
+    return ADGB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts) {
+    if (!ctx) return ADGB_EINVAL;
+    *ctx = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ADGB_EDEVICE;
+    adgb_ctx *c = new (std::nothrow) adgb_ctx();
+    if (!c) return ADGB_ENOMEM;
+    c->device = device;
+    if (opts) c->opts = *opts;
+    if (c->opts.threads_per_pose != 0 && c->opts.threads_per_pose != 32 &&
+        c->opts.threads_per_pose != 64 && c->opts.threads_per_pose != 128) {
+        delete c;
+        return ADGB_EINVAL;
+    }
+    if (c->opts.poses_per_block < 0 || c->opts.poses_per_block > 8 ||
+        c->opts.reduce_variant < 0 || c->opts.reduce_variant >= ADGB_REDUCE_N) {
+        delete c;
+        return ADGB_EINVAL;
+    }
+    DeviceGuard g(device);
+    if (!g.ok || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return ADGB_EDEVICE;
+    }
+    *ctx = c;
+    return ADGB_OK;
+}
+
+int adgb_destroy(adgb_ctx *c) {
+    if (!c) return ADGB_EINVAL;
+    {
+        DeviceGuard g(c->device);
+        for (auto &kv : c->recs) cudaFree(kv.second.cells);
+        for (auto &kv : c->ligs) cudaFree(kv.second.mem);
+        if (c->stage) cudaFree(c->stage);
+        if (c->stream) cudaStreamDestroy(c->stream);
+    }
+    delete c;
+    return ADGB_OK;
+}
+
+const char *adgb_last_error(const adgb_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int upload_receptor_grids(adgb_ctx *c, const adgb_grid_desc *g, const float *maps, int *receptor_id) {
+    if (!c) return ADGB_EINVAL;
+    if (!g || !maps || !receptor_id) return fail(c, ADGB_EINVAL, "receptor: null argument");
+    if (g->nx < 2 || g->ny < 2 || g->nz < 2 || !(g->spacing > 0) || !finite(g->spacing) ||
+        g->n_type_maps < 1 || g->n_type_maps > 254 || !finite(g->origin[0]) ||
+        !finite(g->origin[1]) || !finite(g->origin[2]))
+        return fail(c, ADGB_EINVAL, "receptor: bad grid description");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
+    const int M = g->n_type_maps + 2;
+    const size_t npts = (size_t)g->nx * g->ny * g->nz;
+    const size_t ncell = (size_t)(g->nx - 1) * (g->ny - 1) * (g->nz - 1);
+    float *plain = nullptr, *cells = nullptr;
+    cudaError_t e = cudaMalloc(&plain, npts * M * sizeof(float));
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "receptor: %s", cudaGetErrorString(e));
+    e = cudaMalloc(&cells, ncell * M * 8 * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaFree(plain);
+        return fail(c, ADGB_ENOMEM, "receptor: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(plain, maps, npts * M * sizeof(float), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_pack_grid(plain, g->nx, g->ny, g->nz, M, cells, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(plain);
+    if (e != cudaSuccess) {
+        cudaFree(cells);
+        return cuda_fail(c, e, "receptor upload");
+    }
+    Receptor R;
+    R.cells = cells;
+    R.n_type_maps = g->n_type_maps;
+    R.dev.nx = g->nx;
+    R.dev.ny = g->ny;
+    R.dev.nz = g->nz;
+    R.dev.M = M;
+    const int n[3] = {g->nx, g->ny, g->nz};
+    for (int d = 0; d < 3; d++) {
+        R.dev.lo[d] = g->origin[d];
+        R.dev.hi[d] = (float)((double)g->origin[d] + (double)(n[d] - 1) * g->spacing);
+    }
+    R.dev.inv_h = (float)(1.0 / (double)g->spacing);
+    R.dev.cells = cells;
+    const int id = c->next_id++;
+    c->recs[id] = R;
+    *receptor_id = id;
+    return ADGB_OK;
+}
+
+int release_receptor(adgb_ctx *c, int id) {
+    if (!c) return ADGB_EINVAL;
+    auto it = c->recs.find(id);
+    if (it == c->recs.end()) return fail(c, ADGB_ENOTFOUND, "unknown receptor id %d", id);
+    DeviceGuard g(c->device);
+    cudaFree(it->second.cells);
+    c->recs.erase(it);
+    return ADGB_OK;
+}
+
+int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *ligand_id) {
+    if (!c) return ADGB_EINVAL;
+    if (!ligand_id) return fail(c, ADGB_EINVAL, "ligand: null id pointer");
+    HostLigand h;
+    int rc = build_ligand(&c->err, d, h);
+    if (rc) return rc;
+    const int N = h.N, T = h.T, NP = h.NP;
+    const int Tz = T > 0 ? T : 1, NPz = NP > 0 ? NP : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
+    const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
+    const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
+    const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
+    std::vector<unsigned char> buf(off, 0);
+    memcpy(&buf[o_ref], h.ref.data(), 16 * N);
+    memcpy(&buf[o_sv], h.sv.data(), 8 * N);
+    memcpy(&buf[o_type], h.type.data(), 4 * N);
+    memcpy(&buf[o_frag], h.frag.data(), 4 * N);
+    if (T) {
+        memcpy(&buf[o_tpar], h.tparent.data(), 4 * T);
+        memcpy(&buf[o_tat], h.tatoms.data(), 16 * T);
+        memcpy(&buf[o_tax], h.taxis.data(), 16 * T);
+        memcpy(&buf[o_tb], h.tbref.data(), 16 * T);
+    }
+    if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
+    memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
+    memcpy(&buf[o_perm], h.perm.data(), 4 * N);
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
+    unsigned char *mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, off);
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "ligand: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(mem, buf.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return cuda_fail(c, e, "ligand upload");
+    }
+    Ligand L;
+    L.mem = mem;
+    L.n_atoms = N;
+    L.n_tors = T;
+    L.n_types = d->n_types;
+    L.max_type = h.max_type;
+    LigDev &v = L.dev;
+    v.n_atoms = N;
+    v.n_tors = T;
+    v.n_pairs = NP;
+    v.n_types = d->n_types;
+    v.ref = reinterpret_cast<const float4 *>(mem + o_ref);
+    v.sv = reinterpret_cast<const float2 *>(mem + o_sv);
+    v.type = reinterpret_cast<const int *>(mem + o_type);
+    v.frag = reinterpret_cast<const int *>(mem + o_frag);
+    v.tparent = reinterpret_cast<const int *>(mem + o_tpar);
+    v.tatoms = reinterpret_cast<const int4 *>(mem + o_tat);
+    v.taxis = reinterpret_cast<const float4 *>(mem + o_tax);
+    v.tbref = reinterpret_cast<const float4 *>(mem + o_tb);
+    v.pairs = reinterpret_cast<const uint32_t *>(mem + o_pairs);
+    v.tptab = reinterpret_cast<const float2 *>(mem + o_tab);
+    v.perm = reinterpret_cast<const int *>(mem + o_perm);
+    const int id = c->next_id++;
+    c->ligs[id] = L;
+    *ligand_id = id;
+    return ADGB_OK;
+}
+
+int validate_ligand_torsion_tree(const adgb_ligand_desc *d, char *msg, int msg_len) {
+    std::string err;
+    HostLigand h;
+    const int rc = build_ligand(&err, d, h);
+    if (msg && msg_len > 0) {
+        strncpy(msg, err.c_str(), (size_t)msg_len - 1);
+        msg[msg_len - 1] = 0;
+    }
+    return rc;
+}
+
+int release_ligand(adgb_ctx *c, int id) {
+    if (!c) return ADGB_EINVAL;
+    auto it = c->ligs.find(id);
+    if (it == c->ligs.end()) return fail(c, ADGB_ENOTFOUND, "unknown ligand id %d", id);
+    DeviceGuard g(c->device);
+    cudaFree(it->second.mem);
+    c->ligs.erase(it);
+    return ADGB_OK;
+}
+
+int pose_coords_dev(adgb_ctx *c, int ligand_id, const float *genes_dev, int n, float *xyz_dev,
+                    adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!genes_dev || !xyz_dev))) return fail(c, ADGB_EINVAL, "pose_coords: bad arguments");
+    Ligand *L = nullptr;
+    int rc = lookup(c, 0, ligand_id, nullptr, &L);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_coords(L->dev, genes_dev, n, xyz_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "pose_coords");
+}
+
+int pose_coords(adgb_ctx *c, int ligand_id, const float *genes, int n, float *xyz) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!genes || !xyz))) return fail(c, ADGB_EINVAL, "pose_coords: bad arguments");
+    Ligand *L = nullptr;
+    int rc = lookup(c, 0, ligand_id, nullptr, &L);
+    if (rc || n == 0) return rc;
+    DeviceGuard g(c->device);
+    const size_t G = 6 + L->n_tors, bg = al256(4 * G * n), bx = 4 * 3 * (size_t)L->n_atoms * n;
+    if ((rc = stage_reserve(c, bg + bx))) return rc;
+    float *dg = (float *)c->stage, *dx = (float *)((char *)c->stage + bg);
+    cudaError_t e = cudaMemcpyAsync(dg, genes, 4 * G * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_coords(L->dev, dg, n, dx, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(xyz, dx, bx, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "pose_coords");
+}
+
+int score_poses_dev(adgb_ctx *c, int receptor_id, int ligand_id, const float *genes_dev, int n,
+                    float *energy_dev, float *grad_dev, int variant, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!genes_dev || !energy_dev))) return fail(c, ADGB_EINVAL, "score_poses: bad arguments");
+    int rc = check_variant(c, variant);
+    if (rc) return rc;
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_eval(R->dev, L->dev, pick_cfg(c, *L, variant), MODE_SCORE, genes_dev,
+                                nullptr, n, 1, 0.f, 0.f, 0, energy_dev, grad_dev, nullptr,
+                                (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "score_poses");
+}
+
+int score_poses(adgb_ctx *c, int receptor_id, int ligand_id, const float *genes, int n,
+                float *energy, float *grad, int variant) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!genes || !energy))) return fail(c, ADGB_EINVAL, "score_poses: bad arguments");
+    int rc = check_variant(c, variant);
+    if (rc) return rc;
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L)) || n == 0) return rc;
+    DeviceGuard g(c->device);
+    const size_t G = 6 + L->n_tors, bg = al256(4 * G * n), be = al256(4 * (size_t)n);
+    if ((rc = stage_reserve(c, 2 * bg + be))) return rc;
+    float *dg = (float *)c->stage, *de = (float *)((char *)c->stage + bg);
+    float *dgr = (float *)((char *)c->stage + bg + be);
+    cudaError_t e = cudaMemcpyAsync(dg, genes, 4 * G * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_eval(R->dev, L->dev, pick_cfg(c, *L, variant), MODE_SCORE, dg, nullptr, n, 1,
+                        0.f, 0.f, 0, de, grad ? dgr : nullptr, nullptr, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, dgr, 4 * G * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "score_poses");
+}
+
+static int check_ls(adgb_ctx *c, const adgb_ls_params *p, int &variant) {
+    if (!p) return fail(c, ADGB_EINVAL, "local_search: null parameters");
+    if (p->iters < 0 || !(p->rho > 0.f && p->rho < 1.f) || !(p->eps > 0.f) || !finite(p->eps))
+        return fail(c, ADGB_EINVAL, "local_search: bad parameters");
+    if (p->flags & ~ADGB_LS_RESUME) return fail(c, ADGB_EINVAL, "local_search: unknown flags");
+    variant = p->reduce_variant;
+    return check_variant(c, variant);
+}
+
+int local_search_dev(adgb_ctx *c, int receptor_id, int ligand_id, float *genes_dev, int n,
+                     const adgb_ls_params *p, float *best_energy_dev, float *state_dev,
+                     adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant, rc = check_ls(c, p, variant);
+    if (rc) return rc;
+    const bool resume = p->flags & ADGB_LS_RESUME;
+    if (n < 0 || (n > 0 && (!genes_dev || !best_energy_dev || (resume && !state_dev))))
+        return fail(c, ADGB_EINVAL, "local_search: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_eval(R->dev, L->dev, pick_cfg(c, *L, variant), MODE_LS, genes_dev,
+                                genes_dev, n, p->iters, p->rho, p->eps, resume, best_energy_dev,
+                                nullptr, state_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search");
+}
+
+int local_search(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int n,
+                 const adgb_ls_params *p, float *best_energy, float *state) {
+    if (!c) return ADGB_EINVAL;
+    int variant, rc = check_ls(c, p, variant);
+    if (rc) return rc;
+    const bool resume = p->flags & ADGB_LS_RESUME;
+    if (n < 0 || (n > 0 && (!genes || !best_energy || (resume && !state))))
+        return fail(c, ADGB_EINVAL, "local_search: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L)) || n == 0) return rc;
+    DeviceGuard g(c->device);
+    const size_t G = 6 + L->n_tors, bg = al256(4 * G * n), be = al256(4 * (size_t)n);
+    const size_t bs = state ? al256(4 * 3 * G * n) : 0;
+    if ((rc = stage_reserve(c, bg + be + bs))) return rc;
+    float *dg = (float *)c->stage, *de = (float *)((char *)c->stage + bg);
+    float *ds = state ? (float *)((char *)c->stage + bg + be) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dg, genes, 4 * G * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && resume) e = cudaMemcpyAsync(ds, state, 4 * 3 * G * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_eval(R->dev, L->dev, pick_cfg(c, *L, variant), MODE_LS, dg, dg, n, p->iters,
+                        p->rho, p->eps, resume, de, nullptr, ds, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(genes, dg, 4 * G * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best_energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && state) e = cudaMemcpyAsync(state, ds, 4 * 3 * G * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search");
+}
+
+int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads, int n_blocks,
+                      int reps, float *out_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    const bool mma = variant == ADGB_REDUCE_MMA_TF32X2 || variant == ADGB_REDUCE_MMA_BF16X3;
+    if (!(mma || variant == ADGB_REDUCE_SHFL || variant == ADGB_REDUCE4_PAPER_FS))
+        return fail(c, ADGB_EINVAL, "reduce4_bench: unknown variant %d", variant);
+    if (threads < 32 || threads > 1024 || threads % 32 || n_blocks < 1 || reps < 1 || !in_dev || !out_dev)
+        return fail(c, ADGB_EINVAL, "reduce4_bench: bad arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_reduce4_bench(variant, in_dev, threads, n_blocks, reps, out_dev,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "reduce4_bench");
+}
+
+}  // extern "C"

@@ -1,0 +1,539 @@
+// Fused scoring / ADADELTA local-search kernel (Sec. 2.1, Sec. 3): one pose
+// group of TPP threads per genotype, several pose groups per block sharing
+// the ligand's constants in shared memory.  One launch runs every
+// genotype's whole local search; between evaluations nothing leaves the SM
+// except the grid-map gathers.
+//
+// Per evaluation (group barrier = __syncwarp for TPP = 32, bar.sync with a
+// per-group id otherwise):
+//   1. gene owners publish the genes and sin / (1 - cos) of every angle;
+//   2. each thread builds its atoms' coordinates (torsions deepest-first
+//      about reference axes, then rotation, then translation) and their
+//      trilinear grid energy and gradient;
+//   3. threads stride over the pair list: four pair terms, forces added to
+//      both atoms in shared memory;
+//   4. per-thread partials of (E, sum g, torque) and the torsion gradients
+//      (each torsion's moving set is one contiguous atom range);
+//   5. one 8-wide reduce-and-broadcast (warp shuffles or tensor cores);
+//   6. gene gradient, best tracking and the ADADELTA update by the threads
+//      that own the genes.
+#include <math.h>
+
+#include "adgb_internal.cuh"
+#include "reduce.cuh"
+
+namespace adgb {
+
+struct EvalArgs {
+    RecDev rec;
+    LigDev lig;
+    SmemLayout L;
+    const float *genes_in;
+    float *genes_out;
+    float *energy;
+    float *grad;
+    float *state;
+    int n, iters, resume, mode;
+    float rho, eps;
+};
+
+constexpr float KQQ = ADGB_W_EL * ADGB_ELEC_KCAL;
+constexpr float INV_SIG2 = 1.0f / (ADGB_DS_SIGMA * ADGB_DS_SIGMA);
+constexpr float HALF_INV_SIG2 = 0.5f / (ADGB_DS_SIGMA * ADGB_DS_SIGMA);
+constexpr float RMIN2 = ADGB_R_MIN * ADGB_R_MIN;
+constexpr float PI_F = 3.14159265358979f;
+constexpr int SC_ROT = ADGB_MAX_TORS;  // sc[] slots after the torsions: phi, theta, alpha
+
+template <int TPP>
+__device__ __forceinline__ void group_sync(int group) {
+    if constexpr (TPP == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(group + 1), "r"(TPP) : "memory");
+    }
+}
+
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// p += s (k x v) + omc (k x (k x v)), v = p - b: rotation by the angle with
+// sin = s, 1 - cos = omc about the axis k through b.  Exact at s = omc = 0.
+__device__ __forceinline__ void rotate_about(float3 &p, float4 k4, float4 b4, float2 c) {
+    const float3 k = make_float3(k4.x, k4.y, k4.z);
+    const float3 v = make_float3(p.x - b4.x, p.y - b4.y, p.z - b4.z);
+    const float3 kv = cross3(k, v);
+    const float3 kkv = cross3(k, kv);
+    p.x += c.x * kv.x + c.y * kkv.x;
+    p.y += c.x * kv.y + c.y * kkv.y;
+    p.z += c.x * kv.z + c.y * kkv.z;
+}
+
+// Intermolecular term of one atom: the atom type's map plus q times e plus
+// |q| times d, trilinearly interpolated at the point clamped onto the grid;
+// a point outside pays W_OUT times its squared distance to the grid.
+__device__ __forceinline__ float inter_atom(const RecDev &R, int t, float q, float3 x,
+                                            float3 &g) {
+    const float xs[3] = {x.x, x.y, x.z};
+    const int n[3] = {R.nx, R.ny, R.nz};
+    float f[3], gout[3], pen = 0.f;
+    bool ins[3];
+    int i0[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const float xc = fminf(fmaxf(xs[d], R.lo[d]), R.hi[d]);
+        ins[d] = xs[d] >= R.lo[d] && xs[d] <= R.hi[d];
+        const float dd = xs[d] - xc;
+        pen += dd * dd;
+        gout[d] = 2.f * ADGB_W_OUT * dd;
+        const float u = (xc - R.lo[d]) * R.inv_h;
+        int c = (int)u;  // u >= 0
+        c = c > n[d] - 2 ? n[d] - 2 : c;
+        i0[d] = c;
+        f[d] = u - (float)c;
+    }
+    const size_t cell = ((size_t)i0[2] * (R.ny - 1) + i0[1]) * (R.nx - 1) + i0[0];
+    const float4 *cp = reinterpret_cast<const float4 *>(R.cells + cell * (size_t)R.M * 8);
+    const float4 t0 = __ldg(cp + 2 * t), t1 = __ldg(cp + 2 * t + 1);
+    const float4 e0 = __ldg(cp + 2 * (R.M - 2)), e1 = __ldg(cp + 2 * (R.M - 2) + 1);
+    const float4 d0 = __ldg(cp + 2 * (R.M - 1)), d1 = __ldg(cp + 2 * (R.M - 1) + 1);
+    const float aq = fabsf(q);
+    // corner c = cx + 2 cy + 4 cz; w = map_t + q e + |q| d at that corner
+    const float w0 = t0.x + q * e0.x + aq * d0.x, w1 = t0.y + q * e0.y + aq * d0.y;
+    const float w2 = t0.z + q * e0.z + aq * d0.z, w3 = t0.w + q * e0.w + aq * d0.w;
+    const float w4 = t1.x + q * e1.x + aq * d1.x, w5 = t1.y + q * e1.y + aq * d1.y;
+    const float w6 = t1.z + q * e1.z + aq * d1.z, w7 = t1.w + q * e1.w + aq * d1.w;
+    const float fx = f[0], fy = f[1], fz = f[2];
+    const float x00 = w1 - w0, x10 = w3 - w2, x01 = w5 - w4, x11 = w7 - w6;
+    const float c00 = w0 + fx * x00, c10 = w2 + fx * x10;
+    const float c01 = w4 + fx * x01, c11 = w6 + fx * x11;
+    const float y0 = c10 - c00, y1 = c11 - c01;
+    const float c0 = c00 + fy * y0, c1 = c01 + fy * y1;
+    const float val = c0 + fz * (c1 - c0);
+    const float dx0 = x00 + fy * (x10 - x00), dx1 = x01 + fy * (x11 - x01);
+    const float dfx = dx0 + fz * (dx1 - dx0);
+    const float dfy = y0 + fz * (y1 - y0);
+    const float dfz = c1 - c0;
+    g.x = (ins[0] ? dfx * R.inv_h : 0.f) + gout[0];
+    g.y = (ins[1] ? dfy * R.inv_h : 0.f) + gout[1];
+    g.z = (ins[2] ? dfz * R.inv_h : 0.f) + gout[2];
+    return val + ADGB_W_OUT * pen;
+}
+
+// One intramolecular pair: 12-6 (12-10 for donor-acceptor pairs) with
+// A r^-12 - B r^-m, Coulomb with the Mehler-Solmajer dielectric, and
+// desolvation.  Returns the energy; f = dE/dx_i (atom j gets -f).
+__device__ __forceinline__ float pair_term(float4 xi, float4 xj, float2 svi, float2 svj,
+                                           float2 ab, bool hb, float3 &f) {
+    const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const bool live = r2 >= RMIN2;
+    const float r2c = fmaxf(r2, RMIN2);
+    const float rinv = rsqrtf(r2c);
+    const float rc = r2c * rinv;
+    const float r2i = rinv * rinv;
+    const float r6i = r2i * r2i * r2i;
+    const float r12i = r6i * r6i;
+    const float rmi = hb ? r6i * r2i * r2i : r6i;
+    const float m = hb ? 10.f : 6.f;
+    const float evdw = ab.x * r12i - ab.y * rmi;
+    const float dvdw = (-12.f * ab.x * r12i + m * ab.y * rmi) * rinv;
+    const float C = KQQ * xi.w * xj.w;
+    const float ex = __expf(-MS_LAMBDA * MS_B * rc);
+    const float iden = __fdividef(1.f, 1.f + MS_K * ex);
+    const float epsr = MS_A + MS_B * iden;
+    const float deps = (MS_B * MS_K * MS_LAMBDA * MS_B) * ex * iden * iden;
+    const float eel = __fdividef(C * rinv, epsr);
+    const float del = -eel * (rinv + __fdividef(deps, epsr));
+    const float eds = (svi.x * svj.y + svj.x * svi.y) * __expf(-r2 * HALF_INV_SIG2);
+    const float fr = live ? (dvdw + del) * rinv : 0.f;
+    const float fd = -eds * INV_SIG2;
+    f = make_float3((fr + fd) * dx, (fr + fd) * dy, (fr + fd) * dz);
+    return evdw + eel + eds;
+}
+
+template <int TPP, int VAR>
+__device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage, int group,
+                                           int gt) {
+    warp_sum8<VAR>(v, stage);
+    if constexpr (TPP > 32) {
+        const int w = gt >> 5;
+        if ((gt & 31) == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; c++) red[w * 8 + c] = v[c];
+        }
+        group_sync<TPP>(group);
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            float s = red[c];
+#pragma unroll
+            for (int k = 1; k < TPP / 32; k++) s += red[k * 8 + c];
+            v[c] = s;
+        }
+    }
+}
+
+template <int TPP, int VAR>
+__global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const LigDev &lig = a.lig;
+    const RecDev &rec = a.rec;
+    const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
+    float4 *s_ref = reinterpret_cast<float4 *>(sm + a.L.ref);
+    float2 *s_sv = reinterpret_cast<float2 *>(sm + a.L.sv);
+    int *s_type = reinterpret_cast<int *>(sm + a.L.type);
+    int *s_frag = reinterpret_cast<int *>(sm + a.L.frag);
+    int *s_tpar = reinterpret_cast<int *>(sm + a.L.tparent);
+    int4 *s_tat = reinterpret_cast<int4 *>(sm + a.L.tatoms);
+    float4 *s_tax = reinterpret_cast<float4 *>(sm + a.L.taxis);
+    float4 *s_tb = reinterpret_cast<float4 *>(sm + a.L.tbref);
+    float2 *s_tab = reinterpret_cast<float2 *>(sm + a.L.tptab);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        s_ref[i] = lig.ref[i];
+        s_sv[i] = lig.sv[i];
+        s_type[i] = lig.type[i];
+        s_frag[i] = lig.frag[i];
+    }
+    for (int k = threadIdx.x; k < T; k += blockDim.x) {
+        s_tpar[k] = lig.tparent[k];
+        s_tat[k] = lig.tatoms[k];
+        s_tax[k] = lig.taxis[k];
+        s_tb[k] = lig.tbref[k];
+    }
+    for (int k = threadIdx.x; k < TYPE_TAB; k += blockDim.x) s_tab[k] = lig.tptab[k];
+    __syncthreads();
+
+    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
+    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
+    if (pose >= a.n) return;
+    unsigned char *P = sm + a.L.pose0 + group * a.L.pose_stride;
+    float4 *xyz = reinterpret_cast<float4 *>(P + a.L.p_xyz);
+    float4 *grd = reinterpret_cast<float4 *>(P + a.L.p_grad);
+    float *genes_s = reinterpret_cast<float *>(P + a.L.p_genes);
+    float *ggrad = reinterpret_cast<float *>(P + a.L.p_ggrad);
+    float2 *sc = reinterpret_cast<float2 *>(P + a.L.p_sc);
+    float *red = reinterpret_cast<float *>(P + a.L.p_red);
+    float *stage = reinterpret_cast<float *>(P + a.L.p_stage) + (gt >> 5) * 32 * 12;
+
+    constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
+    float om[NG], eg2[NG], ed2[NG], best[NG];
+#pragma unroll
+    for (int r = 0; r < NG; r++) {
+        const int j = gt + r * TPP;
+        om[r] = eg2[r] = ed2[r] = 0.f;
+        if (j < G) {
+            if (a.resume) {
+                const float *st = a.state + (size_t)pose * 3 * G;
+                om[r] = st[j];
+                eg2[r] = st[G + j];
+                ed2[r] = st[2 * G + j];
+            } else {
+                om[r] = a.genes_in[(size_t)pose * G + j];
+            }
+        }
+        best[r] = om[r];
+    }
+    float best_e = INFINITY;
+    const int iters = a.mode == MODE_SCORE ? 1 : a.iters;
+
+    for (int it = 0; it < iters; it++) {
+        // 1. publish genes, sin and 1 - cos of every angle (half-angle form:
+        //    sin = 2 sh ch, 1 - cos = 2 sh^2, exact zero at a zero angle)
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int j = gt + r * TPP;
+            if (j < G) {
+                genes_s[j] = om[r];
+                if (j >= 3) {
+                    if (j == 3 || j == 4) {
+                        float s, c;
+                        sincosf(om[r], &s, &c);
+                        sc[SC_ROT + j - 3] = make_float2(s, c);
+                    } else {
+                        float sh, ch;
+                        sincosf(0.5f * om[r], &sh, &ch);
+                        const float2 v = make_float2(2.f * sh * ch, 2.f * sh * sh);
+                        if (j == 5) sc[SC_ROT + 2] = v;
+                        else sc[j - 6] = v;
+                    }
+                }
+            }
+        }
+        group_sync<TPP>(group);
+        const float3 tr = make_float3(genes_s[0], genes_s[1], genes_s[2]);
+        const float2 sphi = sc[SC_ROT], sth = sc[SC_ROT + 1], sal = sc[SC_ROT + 2];
+        const float3 u = make_float3(sth.x * sphi.y, sth.x * sphi.x, sth.y);
+        // R - I = sin(a) [u]x + (1 - cos(a)) (u u^T - I)
+        const float s = sal.x, o = sal.y;
+        const float m00 = o * (u.x * u.x - 1.f), m11 = o * (u.y * u.y - 1.f),
+                    m22 = o * (u.z * u.z - 1.f);
+        const float m01 = o * u.x * u.y - s * u.z, m10 = o * u.x * u.y + s * u.z;
+        const float m02 = o * u.x * u.z + s * u.y, m20 = o * u.x * u.z - s * u.y;
+        const float m12 = o * u.y * u.z - s * u.x, m21 = o * u.y * u.z + s * u.x;
+
+        // 2. coordinates and intermolecular terms
+        float e_part = 0.f;
+        for (int i = gt; i < N; i += TPP) {
+            const float4 r4 = s_ref[i];
+            float3 p = make_float3(r4.x, r4.y, r4.z);
+            for (int k = s_frag[i]; k >= 0; k = s_tpar[k]) rotate_about(p, s_tax[k], s_tb[k], sc[k]);
+            float3 x;
+            x.x = p.x + (m00 * p.x + m01 * p.y + m02 * p.z) + tr.x;
+            x.y = p.y + (m10 * p.x + m11 * p.y + m12 * p.z) + tr.y;
+            x.z = p.z + (m20 * p.x + m21 * p.y + m22 * p.z) + tr.z;
+            xyz[i] = make_float4(x.x, x.y, x.z, r4.w);
+            float3 g;
+            e_part += inter_atom(rec, s_type[i], r4.w, x, g);
+            grd[i] = make_float4(g.x, g.y, g.z, 0.f);
+        }
+        group_sync<TPP>(group);
+
+        // 3. intramolecular pairs
+        for (int p = gt; p < NP; p += TPP) {
+            const uint32_t pr = __ldg(lig.pairs + p);
+            const int i = pr & 255, j = (pr >> 8) & 255;
+            float3 f;
+            e_part += pair_term(xyz[i], xyz[j], s_sv[i], s_sv[j], s_tab[(pr >> 16) & 255],
+                                (pr >> 24) & 1, f);
+            atomicAdd(&grd[i].x, f.x);
+            atomicAdd(&grd[i].y, f.y);
+            atomicAdd(&grd[i].z, f.z);
+            atomicAdd(&grd[j].x, -f.x);
+            atomicAdd(&grd[j].y, -f.y);
+            atomicAdd(&grd[j].z, -f.z);
+        }
+        group_sync<TPP>(group);
+
+        // 4. partial sums of (E, sum g, torque about the centre); torsion gradients
+        float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int i = gt; i < N; i += TPP) {
+            const float4 g = grd[i], x = xyz[i];
+            const float3 d = make_float3(x.x - tr.x, x.y - tr.y, x.z - tr.z);
+            v[1] += g.x;
+            v[2] += g.y;
+            v[3] += g.z;
+            v[4] += d.y * g.z - d.z * g.y;
+            v[5] += d.z * g.x - d.x * g.z;
+            v[6] += d.x * g.y - d.y * g.x;
+        }
+        for (int k = gt; k < T; k += TPP) {
+            const int4 ta = s_tat[k];
+            const float4 xa = xyz[ta.x], xb = xyz[ta.y];
+            float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
+            const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
+            float3 acc = make_float3(0.f, 0.f, 0.f);
+            for (int i = ta.z; i < ta.w; i++) {
+                const float4 x = xyz[i], g = grd[i];
+                const float3 d = make_float3(x.x - xb.x, x.y - xb.y, x.z - xb.z);
+                acc.x += d.y * g.z - d.z * g.y;
+                acc.y += d.z * g.x - d.x * g.z;
+                acc.z += d.x * g.y - d.y * g.x;
+            }
+            ggrad[6 + k] = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
+        }
+
+        // 5. one reduce-and-broadcast of the 8-vector
+        group_sum8<TPP, VAR>(v, red, stage, group, gt);
+        group_sync<TPP>(group);  // torsion gradients visible
+
+        // 6. gene gradient, best tracking, ADADELTA
+        const float E = v[0];
+        float gj[NG];
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int j = gt + r * TPP;
+            float g = 0.f;
+            if (j < 3) {
+                g = v[1 + j];
+            } else if (j < 5) {
+                // d u / d phi or d theta; angular velocity sin(a) du + (1-cos a) u x du
+                const float3 du = j == 3 ? make_float3(-sth.x * sphi.x, sth.x * sphi.y, 0.f)
+                                         : make_float3(sth.y * sphi.y, sth.y * sphi.x, -sth.x);
+                const float3 uxd = cross3(u, du);
+                const float3 w = make_float3(s * du.x + o * uxd.x, s * du.y + o * uxd.y,
+                                             s * du.z + o * uxd.z);
+                g = v[4] * w.x + v[5] * w.y + v[6] * w.z;
+            } else if (j == 5) {
+                g = v[4] * u.x + v[5] * u.y + v[6] * u.z;
+            } else if (j < G) {
+                g = ggrad[j];
+            }
+            gj[r] = g;
+        }
+        if (a.mode == MODE_SCORE) {
+            if (gt == 0) a.energy[pose] = E;
+            if (a.grad) {
+#pragma unroll
+                for (int r = 0; r < NG; r++) {
+                    const int j = gt + r * TPP;
+                    if (j < G) a.grad[(size_t)pose * G + j] = gj[r];
+                }
+            }
+            return;
+        }
+        if (E < best_e) {
+            best_e = E;
+#pragma unroll
+            for (int r = 0; r < NG; r++) best[r] = om[r];
+        }
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int j = gt + r * TPP;
+            if (j < G) {
+                const float g = gj[r];
+                eg2[r] = a.rho * eg2[r] + (1.f - a.rho) * g * g;
+                const float d = -sqrtf(ed2[r] + a.eps) * rsqrtf(eg2[r] + a.eps) * g;
+                ed2[r] = a.rho * ed2[r] + (1.f - a.rho) * d * d;
+                float w = om[r] + d;
+                if (j >= 6) w -= 2.f * PI_F * floorf((w + PI_F) * (0.5f / PI_F));
+                om[r] = w;
+            }
+        }
+    }
+    if (a.mode == MODE_SCORE) return;  // iters == 0 never reaches here in score mode
+#pragma unroll
+    for (int r = 0; r < NG; r++) {
+        const int j = gt + r * TPP;
+        if (j < G) {
+            a.genes_out[(size_t)pose * G + j] = best[r];
+            if (a.state) {
+                float *st = a.state + (size_t)pose * 3 * G;
+                st[j] = om[r];
+                st[G + j] = eg2[r];
+                st[2 * G + j] = ed2[r];
+            }
+        }
+    }
+    if (gt == 0) a.energy[pose] = best_e;
+}
+
+template <int TPP, int VAR>
+static cudaError_t launch_t(const EvalArgs &a, int ppb, cudaStream_t s) {
+    auto k = eval_kernel<TPP, VAR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         a.L.total);
+    if (e != cudaSuccess) return e;
+    const int blocks = (a.n + ppb - 1) / ppb;
+    k<<<blocks, TPP * ppb, a.L.total, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPP>
+static cudaError_t launch_v(const EvalArgs &a, int ppb, int variant, cudaStream_t s) {
+    switch (variant) {
+        case ADGB_REDUCE_SHFL: return launch_t<TPP, ADGB_REDUCE_SHFL>(a, ppb, s);
+        case ADGB_REDUCE_MMA_TF32X2: return launch_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, ppb, s);
+        case ADGB_REDUCE_MMA_BF16X3: return launch_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, ppb, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, int mode,
+                        const float *genes_in, float *genes_out, int n, int iters, float rho,
+                        float eps, int resume, float *energy, float *grad, float *state,
+                        cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    EvalArgs a;
+    a.rec = rec;
+    a.lig = lig;
+    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32);
+    a.genes_in = genes_in;
+    a.genes_out = genes_out;
+    a.energy = energy;
+    a.grad = grad;
+    a.state = state;
+    a.n = n;
+    a.iters = iters;
+    a.resume = resume;
+    a.mode = mode;
+    a.rho = rho;
+    a.eps = eps;
+    switch (cfg.tpp) {
+        case 32: return launch_v<32>(a, cfg.ppb, cfg.variant, s);
+        case 64: return launch_v<64>(a, cfg.ppb, cfg.variant, s);
+        case 128: return launch_v<128>(a, cfg.ppb, cfg.variant, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------ pose -> coords
+// One block per genotype: coordinates only, written in the caller's atom order.
+__global__ void __launch_bounds__(128) coords_kernel(const LigDev lig, const float *genes,
+                                                     int n, float *out) {
+    __shared__ float2 sc[ADGB_MAX_TORS + 3];
+    const int pose = blockIdx.x;
+    const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T;
+    const float *gp = genes + (size_t)pose * G;
+    for (int j = threadIdx.x; j < G; j += blockDim.x) {
+        if (j == 3 || j == 4) {
+            float s, c;
+            sincosf(gp[j], &s, &c);
+            sc[SC_ROT + j - 3] = make_float2(s, c);
+        } else if (j >= 5) {
+            float sh, ch;
+            sincosf(0.5f * gp[j], &sh, &ch);
+            const float2 v = make_float2(2.f * sh * ch, 2.f * sh * sh);
+            if (j == 5) sc[SC_ROT + 2] = v;
+            else sc[j - 6] = v;
+        }
+    }
+    __syncthreads();
+    const float2 sphi = sc[SC_ROT], sth = sc[SC_ROT + 1], sal = sc[SC_ROT + 2];
+    const float3 u = make_float3(sth.x * sphi.y, sth.x * sphi.x, sth.y);
+    const float s = sal.x, o = sal.y;
+    const float m00 = o * (u.x * u.x - 1.f), m11 = o * (u.y * u.y - 1.f), m22 = o * (u.z * u.z - 1.f);
+    const float m01 = o * u.x * u.y - s * u.z, m10 = o * u.x * u.y + s * u.z;
+    const float m02 = o * u.x * u.z + s * u.y, m20 = o * u.x * u.z - s * u.y;
+    const float m12 = o * u.y * u.z - s * u.x, m21 = o * u.y * u.z + s * u.x;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const float4 r4 = lig.ref[i];
+        float3 p = make_float3(r4.x, r4.y, r4.z);
+        for (int k = lig.frag[i]; k >= 0; k = lig.tparent[k])
+            rotate_about(p, lig.taxis[k], lig.tbref[k], sc[k]);
+        float *o3 = out + ((size_t)pose * N + lig.perm[i]) * 3;
+        o3[0] = p.x + (m00 * p.x + m01 * p.y + m02 * p.z) + gp[0];
+        o3[1] = p.y + (m10 * p.x + m11 * p.y + m12 * p.z) + gp[1];
+        o3[2] = p.z + (m20 * p.x + m21 * p.y + m22 * p.z) + gp[2];
+    }
+}
+
+cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    coords_kernel<<<n, 128, 0, s>>>(lig, genes, n, xyz);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- grid packing
+// cells[cell][m][c] <- maps[m][z+cz][y+cy][x+cx], c = cx + 2 cy + 4 cz.
+__global__ void pack_grid_kernel(const float *maps, int nx, int ny, int nz, int M,
+                                 float *cells) {
+    const long ncell = (long)(nx - 1) * (ny - 1) * (nz - 1);
+    const long total = ncell * M;
+    for (long w = blockIdx.x * (long)blockDim.x + threadIdx.x; w < total;
+         w += (long)gridDim.x * blockDim.x) {
+        const long cell = w / M;
+        const int m = (int)(w - cell * M);
+        const int ix = (int)(cell % (nx - 1));
+        const int iy = (int)((cell / (nx - 1)) % (ny - 1));
+        const int iz = (int)(cell / ((long)(nx - 1) * (ny - 1)));
+        const float *src = maps + (size_t)m * nx * ny * nz;
+        float v[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+            v[c] = src[((size_t)(iz + cz) * ny + (iy + cy)) * nx + (ix + cx)];
+        }
+        float4 *dst = reinterpret_cast<float4 *>(cells + (size_t)w * 8);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M, float *cells,
+                             cudaStream_t s) {
+    pack_grid_kernel<<<152 * 8, 256, 0, s>>>(maps, nx, ny, nz, M, cells);
+    return cudaGetLastError();
+}
+
+}  // namespace adgb
