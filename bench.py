@@ -177,12 +177,12 @@ def reference_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="adgb", choices=["adgb", "reference"])
     ap.add_argument("--variant", default="shfl")
     ap.add_argument("--ref-genotypes", type=int, default=400)
-    ap.add_argument("--cpu-genotypes", type=int, default=400)
+    ap.add_argument("--cpu-genotypes", type=int, default=3000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-variants", action="store_true")
     args = ap.parse_args()
@@ -227,14 +227,15 @@ def main():
         ev1.record(stream)
         return ev0, ev1
 
-    for i in range(args.warmup):
-        step(i, variant)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
     evs = []
     with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)                       # let the sampler start
+        for i in range(args.warmup):
+            step(i, variant)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.steps):
             evs.append(step(args.warmup + i, variant))

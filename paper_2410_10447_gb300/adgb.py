@@ -268,7 +268,9 @@ class Context:
         e = np.zeros(n, np.float32)
         st = None
         if resume or want_state:
-            st = _f32(state) if state is not None else np.zeros((n, 3, G), np.float32)
+            # the C call overwrites the state in place: work on a copy
+            st = (np.array(state, dtype=np.float32, order="C", copy=True) if state is not None
+                  else np.zeros((n, 3, G), np.float32))
         p = _LSParams(int(iters), float(rho), float(eps), int(variant), LS_RESUME if resume else 0)
         self._chk(self.lib.local_search(self.h, rid, lid, g.ctypes.data, n, C.byref(p), e.ctypes.data,
                                         _ptr(st)))

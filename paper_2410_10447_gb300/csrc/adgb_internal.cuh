@@ -43,21 +43,24 @@ struct LigDev {
     const uint32_t *pairs;    // [Np] i | j << 8 | (ti*16+tj) << 16 | hb << 24
     const float2 *tptab;      // [256] (A, B): E = A r^-12 - B r^-m, m = 10 if hb else 6
     const int *perm;          // [N] internal index -> caller's index
+    const int *inc_off;       // [N+1] incidence list of atom i: inc[inc_off[i] .. inc_off[i+1])
+    const uint16_t *inc;      // [2 Np] (pair index << 1) | (atom is the pair's second atom), ascending
 };
 
 // Shared-memory layout of one block of the scoring / local-search kernel:
 // per-ligand constants once, then per-pose working arrays.  All offsets in
 // bytes, 16-byte aligned.
 struct SmemLayout {
-    int ref, sv, type, frag, tparent, tatoms, taxis, tbref, tptab;
+    int ref, sv, type, frag, tparent, tatoms, taxis, tbref, tptab, incoff;
     int pose0, pose_stride;          // first pose block, bytes per pose
     // offsets inside one pose block
-    int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage;
+    int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage, p_force;
+    int chunk;                       // pairs per force-buffer chunk
     int total;
 
     static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-    __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose) {
+    __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose, int ch) {
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
         sv = o;      o = al16(o + 8 * N);
@@ -68,6 +71,7 @@ struct SmemLayout {
         taxis = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tbref = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tptab = o;   o = al16(o + 8 * TYPE_TAB);
+        incoff = o;  o = al16(o + 4 * (N + 1));
         pose0 = o;
         int q = 0;
         p_xyz = q;   q = al16(q + 16 * N);
@@ -77,6 +81,8 @@ struct SmemLayout {
         p_sc = q;    q = al16(q + 8 * (ADGB_MAX_TORS + 4));
         p_red = q;   q = al16(q + 4 * 8 * warps_per_pose);
         p_stage = q; q = al16(q + 4 * 32 * 12 * warps_per_pose);
+        chunk = ch > 0 ? ch : 1;
+        p_force = q; q = al16(q + 16 * chunk);
         pose_stride = q;
         total = pose0 + ppb * pose_stride;
     }
@@ -84,9 +90,10 @@ struct SmemLayout {
 
 // Launch configuration of the fused kernel.
 struct EvalCfg {
-    int tpp;        // threads per pose (32, 64, 128, 256)
+    int tpp;        // threads per pose (32, 64, 128)
     int ppb;        // poses per block
     int variant;    // ADGB_REDUCE_*
+    int chunk;      // pairs per force-buffer chunk
 };
 
 // Host-side launchers (eval.cu, reduce_bench.cu).

@@ -26,7 +26,7 @@ struct Receptor {
 struct Ligand {
     LigDev dev;
     void *mem = nullptr;
-    int n_atoms = 0, n_tors = 0, n_types = 0, max_type = 0;
+    int n_atoms = 0, n_tors = 0, n_types = 0, n_pairs = 0, max_type = 0;
 };
 
 }  // namespace
@@ -129,6 +129,8 @@ struct HostLigand {
     std::vector<float4> taxis, tbref;
     std::vector<uint32_t> pairs;
     std::vector<float2> tptab;
+    std::vector<int> inc_off;
+    std::vector<uint16_t> inc;
     int max_type = 0;
 };
 
@@ -138,7 +140,9 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
     if (N < 1 || N > ADGB_MAX_ATOMS) return ferr(err, ADGB_EINVAL, "ligand: n_atoms %d not in 1..%d", N, ADGB_MAX_ATOMS);
     if (NT < 1 || NT > ADGB_MAX_TYPES) return ferr(err, ADGB_EINVAL, "ligand: n_types %d not in 1..%d", NT, ADGB_MAX_TYPES);
     if (T < 0 || T > ADGB_MAX_TORS) return ferr(err, ADGB_EINVAL, "ligand: n_tors %d not in 0..%d", T, ADGB_MAX_TORS);
-    if (NP < 0) return ferr(err, ADGB_EINVAL, "ligand: n_pairs %d < 0", NP);
+    if (NP < 0 || NP > ADGB_MAX_ATOMS * (ADGB_MAX_ATOMS - 1) / 2)
+        return ferr(err, ADGB_EINVAL, "ligand: n_pairs %d not in 0..%d", NP,
+                    ADGB_MAX_ATOMS * (ADGB_MAX_ATOMS - 1) / 2);
     if (!d->type || !d->charge || !d->xyz || !d->R || !d->eps || !d->vol || !d->solpar || !d->hb_role)
         return ferr(err, ADGB_EINVAL, "ligand: null per-atom or per-type array");
     if (T > 0 && (!d->tors_bond || !d->mov_off)) return ferr(err, ADGB_EINVAL, "ligand: null torsion arrays");
@@ -278,6 +282,21 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         h.pairs[p] = (uint32_t)inv[i] | (uint32_t)inv[j] << 8 |
                      (uint32_t)(ti * ADGB_MAX_TYPES + tj) << 16 | hb << 24;
     }
+    // incidence lists: for every atom the pairs it belongs to, ascending
+    h.inc_off.assign(N + 1, 0);
+    for (int p = 0; p < NP; p++) {
+        h.inc_off[(h.pairs[p] & 255) + 1]++;
+        h.inc_off[((h.pairs[p] >> 8) & 255) + 1]++;
+    }
+    for (int i = 0; i < N; i++) h.inc_off[i + 1] += h.inc_off[i];
+    h.inc.assign(2 * (size_t)NP, 0);
+    {
+        std::vector<int> fill(h.inc_off.begin(), h.inc_off.end() - 1);
+        for (int p = 0; p < NP; p++) {
+            h.inc[fill[h.pairs[p] & 255]++] = (uint16_t)(p << 1);
+            h.inc[fill[(h.pairs[p] >> 8) & 255]++] = (uint16_t)((p << 1) | 1);
+        }
+    }
     h.tptab.assign(TYPE_TAB, make_float2(0.f, 0.f));
     for (int ti = 0; ti < NT; ti++)
         for (int tj = 0; tj < NT; tj++) {
@@ -302,13 +321,18 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
 EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     EvalCfg cfg;
     cfg.variant = variant;
-    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 32;
+    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 64;
     int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 8;
     while (ppb > 1 && cfg.tpp * ppb > 256) ppb--;
+    // shared memory per block kept near 96 KB so that two blocks fit an SM;
+    // the pair-force buffer takes what the per-pose arrays leave
+    const int budget = 96 * 1024;
     SmemLayout lay;
-    for (; ppb > 1; ppb--) {
-        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32);
-        if (lay.total <= 110 * 1024) break;
+    for (;; ppb--) {
+        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, 1);
+        const int room = (budget - lay.total) / ppb / 16;
+        cfg.chunk = std::max(1, std::min(L.n_pairs, std::min(room, 4096)));
+        if (room >= 256 || room >= L.n_pairs || ppb == 1) break;
     }
     cfg.ppb = ppb;
     return cfg;
@@ -453,6 +477,7 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
     const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
     const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
+    const size_t o_incoff = take(4 * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
     std::vector<unsigned char> buf(off, 0);
     memcpy(&buf[o_ref], h.ref.data(), 16 * N);
     memcpy(&buf[o_sv], h.sv.data(), 8 * N);
@@ -467,6 +492,8 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
     memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
     memcpy(&buf[o_perm], h.perm.data(), 4 * N);
+    memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (N + 1));
+    if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
     unsigned char *mem = nullptr;
@@ -482,6 +509,7 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     L.n_atoms = N;
     L.n_tors = T;
     L.n_types = d->n_types;
+    L.n_pairs = NP;
     L.max_type = h.max_type;
     LigDev &v = L.dev;
     v.n_atoms = N;
@@ -499,6 +527,8 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     v.pairs = reinterpret_cast<const uint32_t *>(mem + o_pairs);
     v.tptab = reinterpret_cast<const float2 *>(mem + o_tab);
     v.perm = reinterpret_cast<const int *>(mem + o_perm);
+    v.inc_off = reinterpret_cast<const int *>(mem + o_incoff);
+    v.inc = reinterpret_cast<const uint16_t *>(mem + o_inc);
     const int id = c->next_id++;
     c->ligs[id] = L;
     *ligand_id = id;

@@ -10,8 +10,10 @@
 //   2. each thread builds its atoms' coordinates (torsions deepest-first
 //      about reference axes, then rotation, then translation) and their
 //      trilinear grid energy and gradient;
-//   3. threads stride over the pair list: four pair terms, forces added to
-//      both atoms in shared memory;
+//   3. threads stride over the pair list: four pair terms, each pair's force
+//      written to its own slot of a per-pose force buffer, then every atom's
+//      owner thread sums the forces of its pairs (no atomics; chunked when
+//      the pair list exceeds the buffer);
 //   4. per-thread partials of (E, sum g, torque) and the torsion gradients
 //      (each torsion's moving set is one contiguous atom range);
 //   5. one 8-wide reduce-and-broadcast (warp shuffles or tensor cores);
@@ -188,6 +190,8 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
     float4 *s_tax = reinterpret_cast<float4 *>(sm + a.L.taxis);
     float4 *s_tb = reinterpret_cast<float4 *>(sm + a.L.tbref);
     float2 *s_tab = reinterpret_cast<float2 *>(sm + a.L.tptab);
+    int *s_incoff = reinterpret_cast<int *>(sm + a.L.incoff);
+    for (int i = threadIdx.x; i <= N; i += blockDim.x) s_incoff[i] = lig.inc_off[i];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_ref[i] = lig.ref[i];
         s_sv[i] = lig.sv[i];
@@ -214,6 +218,9 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
     float2 *sc = reinterpret_cast<float2 *>(P + a.L.p_sc);
     float *red = reinterpret_cast<float *>(P + a.L.p_red);
     float *stage = reinterpret_cast<float *>(P + a.L.p_stage) + (gt >> 5) * 32 * 12;
+    float4 *fbuf = reinterpret_cast<float4 *>(P + a.L.p_force);
+    const int CH = a.L.chunk;
+    constexpr int MAXA = ADGB_MAX_ATOMS / TPP;  // atoms owned per thread, at most
 
     constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
     float om[NG], eg2[NG], ed2[NG], best[NG];
@@ -288,21 +295,52 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
         }
         group_sync<TPP>(group);
 
-        // 3. intramolecular pairs
-        for (int p = gt; p < NP; p += TPP) {
-            const uint32_t pr = __ldg(lig.pairs + p);
-            const int i = pr & 255, j = (pr >> 8) & 255;
-            float3 f;
-            e_part += pair_term(xyz[i], xyz[j], s_sv[i], s_sv[j], s_tab[(pr >> 16) & 255],
-                                (pr >> 24) & 1, f);
-            atomicAdd(&grd[i].x, f.x);
-            atomicAdd(&grd[i].y, f.y);
-            atomicAdd(&grd[i].z, f.z);
-            atomicAdd(&grd[j].x, -f.x);
-            atomicAdd(&grd[j].y, -f.y);
-            atomicAdd(&grd[j].z, -f.z);
+        // 3. intramolecular pairs, chunk by chunk: every pair's force goes to
+        //    its own slot of the force buffer, then each atom's owner adds the
+        //    forces of its pairs (incidence list, ascending pair index).  No
+        //    two threads ever write the same word.
+        int cur[MAXA];
+#pragma unroll
+        for (int m = 0; m < MAXA; m++) {
+            const int i = gt + m * TPP;
+            cur[m] = i < N ? s_incoff[i] : 0;
         }
-        group_sync<TPP>(group);
+        for (int c0 = 0; c0 < NP; c0 += CH) {
+            const int c1 = min(NP, c0 + CH);
+            for (int p = c0 + gt; p < c1; p += TPP) {
+                const uint32_t pr = __ldg(lig.pairs + p);
+                const int i = pr & 255, j = (pr >> 8) & 255;
+                float3 f;
+                e_part += pair_term(xyz[i], xyz[j], s_sv[i], s_sv[j], s_tab[(pr >> 16) & 255],
+                                    (pr >> 24) & 1, f);
+                fbuf[p - c0] = make_float4(f.x, f.y, f.z, 0.f);
+            }
+            group_sync<TPP>(group);
+#pragma unroll
+            for (int m = 0; m < MAXA; m++) {
+                const int i = gt + m * TPP;
+                if (i < N) {
+                    const int end = s_incoff[i + 1];
+                    int c = cur[m];
+                    float ax = 0.f, ay = 0.f, az = 0.f;
+                    for (; c < end; c++) {
+                        const uint32_t e = __ldg(lig.inc + c);
+                        const int p = (int)(e >> 1);
+                        if (p >= c1) break;
+                        const float4 f = fbuf[p - c0];
+                        const float sg = (e & 1) ? -1.f : 1.f;
+                        ax += sg * f.x;
+                        ay += sg * f.y;
+                        az += sg * f.z;
+                    }
+                    cur[m] = c;
+                    float4 g = grd[i];
+                    grd[i] = make_float4(g.x + ax, g.y + ay, g.z + az, 0.f);
+                }
+            }
+            group_sync<TPP>(group);
+        }
+        if (NP == 0) group_sync<TPP>(group);
 
         // 4. partial sums of (E, sum g, torque about the centre); torsion gradients
         float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -436,7 +474,7 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     EvalArgs a;
     a.rec = rec;
     a.lig = lig;
-    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32);
+    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk);
     a.genes_in = genes_in;
     a.genes_out = genes_out;
     a.energy = energy;
