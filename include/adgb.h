@@ -75,8 +75,8 @@ enum {
 #define ADGB_W_OUT 10.0f     /* out-of-grid penalty (kcal/mol/A^2) */
 
 typedef struct {
-    int threads_per_pose;  /* 0 = pick per ligand; else 32, 64, 128 or 256 */
-    int poses_per_block;   /* 0 = pick per ligand; else 1..8 */
+    int threads_per_pose;  /* 0 = pick per ligand; else 32, 64 or 128 */
+    int poses_per_block;   /* 0 = pick per ligand; else 1..8 (at most 128 threads a block) */
     int reduce_variant;    /* default ADGB_REDUCE_* for calls that do not say */
 } adgb_options;
 

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/adgb.h"
+#include "adgb.h"  // include/ is on the include path
 
 namespace adgb {
 
@@ -52,6 +52,7 @@ struct LigDev {
 // bytes, 16-byte aligned.
 struct SmemLayout {
     int ref, sv, type, frag, tparent, tatoms, taxis, tbref, tptab, incoff;
+    int spairs, sinc, pairs_in_smem;   // optional copies of the pair list and incidence lists
     int pose0, pose_stride;          // first pose block, bytes per pose
     // offsets inside one pose block
     int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage, p_force;
@@ -60,7 +61,8 @@ struct SmemLayout {
 
     static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
-    __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose, int ch) {
+    __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose, int ch,
+                                         int np = 0, bool stage_pairs = false) {
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
         sv = o;      o = al16(o + 8 * N);
@@ -72,6 +74,9 @@ struct SmemLayout {
         tbref = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tptab = o;   o = al16(o + 8 * TYPE_TAB);
         incoff = o;  o = al16(o + 4 * (N + 1));
+        pairs_in_smem = stage_pairs ? 1 : 0;
+        spairs = o;  if (stage_pairs) o = al16(o + 4 * np);
+        sinc = o;    if (stage_pairs) o = al16(o + 4 * np);
         pose0 = o;
         int q = 0;
         p_xyz = q;   q = al16(q + 16 * N);
@@ -94,6 +99,7 @@ struct EvalCfg {
     int ppb;        // poses per block
     int variant;    // ADGB_REDUCE_*
     int chunk;      // pairs per force-buffer chunk
+    int stage_pairs;  // copy the pair list and incidence lists to shared memory
 };
 
 // Host-side launchers (eval.cu, reduce_bench.cu).

@@ -321,15 +321,18 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
 EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     EvalCfg cfg;
     cfg.variant = variant;
-    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 64;
-    int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 8;
-    while (ppb > 1 && cfg.tpp * ppb > 256) ppb--;
-    // shared memory per block kept near 96 KB so that two blocks fit an SM;
-    // the pair-force buffer takes what the per-pose arrays leave
-    const int budget = 96 * 1024;
+    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 32;
+    int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
+    while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;
+    // the pair list (4 B a pair) and incidence lists (4 B a pair) are copied
+    // to shared memory when they take at most 24 KB
+    cfg.stage_pairs = 8 * L.n_pairs <= 24 * 1024;
+    // shared memory per block kept near 48 KB so that four 128-thread blocks
+    // fit an SM; the pair-force buffer takes what the per-pose arrays leave
+    const int budget = 48 * 1024;
     SmemLayout lay;
     for (;; ppb--) {
-        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, 1);
+        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, 1, L.n_pairs, cfg.stage_pairs);
         const int room = (budget - lay.total) / ppb / 16;
         cfg.chunk = std::max(1, std::min(L.n_pairs, std::min(room, 4096)));
         if (room >= 256 || room >= L.n_pairs || ppb == 1) break;

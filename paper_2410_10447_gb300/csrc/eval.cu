@@ -140,13 +140,16 @@ __device__ __forceinline__ float pair_term(float4 xi, float4 xj, float2 svi, flo
     const float m = hb ? 10.f : 6.f;
     const float evdw = ab.x * r12i - ab.y * rmi;
     const float dvdw = (-12.f * ab.x * r12i + m * ab.y * rmi) * rinv;
+    // eps(r) = num / den with den = 1 + k e^{-lambda B r}, num = A den + B;
+    // 1/eps = den^2 r and eps'/eps = B k lambda B e^{..} r with r = 1/(den num):
+    // one reciprocal for the whole dielectric.
     const float C = KQQ * xi.w * xj.w;
     const float ex = __expf(-MS_LAMBDA * MS_B * rc);
-    const float iden = __fdividef(1.f, 1.f + MS_K * ex);
-    const float epsr = MS_A + MS_B * iden;
-    const float deps = (MS_B * MS_K * MS_LAMBDA * MS_B) * ex * iden * iden;
-    const float eel = __fdividef(C * rinv, epsr);
-    const float del = -eel * (rinv + __fdividef(deps, epsr));
+    const float den = 1.f + MS_K * ex;
+    const float num = MS_A * den + MS_B;
+    const float rr = __fdividef(1.f, den * num);
+    const float eel = C * rinv * (den * den * rr);
+    const float del = -eel * (rinv + (MS_B * MS_K * MS_LAMBDA * MS_B) * ex * rr);
     const float eds = (svi.x * svj.y + svj.x * svi.y) * __expf(-r2 * HALF_INV_SIG2);
     const float fr = live ? (dvdw + del) * rinv : 0.f;
     const float fd = -eds * INV_SIG2;
@@ -175,8 +178,15 @@ __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage,
     }
 }
 
+// Blocks of at most 128 threads; ADGB_MIN_BLOCKS resident blocks per SM
+// bound the registers (5 -> 96 registers a thread, no spills; 3000
+// one-warp genotypes then run in a single wave of 20 warps an SM).
+#ifndef ADGB_MIN_BLOCKS
+#define ADGB_MIN_BLOCKS 5
+#endif
+
 template <int TPP, int VAR>
-__global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
+__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
     extern __shared__ __align__(16) unsigned char sm[];
     const LigDev &lig = a.lig;
     const RecDev &rec = a.rec;
@@ -192,6 +202,17 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
     float2 *s_tab = reinterpret_cast<float2 *>(sm + a.L.tptab);
     int *s_incoff = reinterpret_cast<int *>(sm + a.L.incoff);
     for (int i = threadIdx.x; i <= N; i += blockDim.x) s_incoff[i] = lig.inc_off[i];
+    // pair records and incidence lists: shared memory when they fit
+    const uint32_t *prs = lig.pairs;
+    const uint16_t *incl = lig.inc;
+    if (a.L.pairs_in_smem) {
+        uint32_t *sp = reinterpret_cast<uint32_t *>(sm + a.L.spairs);
+        uint16_t *si = reinterpret_cast<uint16_t *>(sm + a.L.sinc);
+        for (int p = threadIdx.x; p < NP; p += blockDim.x) sp[p] = lig.pairs[p];
+        for (int p = threadIdx.x; p < 2 * NP; p += blockDim.x) si[p] = lig.inc[p];
+        prs = sp;
+        incl = si;
+    }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_ref[i] = lig.ref[i];
         s_sv[i] = lig.sv[i];
@@ -245,24 +266,22 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
 
     for (int it = 0; it < iters; it++) {
         // 1. publish genes, sin and 1 - cos of every angle (half-angle form:
-        //    sin = 2 sh ch, 1 - cos = 2 sh^2, exact zero at a zero angle)
+        //    sin = 2 sh ch, 1 - cos = 2 sh^2, exact zero at a zero angle).  phi
+        //    and theta are published as (sin, cos) of the full angle.  One
+        //    sincosf per gene on every lane keeps the lanes converged.
 #pragma unroll
         for (int r = 0; r < NG; r++) {
             const int j = gt + r * TPP;
-            if (j < G) {
-                genes_s[j] = om[r];
-                if (j >= 3) {
-                    if (j == 3 || j == 4) {
-                        float s, c;
-                        sincosf(om[r], &s, &c);
-                        sc[SC_ROT + j - 3] = make_float2(s, c);
-                    } else {
-                        float sh, ch;
-                        sincosf(0.5f * om[r], &sh, &ch);
-                        const float2 v = make_float2(2.f * sh * ch, 2.f * sh * sh);
-                        if (j == 5) sc[SC_ROT + 2] = v;
-                        else sc[j - 6] = v;
-                    }
+            if (r * TPP < G) {
+                const bool full = j == 3 || j == 4;
+                float sh, ch;
+                sincosf(full ? om[r] : 0.5f * om[r], &sh, &ch);
+                if (j < G) {
+                    genes_s[j] = om[r];
+                    const float2 v = full ? make_float2(sh, ch)
+                                          : make_float2(2.f * sh * ch, 2.f * sh * sh);
+                    if (j >= 6) sc[j - 6] = v;
+                    else if (j >= 3) sc[SC_ROT + j - 3] = v;
                 }
             }
         }
@@ -308,7 +327,7 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
         for (int c0 = 0; c0 < NP; c0 += CH) {
             const int c1 = min(NP, c0 + CH);
             for (int p = c0 + gt; p < c1; p += TPP) {
-                const uint32_t pr = __ldg(lig.pairs + p);
+                const uint32_t pr = prs[p];
                 const int i = pr & 255, j = (pr >> 8) & 255;
                 float3 f;
                 e_part += pair_term(xyz[i], xyz[j], s_sv[i], s_sv[j], s_tab[(pr >> 16) & 255],
@@ -323,15 +342,28 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
                     const int end = s_incoff[i + 1];
                     int c = cur[m];
                     float ax = 0.f, ay = 0.f, az = 0.f;
-                    for (; c < end; c++) {
-                        const uint32_t e = __ldg(lig.inc + c);
-                        const int p = (int)(e >> 1);
-                        if (p >= c1) break;
-                        const float4 f = fbuf[p - c0];
-                        const float sg = (e & 1) ? -1.f : 1.f;
-                        ax += sg * f.x;
-                        ay += sg * f.y;
-                        az += sg * f.z;
+                    if (c1 == NP && c0 == 0) {
+                        // the whole list is in this chunk: no bound test
+#pragma unroll 4
+                        for (; c < end; c++) {
+                            const uint32_t e = incl[c];
+                            const float4 f = fbuf[e >> 1];
+                            const float sg = (e & 1) ? -1.f : 1.f;
+                            ax += sg * f.x;
+                            ay += sg * f.y;
+                            az += sg * f.z;
+                        }
+                    } else {
+                        for (; c < end; c++) {
+                            const uint32_t e = incl[c];
+                            const int p = (int)(e >> 1);
+                            if (p >= c1) break;
+                            const float4 f = fbuf[p - c0];
+                            const float sg = (e & 1) ? -1.f : 1.f;
+                            ax += sg * f.x;
+                            ay += sg * f.y;
+                            az += sg * f.z;
+                        }
                     }
                     cur[m] = c;
                     float4 g = grd[i];
@@ -354,6 +386,50 @@ __global__ void __launch_bounds__(256) eval_kernel(const EvalArgs a) {
             v[5] += d.z * g.x - d.x * g.z;
             v[6] += d.x * g.y - d.y * g.x;
         }
+        if (N <= 32) {
+            // one atom per lane of the group's first warp; atoms are in
+            // depth-first order, so a torsion's moving set [s, e) sums to
+            // P[e-1] - P[s-1] of the inclusive prefix P of (g, (x - t) x g).
+            if (gt < 32) {
+                float w[6] = {v[1], v[2], v[3], v[4], v[5], v[6]};
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        const float y = __shfl_up_sync(0xffffffffu, w[c], off);
+                        if (gt >= off) w[c] += y;
+                    }
+                }
+                for (int k0 = 0; k0 < T; k0 += 32) {
+                    const int k = k0 + gt;
+                    const int4 ta = k < T ? s_tat[k] : make_int4(0, 0, 0, 0);
+                    const int hi = max(ta.w - 1, 0), lo = max(ta.z - 1, 0);
+                    float sm6[6];
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        const float ph = __shfl_sync(0xffffffffu, w[c], hi);
+                        const float pl = __shfl_sync(0xffffffffu, w[c], lo);
+                        sm6[c] = ph - (ta.z > 0 ? pl : 0.f);
+                    }
+                    if (k < T) {
+                        float gk = 0.f;
+                        if (ta.w > ta.z) {
+                            const float4 xa = xyz[ta.x], xb = xyz[ta.y];
+                            const float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
+                            const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
+                            // sum (x - x_b) x g = sum (x - t) x g - (x_b - t) x sum g
+                            const float3 bt = make_float3(xb.x - tr.x, xb.y - tr.y, xb.z - tr.z);
+                            const float3 acc = make_float3(
+                                sm6[3] - (bt.y * sm6[2] - bt.z * sm6[1]),
+                                sm6[4] - (bt.z * sm6[0] - bt.x * sm6[2]),
+                                sm6[5] - (bt.x * sm6[1] - bt.y * sm6[0]));
+                            gk = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
+                        }
+                        ggrad[6 + k] = gk;
+                    }
+                }
+            }
+        } else
         for (int k = gt; k < T; k += TPP) {
             const int4 ta = s_tat[k];
             const float4 xa = xyz[ta.x], xb = xyz[ta.y];
@@ -474,7 +550,8 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     EvalArgs a;
     a.rec = rec;
     a.lig = lig;
-    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk);
+    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk, lig.n_pairs,
+             cfg.stage_pairs != 0);
     a.genes_in = genes_in;
     a.genes_out = genes_out;
     a.energy = energy;

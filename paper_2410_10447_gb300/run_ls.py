@@ -1,0 +1,72 @@
+"""Times local-search launches on a named synthetic workload.
+
+    python -m paper_2410_10447_gb300.run_ls [--workload lga_n32] [--iters 300]
+        [--n 0] [--cfgs 32:4,64:2] [--variants 0,1,2] [--reps 3]
+
+For every launch shape "threads_per_pose:poses_per_block" and reduction
+variant it runs one warm-up launch and `reps` timed launches (CUDA events)
+and prints the best time and evaluations/s.  Used for launch-shape sweeps
+and as the target of ncu captures (one launch per repetition).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    import torch
+
+    import paper_2410_10447_gb300 as P
+    import synth
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="lga_n32")
+    ap.add_argument("--iters", type=int, default=300)
+    ap.add_argument("--n", type=int, default=0, help="genotypes (0 = the workload's own)")
+    ap.add_argument("--cfgs", default="32:4")
+    ap.add_argument("--variants", default="0")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    P.load(build=True)
+    w = synth.workload(a.workload, n_poses=a.n or None)
+    g0 = torch.from_numpy(w["genes"]).cuda()
+    n = g0.shape[0]
+    res = {}
+    for cfg in a.cfgs.split(","):
+        tpp, ppb = map(int, cfg.split(":"))
+        ctx = P.Context(0, threads_per_pose=tpp, poses_per_block=ppb)
+        rid = ctx.upload_receptor_grids(w["receptor"])
+        lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+        for v in map(int, a.variants.split(",")):
+            best = torch.empty(n, device="cuda")
+            g = torch.empty_like(g0)
+            ms = []
+            for _ in range(a.reps + 1):
+                g.copy_(g0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.local_search_dev(rid, lid, g, best, a.iters, variant=v)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = min(ms[1:]) if a.reps else ms[0]
+            key = "%d:%d:v%d" % (tpp, ppb, v)
+            res[key] = dict(ms=t, evals_per_s=n * a.iters / t * 1e3,
+                            median_best=float(best.median()))
+            print("%s tpp=%d ppb=%d variant=%d: %.3f ms  %.1f M evals/s  median best %.3f"
+                  % (a.workload, tpp, ppb, v, t, n * a.iters / t / 1e3, float(best.median())),
+                  flush=True)
+        ctx.close()
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
