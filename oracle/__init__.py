@@ -203,6 +203,67 @@ def score_batch(rec, lig, genes, nthreads=0):
     return e, gg
 
 
+class DockParams(C.Structure):
+    _fields_ = [("n_runs", C.c_int), ("pop", C.c_int), ("max_gens", C.c_int),
+                ("max_evals", C.c_longlong), ("ls_iters", C.c_int), ("ls_rate", C.c_double),
+                ("rho", C.c_double), ("eps", C.c_double), ("p_cross", C.c_double),
+                ("p_mut", C.c_double), ("mut_trans", C.c_double), ("mut_angle", C.c_double),
+                ("seed", C.c_ulonglong)]
+
+
+DOCK_DEFAULTS = dict(n_runs=1, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
+                     ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
+                     mut_angle=np.pi / 2, seed=2410)
+
+
+def dock_params(**kw) -> DockParams:
+    d = dict(DOCK_DEFAULTS)
+    d.update(kw)
+    return DockParams(*[d[f] for f, _ in DockParams._fields_])
+
+
+def philox(ctr, key):
+    """Philox4x32-10 of one 128-bit counter and 64-bit key (4 words)."""
+    c = (C.c_uint * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (C.c_uint * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (C.c_uint * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return list(o)
+
+
+def init_individual(rec, n_tors, seed, run, k):
+    R = _rec(rec)
+    g = np.zeros(6 + n_tors)
+    lib().orc_init_individual(C.byref(R.c), C.c_int(n_tors), C.c_ulonglong(seed), C.c_int(run),
+                              C.c_int(k), _pd(g))
+    return g
+
+
+def ga_generation(genes, energies, params: DockParams, run, gen):
+    """(new genes [pop][G], local-search flags [pop]) of one GA generation."""
+    g = _d(genes)
+    pop, G = g.shape
+    e = _d(energies)
+    out = np.zeros_like(g)
+    fl = np.zeros(pop, np.int32)
+    lib().orc_ga_generation(C.c_int(G), C.c_int(pop), _pd(g), _pd(e), C.byref(params),
+                            C.c_int(run), C.c_int(gen), _pd(out), _pi(fl))
+    return out, fl
+
+
+def dock(rec, lig, params: DockParams, nthreads=0):
+    """(best genes [runs][G], best energies [runs], evaluations [runs])."""
+    R, L = _rec(rec), _lig(lig)
+    bg = np.zeros((params.n_runs, L.G))
+    be = np.zeros(params.n_runs)
+    ev = np.zeros(params.n_runs, np.int64)
+    rc = lib().orc_dock(C.byref(R.c), C.byref(L.c), C.byref(params), _pd(bg), _pd(be),
+                        ev.ctypes.data_as(C.POINTER(C.c_longlong)), C.c_int(nthreads))
+    if rc:
+        raise ValueError("orc_dock failed")
+    return bg, be, ev
+
+
 def sum_naive(x) -> float:
     x = _d(x).reshape(-1)
     return lib().orc_sum_naive(_pd(x), len(x), 1)

@@ -31,6 +31,7 @@
 #include "adgb_oracle.h"
 
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -465,4 +466,171 @@ double orc_sum_neumaier(const double *x, long n, long stride) {
         s = t;
     }
     return s + c;
+}
+
+/* ------------------------------------------------------------------------
+ * Lamarckian GA (Sec. 2.1: a GA does the global search and every genotype it
+ * produces is refined by the local search).  The paper prints none of the
+ * GA's rules; this is the project's reading, written once here and once,
+ * independently, in the CUDA library:
+ *  - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed, counter
+ *    = (individual, generation, run, call); each call yields four 32-bit
+ *    words, consumed in a fixed order; u(x) = (x >> 8) * 2^-24 in [0,1);
+ *    an index below n is (x * n) >> 32;
+ *  - initial genotype: translation uniform in the central 60% of the grid
+ *    box, axis angles phi = 2 pi u - pi, theta = acos(1 - 2u), angle
+ *    alpha = 2 pi u, torsions 2 pi u - pi;
+ *  - new generation: individual 0 is the previous generation's best
+ *    (elitism); every other child takes two binary tournaments (the lower
+ *    energy wins, ties to the lower index), two-point crossover with
+ *    probability p_cross (cut points c1 <= c2 drawn in 0..G, genes
+ *    [c1, c2) from the second parent), then each gene mutates with
+ *    probability p_mut by a uniform offset in [-1, 1) times mut_trans (A)
+ *    or mut_angle (rad); torsion genes are wrapped to [-pi, pi);
+ *  - each individual is locally searched with probability ls_rate
+ *    (ls_iters evaluations), otherwise scored once (one evaluation);
+ *  - a run stops after max_gens generations or once its evaluations reach
+ *    max_evals; its result is the lowest energy ever seen.
+ * ------------------------------------------------------------------------ */
+
+static uint32_t mulhilo32(uint32_t a, uint32_t b, uint32_t *hi) {
+    uint64_t p = (uint64_t)a * (uint64_t)b;
+    *hi = (uint32_t)(p >> 32);
+    return (uint32_t)p;
+}
+
+/* Philox4x32 with 10 rounds: each round multiplies words 0 and 2 by the
+ * two round multipliers, mixes the high halves with the other words and
+ * the key, and the key is bumped by the two Weyl constants between rounds. */
+void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0, hi1;
+        uint32_t lo0 = mulhilo32(0xD2511F53u, c0, &hi0);
+        uint32_t lo1 = mulhilo32(0xCD9E8D57u, c2, &hi1);
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0;
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+/* word w of the stream (individual k, generation gen, run) */
+static uint32_t draw(unsigned long long seed, int run, int gen, int k, int w) {
+    unsigned int ctr[4] = {(unsigned)k, (unsigned)gen, (unsigned)run, (unsigned)(w / 4)};
+    unsigned int key[2] = {(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)};
+    unsigned int out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[w % 4];
+}
+
+static double u01(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
+static int below(uint32_t x, int n) { return (int)(((uint64_t)x * (uint64_t)n) >> 32); }
+
+#define INIT_GEN 0xFFFFFFFF
+
+int orc_init_individual(const orc_receptor *R, int n_tors, unsigned long long seed, int run,
+                        int k, double *genes) {
+    const int n[3] = {R->nx, R->ny, R->nz};
+    for (int d = 0; d < 3; d++) {
+        double ext = (n[d] - 1) * R->spacing;
+        genes[d] = R->origin[d] + ext * (0.2 + 0.6 * u01(draw(seed, run, (int)INIT_GEN, k, d)));
+    }
+    genes[3] = 2.0 * PI * u01(draw(seed, run, (int)INIT_GEN, k, 3)) - PI;
+    genes[4] = acos(1.0 - 2.0 * u01(draw(seed, run, (int)INIT_GEN, k, 4)));
+    genes[5] = 2.0 * PI * u01(draw(seed, run, (int)INIT_GEN, k, 5));
+    for (int j = 0; j < n_tors; j++)
+        genes[6 + j] = 2.0 * PI * u01(draw(seed, run, (int)INIT_GEN, k, 6 + j)) - PI;
+    return 0;
+}
+
+/* words of child k: 0-3 tournaments, 4 crossover?, 5-6 cuts, 7 local search?,
+ * 8 + 2j mutate gene j?, 9 + 2j its offset */
+int orc_ga_generation(int G, int pop, const double *go, const double *eo,
+                      const orc_dock_params *p, int run, int gen, double *gn, int *ls_flag) {
+    int best = 0;
+    for (int k = 1; k < pop; k++)
+        if (eo[k] < eo[best]) best = k;
+    for (int k = 0; k < pop; k++) {
+        double *child = gn + (size_t)k * G;
+        if (k == 0) {
+            memcpy(child, go + (size_t)best * G, sizeof(double) * G);
+        } else {
+            int par[2];
+            for (int t = 0; t < 2; t++) {
+                int a = below(draw(p->seed, run, gen, k, 2 * t), pop);
+                int b = below(draw(p->seed, run, gen, k, 2 * t + 1), pop);
+                par[t] = (eo[b] < eo[a] || (eo[b] == eo[a] && b < a)) ? b : a;
+            }
+            const double *A = go + (size_t)par[0] * G, *B = go + (size_t)par[1] * G;
+            int c1 = 0, c2 = 0;
+            if (u01(draw(p->seed, run, gen, k, 4)) < p->p_cross) {
+                c1 = below(draw(p->seed, run, gen, k, 5), G + 1);
+                c2 = below(draw(p->seed, run, gen, k, 6), G + 1);
+                if (c1 > c2) { int t = c1; c1 = c2; c2 = t; }
+            }
+            for (int j = 0; j < G; j++) child[j] = (j >= c1 && j < c2) ? B[j] : A[j];
+            for (int j = 0; j < G; j++) {
+                if (u01(draw(p->seed, run, gen, k, 8 + 2 * j)) < p->p_mut) {
+                    double off = 2.0 * u01(draw(p->seed, run, gen, k, 9 + 2 * j)) - 1.0;
+                    child[j] += off * (j < 3 ? p->mut_trans : p->mut_angle);
+                }
+                if (j >= 6) child[j] = wrap_angle(child[j]);
+            }
+        }
+        ls_flag[k] = u01(draw(p->seed, run, gen, k, 7)) < p->ls_rate;
+    }
+    return 0;
+}
+
+/* Whole Lamarckian GA of every run (Sec. 2.1); slow, for small cases. */
+int orc_dock(const orc_receptor *R, const orc_ligand *L, const orc_dock_params *p,
+             double *best_genes, double *best_energy, long long *evals, int nthreads) {
+    const int G = 6 + L->n_tors, P = p->pop;
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+#endif
+    for (int r = 0; r < p->n_runs; r++) {
+        double *ga = (double *)malloc(sizeof(double) * (size_t)P * G);
+        double *gb = (double *)malloc(sizeof(double) * (size_t)P * G);
+        double *e = (double *)malloc(sizeof(double) * (size_t)P);
+        int *fl = (int *)malloc(sizeof(int) * (size_t)P);
+        double *bg = best_genes + (size_t)r * G;
+        double be = INFINITY;
+        long long ev = 0;
+        for (int k = 0; k < P; k++) {
+            orc_init_individual(R, L->n_tors, p->seed, r, k, ga + (size_t)k * G);
+            bad |= orc_score(R, L, ga + (size_t)k * G, e + k, NULL, NULL, NULL) != 0;
+            ev++;
+            if (e[k] < be) { be = e[k]; memcpy(bg, ga + (size_t)k * G, sizeof(double) * G); }
+        }
+        for (int gen = 1; gen <= p->max_gens && ev < p->max_evals; gen++) {
+            orc_ga_generation(G, P, ga, e, p, r, gen, gb, fl);
+            for (int k = 0; k < P; k++) {
+                double *gk = gb + (size_t)k * G;
+                int it = fl[k] ? p->ls_iters : 1;
+                bad |= orc_local_search(R, L, gk, it, p->rho, p->eps, 0, NULL, e + k) != 0;
+                ev += it;
+                if (e[k] < be) { be = e[k]; memcpy(bg, gk, sizeof(double) * G); }
+            }
+            double *t = ga; ga = gb; gb = t;
+        }
+        best_energy[r] = be;
+        if (evals) evals[r] = ev;
+        free(ga); free(gb); free(e); free(fl);
+    }
+    (void)nthreads;
+    return bad ? -1 : 0;
 }

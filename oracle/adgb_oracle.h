@@ -69,6 +69,24 @@ int orc_local_search_batch(const orc_receptor *R, const orc_ligand *L, int n,
 int orc_score_batch(const orc_receptor *R, const orc_ligand *L, int n,
                     const double *genes, double *energy, double *gene_grad,
                     int nthreads);
+/* Lamarckian GA (Sec. 2.1; rules are this project's reading, see adgb_oracle.c) */
+typedef struct {
+    int n_runs, pop, max_gens;
+    long long max_evals;     /* per run */
+    int ls_iters;
+    double ls_rate, rho, eps;
+    double p_cross, p_mut, mut_trans, mut_angle;
+    unsigned long long seed;
+} orc_dock_params;
+
+void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);
+int orc_init_individual(const orc_receptor *R, int n_tors, unsigned long long seed, int run,
+                        int k, double *genes);
+int orc_ga_generation(int G, int pop, const double *genes_old, const double *energy_old,
+                      const orc_dock_params *p, int run, int gen, double *genes_new,
+                      int *ls_flag);
+int orc_dock(const orc_receptor *R, const orc_ligand *L, const orc_dock_params *p,
+             double *best_genes, double *best_energy, long long *evals, int nthreads);
 double orc_sum_naive(const double *x, long n, long stride);
 double orc_sum_neumaier(const double *x, long n, long stride);
 
