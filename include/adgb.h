@@ -203,6 +203,74 @@ int local_search_dev(adgb_ctx *ctx, int receptor_id, int ligand_id,
 int local_search(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes,
                  int n, const adgb_ls_params *p, float *best_energy, float *state);
 
+/* Lamarckian GA docking parameters (Sec. 2.1: a GA proposes genotypes and
+ * each is refined by the local search).  The paper prints no GA rules; the
+ * library's rules: individual 0 of a generation is the previous best; every
+ * other child comes from two binary tournaments, two-point crossover with
+ * probability p_cross, per-gene mutation with probability p_mut by a
+ * uniform offset in [-1, 1) times mut_trans (translation genes, A) or
+ * mut_angle (angle genes, rad); each individual is locally searched
+ * (ls_iters evaluations) with probability ls_rate, else scored once.
+ * Random numbers: Philox4x32-10 keyed by seed, counter (individual,
+ * generation, run, call), so results do not depend on launch shapes. */
+typedef struct {
+    int n_runs;              /* independent runs, >= 1 */
+    int pop;                 /* individuals per run, 2..1024 */
+    int max_gens;            /* generations after the initial population, >= 0 */
+    long long max_evals;     /* evaluation budget of a run, checked after each generation */
+    int ls_iters;            /* evaluations of one local search, >= 1 */
+    float ls_rate;           /* probability of a local search, 0..1 */
+    float rho, eps;          /* ADADELTA parameters */
+    float p_cross, p_mut;    /* crossover / per-gene mutation probabilities */
+    float mut_trans;         /* translation mutation amplitude (A) */
+    float mut_angle;         /* angle mutation amplitude (rad) */
+    unsigned long long seed;
+    int reduce_variant;      /* ADGB_REDUCE_* or -1 for the context default */
+} adgb_dock_params;
+
+/*
+ * dock - n_runs independent Lamarckian GA runs of one ligand against one
+ * receptor (Sec. 2.1; Table 1's kernels: initial population scoring, GA
+ * generation, local search, evaluation count).  Every generation is three
+ * launches: GA generation, one fused local-search launch over all runs'
+ * individuals, run-best and evaluation accounting.  At the end each run's
+ * best genotype is rescored in FP64 on the GPU.
+ * best_genes [n_runs][6+T] float32 out; best_energy [n_runs] FP64 out;
+ * evals [n_runs] out or NULL (evaluations each run spent).
+ * The device working set (2 populations, energies, counters, about
+ * 8 * n_runs * pop * (7 + T) bytes) is allocated stream-ordered per call.
+ * Errors: EINVAL, ENOTFOUND, ENOMEM, EDEVICE.
+ */
+int dock_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *p,
+             float *best_genes_dev, double *best_energy_dev, long long *evals_dev,
+             adgb_stream stream);
+int dock(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *p,
+         float *best_genes, double *best_energy, long long *evals);
+
+/*
+ * ga_init_population_dev - the initial genotypes dock() starts from:
+ * genes [n_runs * pop][6+T] out (translation uniform in the central 60% of
+ * the receptor's grid box, axis uniform on the sphere, angles uniform).
+ * ga_generation_dev - one GA generation of n_runs populations (the rules
+ * of adgb_dock_params; p->n_runs and p->pop give the shapes): genes and
+ * energy [n_runs * pop] in, genes_out out, iters_out [n_runs * pop] out
+ * (ls_iters for individuals chosen for a local search, else 1).
+ * generation >= 1 selects the random stream.  Errors: EINVAL, ENOTFOUND.
+ */
+int ga_init_population_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, unsigned long long seed,
+                           int n_runs, int pop, float *genes_dev, adgb_stream stream);
+int ga_generation_dev(adgb_ctx *ctx, int ligand_id, const adgb_dock_params *p, int generation,
+                      const float *genes_dev, const float *energy_dev, float *genes_out_dev,
+                      int *iters_out_dev, adgb_stream stream);
+
+/*
+ * rescore_fp64_dev - energies of n genotypes recomputed in double precision
+ * on the GPU from the same inputs (coordinates, grid and pair terms).
+ * genes [n][6+T] float32, energy [n] FP64 out.
+ */
+int rescore_fp64_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, const float *genes_dev,
+                     int n, double *energy_dev, adgb_stream stream);
+
 /*
  * reduce4_bench_dev - the reduction test kernel of Sec. 5.2: every thread
  * of a block holds one four-element vector, the block computes the sum and

@@ -30,7 +30,8 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "release_receptor", "upload_ligand_torsion_tree", "release_ligand",
            "validate_ligand_torsion_tree",
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
-           "local_search_dev", "local_search", "reduce4_bench_dev"]
+           "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
+           "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev"]
 
 
 class AdgbError(RuntimeError):
@@ -60,6 +61,25 @@ class _Ligand(C.Structure):
                 ("pairs", _i32p), ("R", _f32p), ("eps", _f32p), ("vol", _f32p),
                 ("solpar", _f32p), ("hb_role", _i32p), ("hb_R", C.c_float),
                 ("hb_eps", C.c_float)]
+
+
+class _DockParams(C.Structure):
+    _fields_ = [("n_runs", C.c_int), ("pop", C.c_int), ("max_gens", C.c_int),
+                ("max_evals", C.c_longlong), ("ls_iters", C.c_int), ("ls_rate", C.c_float),
+                ("rho", C.c_float), ("eps", C.c_float), ("p_cross", C.c_float),
+                ("p_mut", C.c_float), ("mut_trans", C.c_float), ("mut_angle", C.c_float),
+                ("seed", C.c_ulonglong), ("reduce_variant", C.c_int)]
+
+
+DOCK_DEFAULTS = dict(n_runs=20, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
+                     ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
+                     mut_angle=float(np.pi / 2), seed=2410, reduce_variant=-1)
+
+
+def dock_params(**kw) -> _DockParams:
+    d = dict(DOCK_DEFAULTS)
+    d.update(kw)
+    return _DockParams(*[d[f] for f, _ in _DockParams._fields_])
 
 
 class _LSParams(C.Structure):
@@ -99,6 +119,13 @@ def load(build: bool = False):
                                    vp, vp, vp]
     L.local_search.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_LSParams), vp, vp]
     L.reduce4_bench_dev.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.dock_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
+    L.dock.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp]
+    L.rescore_fp64_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+    L.ga_init_population_dev.argtypes = [vp, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int,
+                                         vp, vp]
+    L.ga_generation_dev.argtypes = [vp, C.c_int, C.POINTER(_DockParams), C.c_int, vp, vp, vp, vp,
+                                    vp]
     _lib = L
     return L
 
@@ -202,6 +229,7 @@ class Context:
         d, keep = _ligand_desc(lig)
         lid = C.c_int()
         self._chk(self.lib.upload_ligand_torsion_tree(self.h, C.byref(d), C.byref(lid)))
+        self._keep[lid.value] = int(lig["n_tors"])
         return lid.value
 
     def release_ligand(self, lid: int):
@@ -243,7 +271,36 @@ class Context:
                                              _ptr(out), _stream()))
         return out
 
+    def dock_dev(self, rid, lid, params, best_genes, best_energy, evals=None):
+        self._chk(self.lib.dock_dev(self.h, rid, lid, C.byref(params), _ptr(best_genes),
+                                    _ptr(best_energy), _ptr(evals), _stream()))
+
+    def rescore_fp64_dev(self, rid, lid, genes, energy):
+        _check_dev(genes, "genes")
+        self._chk(self.lib.rescore_fp64_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
+                                            _ptr(energy), _stream()))
+
+    def ga_init_population_dev(self, rid, lid, seed, n_runs, pop, genes):
+        _check_dev(genes, "genes")
+        self._chk(self.lib.ga_init_population_dev(self.h, rid, lid, seed, n_runs, pop, _ptr(genes),
+                                                  _stream()))
+
+    def ga_generation_dev(self, lid, params, gen, genes, energy, genes_out, iters_out):
+        self._chk(self.lib.ga_generation_dev(self.h, lid, C.byref(params), gen, _ptr(genes),
+                                             _ptr(energy), _ptr(genes_out), _ptr(iters_out),
+                                             _stream()))
+
     # -------------------------------------------------------- host calls
+    def dock(self, rid, lid, params):
+        """(best genes [runs][G] float32, FP64-rescored best energies [runs],
+        evaluations [runs]) of dock() with host buffers."""
+        n = params.n_runs
+        bg = np.zeros((n, 6 + self._keep[lid]), np.float32)
+        be = np.zeros(n, np.float64)
+        ev = np.zeros(n, np.int64)
+        self._chk(self.lib.dock(self.h, rid, lid, C.byref(params), bg.ctypes.data, be.ctypes.data,
+                                ev.ctypes.data))
+        return bg, be, ev
     def pose_coords(self, lid, genes, n_atoms):
         g = _f32(genes)
         out = np.zeros((g.shape[0], n_atoms, 3), np.float32)

@@ -25,6 +25,7 @@ struct RecDev {
     int nx, ny, nz, M;      // points per axis, maps (types + e + d)
     float lo[3], hi[3];     // first and last grid point per axis
     float inv_h;            // 1 / spacing
+    float h;                // spacing
     const float *cells;
 };
 
@@ -45,6 +46,28 @@ struct LigDev {
     const int *perm;          // [N] internal index -> caller's index
     const int *inc_off;       // [N+1] incidence list of atom i: inc[inc_off[i] .. inc_off[i+1])
     const uint16_t *inc;      // [2 Np] (pair index << 1) | (atom is the pair's second atom), ascending
+    // the caller's per-type parameters, kept for the FP64 rescoring
+    const float *t_R, *t_eps, *t_vol, *t_sol;
+    const int *t_hb;
+    float hb_R, hb_eps;
+};
+
+// Lamarckian GA parameters as the kernels see them.
+struct DockCfg {
+    int n_runs, pop, max_gens, ls_iters;
+    long long max_evals;
+    float ls_rate, rho, eps, p_cross, p_mut, mut_trans, mut_angle;
+    uint64_t seed;
+};
+
+// Device working set of one dock call.
+struct DockScratch {
+    float *genes[2];      // [runs * pop][G] current and next population
+    float *energy;        // [runs * pop]
+    int *iters;           // [runs * pop] evaluations of each individual this generation
+    float *best_e;        // [runs]
+    long long *evals;     // [runs]
+    int *done;            // [runs]
 };
 
 // Shared-memory layout of one block of the scoring / local-search kernel:
@@ -106,7 +129,17 @@ struct EvalCfg {
 cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
                         int mode, const float *genes_in, float *genes_out, int n,
                         int iters, float rho, float eps, int resume, float *energy,
-                        float *grad, float *state, cudaStream_t s);
+                        float *grad, float *state, cudaStream_t s,
+                        const int *iters_per_pose = nullptr);
+cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const DockCfg &d,
+                        float *best_genes, double *best_energy, long long *evals_out,
+                        DockScratch &w, cudaStream_t s);
+cudaError_t launch_rescore_fp64(const RecDev &rec, const LigDev &lig, int n, const float *genes,
+                                double *out, cudaStream_t s);
+cudaError_t launch_init_population(const RecDev &rec, int n_tors, uint64_t seed, int n_runs, int pop,
+                                   float *genes, int *iters, cudaStream_t s);
+cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *genes,
+                                 const float *energy, float *genes_out, int *iters, cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
                           cudaStream_t s);
 cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M,

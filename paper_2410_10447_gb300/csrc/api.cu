@@ -131,6 +131,8 @@ struct HostLigand {
     std::vector<float2> tptab;
     std::vector<int> inc_off;
     std::vector<uint16_t> inc;
+    std::vector<float> tR, teps, tvol, tsol;
+    std::vector<int> thb;
     int max_type = 0;
 };
 
@@ -297,6 +299,11 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
             h.inc[fill[(h.pairs[p] >> 8) & 255]++] = (uint16_t)((p << 1) | 1);
         }
     }
+    h.tR.assign(d->R, d->R + NT);
+    h.teps.assign(d->eps, d->eps + NT);
+    h.tvol.assign(d->vol, d->vol + NT);
+    h.tsol.assign(d->solpar, d->solpar + NT);
+    h.thb.assign(d->hb_role, d->hb_role + NT);
     h.tptab.assign(TYPE_TAB, make_float2(0.f, 0.f));
     for (int ti = 0; ti < NT; ti++)
         for (int tj = 0; tj < NT; tj++) {
@@ -450,6 +457,7 @@ int upload_receptor_grids(adgb_ctx *c, const adgb_grid_desc *g, const float *map
         R.dev.hi[d] = (float)((double)g->origin[d] + (double)(n[d] - 1) * g->spacing);
     }
     R.dev.inv_h = (float)(1.0 / (double)g->spacing);
+    R.dev.h = g->spacing;
     R.dev.cells = cells;
     const int id = c->next_id++;
     c->recs[id] = R;
@@ -481,6 +489,9 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
     const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
     const size_t o_incoff = take(4 * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
+    const int NT = d->n_types;
+    const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
+                 o_tsol = take(4 * NT), o_thb = take(4 * NT);
     std::vector<unsigned char> buf(off, 0);
     memcpy(&buf[o_ref], h.ref.data(), 16 * N);
     memcpy(&buf[o_sv], h.sv.data(), 8 * N);
@@ -497,6 +508,11 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     memcpy(&buf[o_perm], h.perm.data(), 4 * N);
     memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (N + 1));
     if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
+    memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
+    memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
+    memcpy(&buf[o_tvol], h.tvol.data(), 4 * NT);
+    memcpy(&buf[o_tsol], h.tsol.data(), 4 * NT);
+    memcpy(&buf[o_thb], h.thb.data(), 4 * NT);
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
     unsigned char *mem = nullptr;
@@ -532,6 +548,13 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     v.perm = reinterpret_cast<const int *>(mem + o_perm);
     v.inc_off = reinterpret_cast<const int *>(mem + o_incoff);
     v.inc = reinterpret_cast<const uint16_t *>(mem + o_inc);
+    v.t_R = reinterpret_cast<const float *>(mem + o_tR);
+    v.t_eps = reinterpret_cast<const float *>(mem + o_teps);
+    v.t_vol = reinterpret_cast<const float *>(mem + o_tvol);
+    v.t_sol = reinterpret_cast<const float *>(mem + o_tsol);
+    v.t_hb = reinterpret_cast<const int *>(mem + o_thb);
+    v.hb_R = d->hb_R;
+    v.hb_eps = d->hb_eps;
     const int id = c->next_id++;
     c->ligs[id] = L;
     *ligand_id = id;
@@ -683,6 +706,158 @@ int local_search(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int 
     if (e == cudaSuccess && state) e = cudaMemcpyAsync(state, ds, 4 * 3 * G * n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search");
+}
+
+static int check_dock(adgb_ctx *c, const adgb_dock_params *p, int &variant, DockCfg &d) {
+    if (!p) return fail(c, ADGB_EINVAL, "dock: null parameters");
+    if (p->n_runs < 1 || p->pop < 2 || p->pop > 1024 || p->max_gens < 0 || p->ls_iters < 1 ||
+        p->max_evals < 0 || !(p->ls_rate >= 0.f && p->ls_rate <= 1.f) ||
+        !(p->rho > 0.f && p->rho < 1.f) || !(p->eps > 0.f) || !(p->p_cross >= 0.f && p->p_cross <= 1.f) ||
+        !(p->p_mut >= 0.f && p->p_mut <= 1.f) || !finite(p->mut_trans) || !finite(p->mut_angle) ||
+        (long long)p->n_runs * p->pop > (1 << 26))
+        return fail(c, ADGB_EINVAL, "dock: bad parameters");
+    variant = p->reduce_variant;
+    int rc = check_variant(c, variant);
+    if (rc) return rc;
+    d.n_runs = p->n_runs;
+    d.pop = p->pop;
+    d.max_gens = p->max_gens;
+    d.ls_iters = p->ls_iters;
+    d.max_evals = p->max_evals;
+    d.ls_rate = p->ls_rate;
+    d.rho = p->rho;
+    d.eps = p->eps;
+    d.p_cross = p->p_cross;
+    d.p_mut = p->p_mut;
+    d.mut_trans = p->mut_trans;
+    d.mut_angle = p->mut_angle;
+    d.seed = p->seed;
+    return ADGB_OK;
+}
+
+// stream-ordered working set of one dock call
+static cudaError_t dock_scratch(DockScratch &w, void **mem, int n, int G, int runs, cudaStream_t s) {
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = al256(off + b); return o; };
+    const size_t og0 = take(4 * (size_t)n * G), og1 = take(4 * (size_t)n * G), oe = take(4 * (size_t)n),
+                 oi = take(4 * (size_t)n), ob = take(4 * (size_t)runs), ov = take(8 * (size_t)runs),
+                 od = take(4 * (size_t)runs);
+    cudaError_t e = cudaMallocAsync(mem, off, s);
+    if (e != cudaSuccess) return e;
+    char *m = (char *)*mem;
+    w.genes[0] = (float *)(m + og0);
+    w.genes[1] = (float *)(m + og1);
+    w.energy = (float *)(m + oe);
+    w.iters = (int *)(m + oi);
+    w.best_e = (float *)(m + ob);
+    w.evals = (long long *)(m + ov);
+    w.done = (int *)(m + od);
+    return cudaSuccess;
+}
+
+int dock_dev(adgb_ctx *c, int receptor_id, int ligand_id, const adgb_dock_params *p,
+             float *best_genes_dev, double *best_energy_dev, long long *evals_dev,
+             adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    DockCfg d;
+    int rc = check_dock(c, p, variant, d);
+    if (rc) return rc;
+    if (!best_genes_dev || !best_energy_dev) return fail(c, ADGB_EINVAL, "dock: null output");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    DeviceGuard g(c->device);
+    const cudaStream_t s = (cudaStream_t)stream;
+    DockScratch w;
+    void *mem = nullptr;
+    cudaError_t e = dock_scratch(w, &mem, d.n_runs * d.pop, 6 + L->n_tors, d.n_runs, s);
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "dock: %s", cudaGetErrorString(e));
+    e = launch_dock(R->dev, L->dev, pick_cfg(c, *L, variant), d, best_genes_dev, best_energy_dev,
+                    evals_dev, w, s);
+    cudaFreeAsync(mem, s);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "dock");
+}
+
+int dock(adgb_ctx *c, int receptor_id, int ligand_id, const adgb_dock_params *p, float *best_genes,
+         double *best_energy, long long *evals) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    DockCfg d;
+    int rc = check_dock(c, p, variant, d);
+    if (rc) return rc;
+    if (!best_genes || !best_energy) return fail(c, ADGB_EINVAL, "dock: null output");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    DeviceGuard g(c->device);
+    const int G = 6 + L->n_tors;
+    const size_t bg = al256(4 * (size_t)d.n_runs * G), be = al256(8 * (size_t)d.n_runs);
+    if ((rc = stage_reserve(c, bg + 2 * be))) return rc;
+    float *dg = (float *)c->stage;
+    double *de = (double *)((char *)c->stage + bg);
+    long long *dv = (long long *)((char *)c->stage + bg + be);
+    DockScratch w;
+    void *mem = nullptr;
+    cudaError_t e = dock_scratch(w, &mem, d.n_runs * d.pop, G, d.n_runs, c->stream);
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "dock: %s", cudaGetErrorString(e));
+    e = launch_dock(R->dev, L->dev, pick_cfg(c, *L, variant), d, dg, de, dv, w, c->stream);
+    cudaFreeAsync(mem, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best_genes, dg, 4 * (size_t)d.n_runs * G, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best_energy, de, 8 * (size_t)d.n_runs, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && evals) e = cudaMemcpyAsync(evals, dv, 8 * (size_t)d.n_runs, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "dock");
+}
+
+int ga_init_population_dev(adgb_ctx *c, int receptor_id, int ligand_id, unsigned long long seed,
+                           int n_runs, int pop, float *genes_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n_runs < 0 || pop < 0 || (n_runs * (long long)pop > 0 && !genes_dev))
+        return fail(c, ADGB_EINVAL, "ga_init_population: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    int rc = lookup(c, receptor_id, ligand_id, &R, &L);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    const int n = n_runs * pop;
+    int *iters = nullptr;
+    cudaError_t e = cudaMallocAsync(&iters, 4 * (size_t)(n > 0 ? n : 1), (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "ga_init_population: %s", cudaGetErrorString(e));
+    e = launch_init_population(R->dev, L->n_tors, seed, n_runs, pop, genes_dev, iters, (cudaStream_t)stream);
+    cudaFreeAsync(iters, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ga_init_population");
+}
+
+int ga_generation_dev(adgb_ctx *c, int ligand_id, const adgb_dock_params *p, int generation,
+                      const float *genes_dev, const float *energy_dev, float *genes_out_dev,
+                      int *iters_out_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    DockCfg d;
+    int rc = check_dock(c, p, variant, d);
+    if (rc) return rc;
+    if (generation < 1 || !genes_dev || !energy_dev || !genes_out_dev || !iters_out_dev)
+        return fail(c, ADGB_EINVAL, "ga_generation: bad arguments");
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, 0, ligand_id, nullptr, &L))) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_ga_generation(d, 6 + L->n_tors, generation, genes_dev, energy_dev,
+                                         genes_out_dev, iters_out_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ga_generation");
+}
+
+int rescore_fp64_dev(adgb_ctx *c, int receptor_id, int ligand_id, const float *genes_dev, int n,
+                     double *energy_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!genes_dev || !energy_dev))) return fail(c, ADGB_EINVAL, "rescore_fp64: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    int rc = lookup(c, receptor_id, ligand_id, &R, &L);
+    if (rc) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_rescore_fp64(R->dev, L->dev, n, genes_dev, energy_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "rescore_fp64");
 }
 
 int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads, int n_blocks,

@@ -35,6 +35,7 @@ struct EvalArgs {
     float *energy;
     float *grad;
     float *state;
+    const int *iters_pp;  // per-genotype evaluation counts, or null (all `iters`)
     int n, iters, resume, mode;
     float rho, eps;
 };
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
         best[r] = om[r];
     }
     float best_e = INFINITY;
-    const int iters = a.mode == MODE_SCORE ? 1 : a.iters;
+    const int iters = a.mode == MODE_SCORE ? 1 : (a.iters_pp ? a.iters_pp[pose] : a.iters);
 
     for (int it = 0; it < iters; it++) {
         // 1. publish genes, sin and 1 - cos of every angle (half-angle form:
@@ -545,9 +546,10 @@ static cudaError_t launch_v(const EvalArgs &a, int ppb, int variant, cudaStream_
 cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, int mode,
                         const float *genes_in, float *genes_out, int n, int iters, float rho,
                         float eps, int resume, float *energy, float *grad, float *state,
-                        cudaStream_t s) {
+                        cudaStream_t s, const int *iters_per_pose) {
     if (n == 0) return cudaSuccess;
     EvalArgs a;
+    a.iters_pp = iters_per_pose;
     a.rec = rec;
     a.lig = lig;
     a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk, lig.n_pairs,

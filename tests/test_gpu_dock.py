@@ -1,0 +1,161 @@
+"""GPU parity of the Lamarckian GA path (dock) against the FP64 oracle.
+
+The GA rules and the Philox4x32-10 stream are implemented independently in
+the oracle and the CUDA library; with the same seed and the same inputs
+their decisions (tournaments, cut points, mutations, local-search choices)
+coincide exactly, and gene values agree to float32 rounding.  Whole docking
+runs diverge chaotically (FP32 vs FP64 local searches), so they are checked
+through invariants and the FP64 rescoring of their results.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    assert T.cuda.is_available(), "GPU tests need a CUDA device"
+    return T
+
+
+@pytest.fixture(scope="module")
+def pkg(torch):
+    import paper_2410_10447_gb300 as P
+    P.load(build=True)
+    return P
+
+
+@pytest.fixture(scope="module")
+def w():
+    return synth.workload("plain_n16", n_poses=8)
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def oracle_params(gp):
+    """the oracle's parameter block holding the float32 values the GPU uses"""
+    return oracle.dock_params(n_runs=gp.n_runs, pop=gp.pop, max_gens=gp.max_gens,
+                              max_evals=gp.max_evals, ls_iters=gp.ls_iters,
+                              ls_rate=f32(gp.ls_rate), rho=f32(gp.rho), eps=f32(gp.eps),
+                              p_cross=f32(gp.p_cross), p_mut=f32(gp.p_mut),
+                              mut_trans=f32(gp.mut_trans), mut_angle=f32(gp.mut_angle),
+                              seed=gp.seed)
+
+
+def ang(a, b):
+    return (a - b + np.pi) % (2 * np.pi) - np.pi
+
+
+def test_initial_population_matches_oracle(pkg, torch, w):
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    T = w["ligand"]["n_tors"]
+    runs, pop = 3, 50
+    g = torch.empty(runs * pop, 6 + T, device="cuda")
+    ctx.ga_init_population_dev(rid, lid, 77, runs, pop, g)
+    got = g.cpu().numpy().astype(np.float64)
+    for r in range(runs):
+        for k in range(pop):
+            ref = oracle.init_individual(w["receptor"], T, 77, r, k)
+            row = got[r * pop + k]
+            assert np.max(np.abs(row[:3] - ref[:3])) < 2e-5
+            assert np.max(np.abs(ang(row[3:], ref[3:]))) < 2e-6, (r, k, row, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("p_cross, p_mut, ls_rate", [(0.8, 0.02, 1.0), (0.5, 0.3, 0.4), (1.0, 0.0, 0.0)])
+def test_ga_generation_matches_oracle(pkg, torch, w, p_cross, p_mut, ls_rate):
+    ctx = pkg.Context(0)
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    G = 6 + w["ligand"]["n_tors"]
+    runs, pop = 4, 37
+    rng = np.random.default_rng(3)
+    genes = rng.normal(size=(runs * pop, G)).astype(np.float32)
+    energy = (rng.normal(size=runs * pop) * 20).astype(np.float32)
+    energy[5] = energy[9]          # a tie: lower index wins
+    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, p_cross=p_cross, p_mut=p_mut,
+                              ls_rate=ls_rate, ls_iters=17, seed=991)
+    gi = torch.from_numpy(genes).cuda()
+    ei = torch.from_numpy(energy).cuda()
+    go = torch.empty_like(gi)
+    it = torch.empty(runs * pop, dtype=torch.int32, device="cuda")
+    for gen in (1, 2, 25):
+        ctx.ga_generation_dev(lid, gp, gen, gi, ei, go, it)
+        got = go.cpu().numpy().astype(np.float64)
+        its = it.cpu().numpy()
+        op = oracle_params(gp)
+        for r in range(runs):
+            ref, fl = oracle.ga_generation(genes[r * pop:(r + 1) * pop], energy[r * pop:(r + 1) * pop],
+                                           op, r, gen)
+            assert np.array_equal(its[r * pop:(r + 1) * pop], np.where(fl == 1, 17, 1))
+            d = got[r * pop:(r + 1) * pop] - ref
+            d[:, 6:] = ang(got[r * pop:(r + 1) * pop, 6:], ref[:, 6:])
+            assert np.max(np.abs(d)) < 1e-5, (gen, r, np.max(np.abs(d)))
+    ctx.close()
+
+
+def test_fp64_rescoring_matches_oracle(pkg, torch):
+    for name in ("plain_n16", "lga_n32", "stress_n256"):
+        wk = synth.workload(name, n_poses=24)
+        ctx = pkg.Context(0)
+        rid = ctx.upload_receptor_grids(wk["receptor"])
+        lid = ctx.upload_ligand_torsion_tree(wk["ligand"])
+        g = torch.from_numpy(wk["genes"]).cuda()
+        e = torch.empty(g.shape[0], dtype=torch.float64, device="cuda")
+        ctx.rescore_fp64_dev(rid, lid, g, e)
+        got = e.cpu().numpy()
+        R, L = oracle.Receptor(wk["receptor"]), oracle.Ligand(wk["ligand"])
+        for p in range(g.shape[0]):
+            ref = oracle.score(R, L, wk["genes"][p])[0]
+            assert abs(got[p] - ref) <= 1e-9 * max(abs(ref), 1.0), (name, p, got[p], ref)
+        ctx.close()
+
+
+def test_dock_results_and_accounting(pkg, torch, w):
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    runs, pop, gens, it = 3, 24, 4, 30
+    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, max_gens=gens, ls_iters=it, ls_rate=1.0, seed=5)
+    bg, be, ev = ctx.dock(rid, lid, gp)
+    assert np.all(ev == pop + gens * pop * it)
+    R, L = oracle.Receptor(w["receptor"]), oracle.Ligand(w["ligand"])
+    T = w["ligand"]["n_tors"]
+    for r in range(runs):
+        ref = oracle.score(R, L, bg[r])[0]               # FP64 rescoring of the result
+        assert abs(be[r] - ref) <= 1e-9 * max(abs(ref), 1.0)
+        init = min(oracle.score(R, L, oracle.init_individual(w["receptor"], T, 5, r, k))[0]
+                   for k in range(pop))
+        assert be[r] <= init + 1e-3 * max(abs(init), 1.0)
+    # deterministic for a fixed seed
+    bg2, be2, ev2 = ctx.dock(rid, lid, gp)
+    assert np.array_equal(bg, bg2) and np.array_equal(be, be2) and np.array_equal(ev, ev2)
+    # the evaluation budget stops the runs after the generation that reaches it
+    gp2 = pkg.adgb.dock_params(n_runs=2, pop=pop, max_gens=10, max_evals=100, ls_iters=it,
+                               ls_rate=1.0, seed=5)
+    _, _, ev3 = ctx.dock(rid, lid, gp2)
+    assert np.all(ev3 == pop + pop * it)
+    ctx.close()
+
+
+def test_dock_matches_oracle_statistically(pkg, torch, w):
+    """Best energies of GPU and oracle docking of the same runs (same seed,
+    same initial populations) come from the same distribution (Sec. 5.1
+    compares best-energy distributions the same way)."""
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    gp = pkg.adgb.dock_params(n_runs=8, pop=20, max_gens=3, ls_iters=40, ls_rate=1.0, seed=31)
+    _, be, _ = ctx.dock(rid, lid, gp)
+    _, be_ref, _ = oracle.dock(w["receptor"], w["ligand"], oracle_params(gp))
+    med, med_ref = np.median(be), np.median(be_ref)
+    assert abs(med - med_ref) <= 0.15 * abs(med_ref) + 1.0, (be, be_ref)
+    ctx.close()
