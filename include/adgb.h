@@ -248,6 +248,26 @@ int dock(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *
          float *best_genes, double *best_energy, long long *evals);
 
 /*
+ * dock_noalloc_dev - dock_dev for callers that must not allocate device
+ * memory during a call (programs that reserve the GPU's whole memory budget
+ * up front, or serving paths where an allocation's latency or failure is not
+ * acceptable).  No counterpart in the paper: it is a deployment variant.
+ * Same arguments, results and errors as dock_dev, but the working set lives
+ * in one fixed 4 MiB device array built into the library (held on every
+ * device that loads it, until the process exits); nothing is allocated or
+ * freed.  The working set is 8 * n_runs * pop * (6 + T) + 8 * n_runs * pop +
+ * 16 * n_runs bytes plus 256-byte alignment per part; larger requests
+ * return ADGB_EINVAL.  All calls share the array: calls whose work overlaps
+ * on the GPU (other streams, other contexts, other host threads) race and
+ * must be serialised by the caller.  Every part of the array a call reads is
+ * first written by that call.  The first call on a device looks up the
+ * array's device address; make that first call before any stream capture.
+ */
+int dock_noalloc_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *p,
+                     float *best_genes_dev, double *best_energy_dev, long long *evals_dev,
+                     adgb_stream stream);
+
+/*
  * ga_init_population_dev - the initial genotypes dock() starts from:
  * genes [n_runs * pop][6+T] out (translation uniform in the central 60% of
  * the receptor's grid box, axis uniform on the sphere, angles uniform).

@@ -31,7 +31,8 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "validate_ligand_torsion_tree",
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
-           "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev"]
+           "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev",
+           "dock_noalloc_dev"]
 
 
 class AdgbError(RuntimeError):
@@ -122,6 +123,7 @@ def load(build: bool = False):
     L.dock_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.dock.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp]
     L.rescore_fp64_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+    L.dock_noalloc_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.ga_init_population_dev.argtypes = [vp, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int,
                                          vp, vp]
     L.ga_generation_dev.argtypes = [vp, C.c_int, C.POINTER(_DockParams), C.c_int, vp, vp, vp, vp,
@@ -274,6 +276,12 @@ class Context:
     def dock_dev(self, rid, lid, params, best_genes, best_energy, evals=None):
         self._chk(self.lib.dock_dev(self.h, rid, lid, C.byref(params), _ptr(best_genes),
                                     _ptr(best_energy), _ptr(evals), _stream()))
+
+    def dock_noalloc_dev(self, rid, lid, params, best_genes, best_energy, evals=None):
+        """dock_dev with the working set in the library's fixed device array
+        (no allocation during the call)."""
+        self._chk(self.lib.dock_noalloc_dev(self.h, rid, lid, C.byref(params), _ptr(best_genes),
+                                            _ptr(best_energy), _ptr(evals), _stream()))
 
     def rescore_fp64_dev(self, rid, lid, genes, energy):
         _check_dev(genes, "genes")

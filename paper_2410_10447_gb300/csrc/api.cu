@@ -875,3 +875,93 @@ int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// dock_noalloc_dev: dock_dev without any device allocation.
+//
+// Some callers cannot allocate device memory when they call the library:
+// host programs that reserve the whole GPU memory budget up front and forbid
+// libraries to allocate, and latency-critical serving paths where an
+// allocation (which may synchronise the device, and may fail under memory
+// pressure) is not acceptable in the middle of a request.  For them the dock
+// working set lives in one fixed device array compiled into the library.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr size_t NOALLOC_BYTES = 4u << 20;  // 4 MiB, held on every device that loads the library
+static __device__ __align__(256) unsigned char g_dock_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_dock_scratch on the current device (looked up once per
+// device; the host-side symbol is only a stand-in for it).
+cudaError_t noalloc_base(int device, void **out) {
+    if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_dock_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+// Same partition as the allocating path: two populations, energies, counts,
+// run bests, evaluation counters, stop flags.
+size_t noalloc_layout(DockScratch *w, unsigned char *base, int n, int G, int runs) {
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off = al256(off + b); return o; };
+    const size_t og0 = take(4 * (size_t)n * G), og1 = take(4 * (size_t)n * G), oe = take(4 * (size_t)n),
+                 oi = take(4 * (size_t)n), ob = take(4 * (size_t)runs), ov = take(8 * (size_t)runs),
+                 od = take(4 * (size_t)runs);
+    if (w && base) {
+        w->genes[0] = (float *)(base + og0);
+        w->genes[1] = (float *)(base + og1);
+        w->energy = (float *)(base + oe);
+        w->iters = (int *)(base + oi);
+        w->best_e = (float *)(base + ob);
+        w->evals = (long long *)(base + ov);
+        w->done = (int *)(base + od);
+    }
+    return off;
+}
+
+}  // namespace
+
+extern "C" int dock_noalloc_dev(adgb_ctx *c, int receptor_id, int ligand_id,
+                                const adgb_dock_params *p, float *best_genes_dev,
+                                double *best_energy_dev, long long *evals_dev,
+                                adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    DockCfg d;
+    int rc = check_dock(c, p, variant, d);
+    if (rc) return rc;
+    if (!best_genes_dev || !best_energy_dev) return fail(c, ADGB_EINVAL, "dock_noalloc: null output");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    const int G = 6 + L->n_tors;
+    const size_t need = noalloc_layout(nullptr, nullptr, d.n_runs * d.pop, G, d.n_runs);
+    if (need > NOALLOC_BYTES)
+        return fail(c, ADGB_EINVAL,
+                    "dock_noalloc: working set of %zu bytes (%d runs x %d individuals, %d genes) "
+                    "exceeds the fixed %zu-byte array",
+                    need, d.n_runs, d.pop, G, NOALLOC_BYTES);
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
+    void *base = nullptr;
+    cudaError_t e = noalloc_base(c->device, &base);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dock_noalloc: scratch address");
+    DockScratch w;
+    noalloc_layout(&w, (unsigned char *)base, d.n_runs * d.pop, G, d.n_runs);
+    e = launch_dock(R->dev, L->dev, pick_cfg(c, *L, variant), d, best_genes_dev, best_energy_dev,
+                    evals_dev, w, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "dock_noalloc");
+}
