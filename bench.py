@@ -1,18 +1,23 @@
-"""Benchmark: energy+gradient evaluations per second of the ADADELTA local
-search on the batched-LGA workload (20 runs x 150 genotypes of a 32-atom,
-8-torsion ligand on a 64^3 grid with 10 maps, 300 ADADELTA steps each).
+"""Benchmark: energy+gradient evaluations per second of Lamarckian-GA
+docking on the batched workload `lga_n32`: 20 runs x 150 genotypes of a
+32-atom, 8-torsion ligand against a 64^3 grid with 8+2 maps; 27 generations,
+every individual locally searched with 300 ADADELTA evaluations.
 
-One step = one local-search pass of the whole population: 3000 genotypes x
-300 energy+gradient evaluations = 900,000 evaluations, one kernel launch.
+One step = one whole dock() call: initial population scoring, 27 x (GA
+generation + one fused local-search launch over all 3000 individuals + run
+best/evaluation accounting), FP64 rescoring of the 20 run bests:
+20 * 150 * (1 + 27 * 300) = 24.3M energy+gradient evaluations.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adgb|reference]
                   [--variant shfl|mma_tf32x2|mma_bf16x3]
 
-Prints ONE JSON line (rank 0).  `value` is device-timed (CUDA events on
-the launching stream, inputs resident in HBM, L2 flushed between steps and
-excluded); `e2e` is the same metric through the host-buffer C call
-`local_search` (host->device genes, device->host genes and energies inside
-the timed region).  `--impl reference` times the FP64 CPU oracle instead.
+Prints ONE JSON line (rank 0).  `value`: device time (CUDA events on the
+launching stream; receptor and ligand resident; L2 flushed between steps,
+flush not timed).  `e2e`: the same metric through the host C calls a
+docking job makes (upload_ligand_torsion_tree, dock with host outputs,
+release_ligand).  The roofline line is for the local-search kernel (98-99%
+of the GPU time), measured from standalone launches of the same shape.
+`--impl reference` times the FP64 CPU oracle's docking on a bounded sample.
 Multi-GPU (torchrun) runs one independent replica per rank (weak scaling).
 """
 from __future__ import annotations
@@ -34,6 +39,11 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "lga_n32"
 ITERS = 300
+RUNS, POP, GENS = 20, 150, 27
+EVALS_PER_DOCK = RUNS * POP * (1 + GENS * ITERS)
+# kernel launches of one dock(): state init, initial population, its scoring
+# and accounting, then GA + local search + accounting per generation, rescoring
+LAUNCHES_PER_DOCK = 4 + 3 * GENS + 1
 # Algorithmic ALU work per energy+gradient evaluation, counted from the
 # method (FMA = 2 flops; one MUFU op = 16 flop-equivalents, the FP32 pipe
 # being 8x wider than the special-function pipe):
@@ -139,12 +149,16 @@ def kernel_sha():
     return h.hexdigest()[:12]
 
 
-def run_oracle_sample(w, n_geno, nthreads):
+def oracle_dock_sample(w, n_runs, gens, nthreads, seed):
+    """FP64 oracle docking of n_runs runs x 150 genotypes for `gens`
+    generations (a bounded sample of the benchmark's dock); returns
+    (evaluations, seconds)."""
     import oracle
+    prm = oracle.dock_params(n_runs=n_runs, pop=POP, max_gens=gens, ls_iters=ITERS,
+                             ls_rate=1.0, seed=seed)
     t = time.perf_counter()
-    oracle.local_search_batch(w["receptor"], w["ligand"], w["genes"][:n_geno], ITERS,
-                              nthreads=nthreads)
-    return time.perf_counter() - t
+    _, _, ev = oracle.dock(w["receptor"], w["ligand"], prm, nthreads=nthreads)
+    return int(ev.sum()), time.perf_counter() - t
 
 
 def reference_arm(args, rank, world):
@@ -154,22 +168,27 @@ def reference_arm(args, rank, world):
     import oracle
     import synth
     oracle.build()
-    w = synth.workload(WORKLOAD)
+    w = synth.workload(WORKLOAD, n_poses=1)
     cores = os.cpu_count() or 1
-    n_geno = args.ref_genotypes
-    for _ in range(args.warmup):
-        run_oracle_sample(w, n_geno, cores)
-    t = sum(run_oracle_sample(w, n_geno, cores) for _ in range(args.steps))
-    evals = args.steps * n_geno * ITERS
-    v = evals / t
+    for i in range(args.warmup):
+        oracle_dock_sample(w, args.ref_runs, 1, cores, 1000 + i)
+    ev = t = 0
+    for i in range(args.steps):
+        e_i, t_i = oracle_dock_sample(w, args.ref_runs, 1, cores, 2000 + i)
+        ev += e_i
+        t += t_i
+    v = ev / t
+    sample = ("%d runs x %d genotypes x 1 generation (%d evaluations) per step, of the "
+              "20 x 150 x 27-generation dock" % (args.ref_runs, POP, ev // args.steps))
     line = {"metric": "energy+gradient evals/s", "value": v, "unit": "evals/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD + ": 20 runs x 150 genotypes, 32 atoms, 8 torsions, "
-                       "64^3 x 10 maps, 300 ADADELTA steps", "sample_genotypes": n_geno},
+                       "64^3 x (8+2) maps, 27 generations x 300 ADADELTA evaluations",
+                       "sample": sample},
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                             "sample": "%d genotypes x %d steps per step (of 3000 x 300)" % (n_geno, ITERS)},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -177,12 +196,12 @@ def reference_arm(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="adgb", choices=["adgb", "reference"])
     ap.add_argument("--variant", default="shfl")
-    ap.add_argument("--ref-genotypes", type=int, default=400)
-    ap.add_argument("--cpu-genotypes", type=int, default=3000)
+    ap.add_argument("--ref-runs", type=int, default=16)
+    ap.add_argument("--cpu-runs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-variants", action="store_true")
     args = ap.parse_args()
@@ -201,44 +220,46 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    pkg.load(build=(rank == 0 and world == 1))
+    pkg.load(build=(world == 1))
     variant = pkg.VARIANTS[args.variant]
     w = synth.workload(WORKLOAD)
     lig = w["ligand"]
-    n, G = w["genes"].shape
+    n, G = RUNS * POP, 6 + lig["n_tors"]
     ctx = pkg.Context(local_rank)
     rid = ctx.upload_receptor_grids(w["receptor"])
     lid = ctx.upload_ligand_torsion_tree(lig)
-    # a distinct seeded population for every step
-    pops = [synth.make_poses(synth.generate.BASE_SEED + 1000 * (rank + 1) + s, n, w["receptor"],
-                             lig["n_tors"]) for s in range(args.warmup + args.steps)]
-    pops_dev = [torch.from_numpy(p).cuda() for p in pops]
-    genes = torch.empty_like(pops_dev[0])
-    best = torch.empty(n, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    best_g = torch.empty(RUNS, G, device="cuda")
+    best_e = torch.empty(RUNS, dtype=torch.float64, device="cuda")
+    evals = torch.empty(RUNS, dtype=torch.int64, device="cuda")
 
-    def step(i, var):
-        genes.copy_(pops_dev[i])
+    def params(i):
+        # a distinct seed for every step and rank: distinct initial populations
+        return pkg.adgb.dock_params(n_runs=RUNS, pop=POP, max_gens=GENS, max_evals=2_500_000,
+                                    ls_iters=ITERS, ls_rate=1.0, reduce_variant=variant,
+                                    seed=1_000_003 * (rank + 1) + i)
+
+    def step(i):
         flush.fill_(i & 255)                       # evict L2 (256 MiB > 129 MB)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        ctx.local_search_dev(rid, lid, genes, best, ITERS, variant=var)
+        ctx.dock_dev(rid, lid, params(i), best_g, best_e, evals)
         ev1.record(stream)
         return ev0, ev1
 
     evs = []
     with ClockSampler(local_rank) as clk:
-        time.sleep(0.3)                       # let the sampler start
+        time.sleep(0.3)                           # let the sampler start
         for i in range(args.warmup):
-            step(i, variant)
+            step(i)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.steps):
-            evs.append(step(args.warmup + i, variant))
+            evs.append(step(args.warmup + i))
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     if dist:
@@ -246,39 +267,63 @@ def main():
     torch.cuda.synchronize()
     dev_ms = [a.elapsed_time(b) for a, b in evs]
     t_dev = sum(dev_ms) / 1e3
-    assert torch.isfinite(best).all()
+    assert int(evals.sum()) == EVALS_PER_DOCK, int(evals.sum())
+    assert torch.isfinite(best_e).all()
     if dist:
         tt = torch.tensor([t_dev], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev = float(tt.item())
-    evals_rank = args.steps * n * ITERS
+    evals_rank = args.steps * EVALS_PER_DOCK
     value = world * evals_rank / t_dev
 
-    # end to end through the host-buffer C call (pinned host memory)
-    pin_g = [torch.from_numpy(p).pin_memory() for p in pops]
-    pin_e = torch.empty(n, dtype=torch.float32).pin_memory()
+    # end to end through the host C calls of one docking job per step
+    lig_bytes = sum(np.asarray(lig[k]).nbytes for k in ("type", "charge", "xyz", "tors_bond",
+                                                           "mov_off", "mov_atoms", "pairs"))
     for i in range(2):
-        ctx.local_search_host_ptr(rid, lid, pin_g[i].data_ptr(), n, ITERS, pin_e.data_ptr(),
-                                  variant=variant)
+        l2 = ctx.upload_ligand_torsion_tree(lig)
+        ctx.dock(rid, l2, params(10_000 + i))
+        ctx.release_ligand(l2)
     if dist:
         dist.barrier()
-    t0 = time.perf_counter()
+    e2e_ms = []
     for i in range(args.steps):
-        ctx.local_search_host_ptr(rid, lid, pin_g[args.warmup + i].data_ptr(), n, ITERS,
-                                  pin_e.data_ptr(), variant=variant)
-    t_e2e = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        l2 = ctx.upload_ligand_torsion_tree(lig)
+        _, be_h, ev_h = ctx.dock(rid, l2, params(args.warmup + i))
+        ctx.release_ligand(l2)
+        e2e_ms.append(1e3 * (time.perf_counter() - t1))
+    t_e2e = sum(e2e_ms) / 1e3
     if dist:
         tt = torch.tensor([t_e2e], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
     e2e = world * evals_rank / t_e2e
 
+    # the local-search kernel alone, same launch shape as inside dock()
+    g0 = torch.from_numpy(synth.make_poses(7, n, w["receptor"], lig["n_tors"])).cuda()
+    gls = torch.empty_like(g0)
+    bls = torch.empty(n, device="cuda")
+    ls_ms = []
+    for i in range(6):
+        gls.copy_(g0)
+        flush.fill_(i & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.local_search_dev(rid, lid, gls, bls, ITERS, variant=variant)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ls_ms.append(a.elapsed_time(b))
+    ls_ms = ls_ms[1:]
     extra = {}
     if args.compare_variants:
         for name, vv in pkg.VARIANTS.items():
             ms = []
             for i in range(3):
-                a, b = step(i, vv)
+                gls.copy_(g0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.local_search_dev(rid, lid, gls, bls, ITERS, variant=vv)
+                b.record(stream)
                 torch.cuda.synchronize()
                 ms.append(a.elapsed_time(b))
             extra[name] = n * ITERS / (min(ms) / 1e3)
@@ -287,9 +332,8 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    # roofline of the local-search kernel (one launch per step)
     fl = eval_flops(lig)
-    launch_s = t_dev / args.steps
+    launch_s = statistics.mean(ls_ms) / 1e3
     achieved = n * ITERS * fl / launch_s / 1e12
     clocks = clk.summary()
     peak = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
@@ -299,32 +343,39 @@ def main():
         import oracle
         oracle.build()
         cores = os.cpu_count() or 1
-        t = run_oracle_sample(w, args.cpu_genotypes, cores)
-        cpu = {"value": args.cpu_genotypes * ITERS / t, "unit": "evals/s", "cores": cores,
-               "kind": "oracle",
-               "sample": "%d of the 3000 genotypes x %d ADADELTA steps, FP64, OpenMP" % (args.cpu_genotypes, ITERS)}
+        ev_c, t_c = oracle_dock_sample(w, args.cpu_runs, 1, cores, 77)
+        cpu = {"value": ev_c / t_c, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle dock of %d runs x %d genotypes x 1 generation (%d "
+                         "evaluations), OpenMP over runs" % (args.cpu_runs, POP, ev_c)}
+    q = lambda v, p: float(np.percentile(v, p))
     line = {
         "metric": "energy+gradient evals/s", "value": value, "unit": "evals/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD + ": 20 runs x 150 genotypes of a 32-atom, 8-torsion, "
-                   "%d-pair ligand, 64^3 grid x 10 maps, 300 ADADELTA steps" % len(lig["pairs"]),
-                   "genotypes_per_gpu": n, "ls_iters": ITERS, "reduce_variant": args.variant,
+        "config": {"workload": WORKLOAD + ": dock of 20 runs x 150 genotypes, 32-atom 8-torsion "
+                   "%d-pair ligand, 64^3 x (8+2) maps, 27 generations x 300 ADADELTA "
+                   "evaluations, FP64 rescoring" % len(lig["pairs"]),
+                   "evals_per_step": EVALS_PER_DOCK, "reduce_variant": args.variant,
                    "l2": "flushed between steps (256 MiB write), flush not timed",
-                   "poses_per_s": world * args.steps * n / t_dev,
+                   "dock_latency_ms": {"p50": q(dev_ms, 50), "p99": q(dev_ms, 99)},
+                   "e2e_dock_latency_ms": {"p50": q(e2e_ms, 50), "p99": q(e2e_ms, 99)},
+                   "poses_per_s": world * args.steps * RUNS * POP * GENS / t_dev,
+                   "ls_kernel_evals_per_s": n * ITERS / launch_s,
                    "wall_s_timed_region": wall},
-        "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": n * G * 4,
-                "d2h_bytes_per_step": n * G * 4 + n * 4},
-        "gpu_launches": args.steps,
+        "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": int(lig_bytes),
+                "d2h_bytes_per_step": RUNS * (G * 4 + 8 + 8)},
+        "gpu_launches": args.steps * LAUNCHES_PER_DOCK,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "flops_per_eval": fl, "peak_basis": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 x 2070 MHz"},
+                     "kernel": "eval_kernel (local search, 3000 genotypes x 300 evaluations)",
+                     "flops_per_eval": fl,
+                     "peak_basis": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
     if extra:
-        line["variants_evals_per_s"] = extra
+        line["variants_ls_evals_per_s"] = extra
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
