@@ -292,6 +292,41 @@ int rescore_fp64_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, const float 
                      int n, double *energy_dev, adgb_stream stream);
 
 /*
+ * Uneven batches: genotypes of many ligands (of different atom, torsion and
+ * pair counts), each against its own receptor, locally searched by ONE
+ * persistent multi-ligand launch.  Blocks take work items (up to
+ * poses-per-block genotypes of one ligand, longest first) from a device
+ * counter, so big and small ligands share the GPU without stragglers.  The
+ * launch is captured into a CUDA graph on the first call and replayed by
+ * later calls with the same buffers and parameters.
+ *
+ * batch_create - item i: n_poses[i] genotypes of ligand ligand_ids[i]
+ *   against receptor receptor_ids[i].  Genotypes of item i occupy rows
+ *   [off_i, off_i + n_poses[i]) of a [total][ADGB_MAX_GENES] float32 array
+ *   (the first 6 + T_i entries of a row are used), off_i = sum of n_poses[j]
+ *   over j < i.  The batch refers to the ligands and receptors: release the
+ *   batch before them.  Errors: EINVAL, ENOTFOUND, ENOMEM.
+ * batch_autotune - times the candidate launch shapes (32, 64 or 128 threads
+ *   a genotype; poses per block; reduction variant) on this batch with
+ *   `iters` evaluations per genotype from genes_dev (read on the context's
+ *   own stream after the caller's work is complete; not modified), keeps the
+ *   fastest for this batch and for later batches of the same size class
+ *   (largest ligand in 32-atom and 512-pair steps), and writes it to chosen
+ *   (may be NULL).  Synchronous.
+ * batch_local_search_dev - local_search over every genotype of the batch:
+ *   genes [total][ADGB_MAX_GENES] in/out, best_energy [total] out, on
+ *   `stream`.  p->flags must not ask for resume.
+ */
+#define ADGB_MAX_GENES (6 + ADGB_MAX_TORS)
+int batch_create(adgb_ctx *ctx, int n_items, const int *receptor_ids, const int *ligand_ids,
+                 const int *n_poses, int *batch_id);
+int batch_autotune(adgb_ctx *ctx, int batch_id, const float *genes_dev, int iters,
+                   adgb_options *chosen);
+int batch_local_search_dev(adgb_ctx *ctx, int batch_id, float *genes_dev,
+                           const adgb_ls_params *p, float *best_energy_dev, adgb_stream stream);
+int batch_release(adgb_ctx *ctx, int batch_id);
+
+/*
  * reduce4_bench_dev - the reduction test kernel of Sec. 5.2: every thread
  * of a block holds one four-element vector, the block computes the sum and
  * every thread receives it.  in [n_blocks][threads][4] float32, out the same

@@ -32,7 +32,9 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
            "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev",
-           "dock_noalloc_dev"]
+           "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
+           "batch_release"]
+MAX_GENES = 46
 
 
 class AdgbError(RuntimeError):
@@ -123,6 +125,10 @@ def load(build: bool = False):
     L.dock_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.dock.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp]
     L.rescore_fp64_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp]
+    L.batch_create.argtypes = [vp, C.c_int, vp, vp, vp, C.POINTER(C.c_int)]
+    L.batch_autotune.argtypes = [vp, C.c_int, vp, C.c_int, C.POINTER(_Options)]
+    L.batch_local_search_dev.argtypes = [vp, C.c_int, vp, C.POINTER(_LSParams), vp, vp]
+    L.batch_release.argtypes = [vp, C.c_int]
     L.dock_noalloc_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.ga_init_population_dev.argtypes = [vp, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int,
                                          vp, vp]
@@ -282,6 +288,32 @@ class Context:
         (no allocation during the call)."""
         self._chk(self.lib.dock_noalloc_dev(self.h, rid, lid, C.byref(params), _ptr(best_genes),
                                             _ptr(best_energy), _ptr(evals), _stream()))
+
+    def batch_create(self, receptor_ids, ligand_ids, n_poses) -> int:
+        r, l, n = _i32(receptor_ids), _i32(ligand_ids), _i32(n_poses)
+        bid = C.c_int()
+        self._chk(self.lib.batch_create(self.h, len(n), r.ctypes.data, l.ctypes.data, n.ctypes.data,
+                                        C.byref(bid)))
+        return bid.value
+
+    def batch_autotune(self, bid, genes, iters=20):
+        _check_dev(genes, "genes")
+        import torch
+        torch.cuda.current_stream().synchronize()
+        o = _Options()
+        self._chk(self.lib.batch_autotune(self.h, bid, _ptr(genes), iters, C.byref(o)))
+        return dict(threads_per_pose=o.threads_per_pose, poses_per_block=o.poses_per_block,
+                    reduce_variant=o.reduce_variant)
+
+    def batch_local_search_dev(self, bid, genes, best_energy, iters, rho=0.8, eps=1e-2, variant=-1):
+        _check_dev(genes, "genes")
+        _check_dev(best_energy, "best_energy")
+        p = _LSParams(int(iters), float(rho), float(eps), int(variant), 0)
+        self._chk(self.lib.batch_local_search_dev(self.h, bid, _ptr(genes), C.byref(p),
+                                                  _ptr(best_energy), _stream()))
+
+    def batch_release(self, bid):
+        self._chk(self.lib.batch_release(self.h, bid))
 
     def rescore_fp64_dev(self, rid, lid, genes, energy):
         _check_dev(genes, "genes")

@@ -114,6 +114,37 @@ struct SmemLayout {
         pose_stride = q;
         total = pose0 + ppb * pose_stride;
     }
+
+    // Layout of one ligand inside a block of `budget` bytes of dynamic shared
+    // memory: the pair list and incidence lists are staged when they take at
+    // most 24 KB, and the pair-force buffer takes what is left (at most 4096
+    // pairs a chunk).  The same rule runs on the host (to size a launch) and
+    // on the device (per work item of the multi-ligand kernel).
+    static __host__ __device__ inline SmemLayout choose(int N, int T, int np, int ppb,
+                                                        int warps_per_pose, int budget) {
+        SmemLayout l;
+        const bool stage = 8 * np <= 24 * 1024;
+        l.make(N, T, ppb, warps_per_pose, 1, np, stage);
+        int room = (budget - (l.total - ppb * 16)) / (ppb * 16);
+        int ch = np < room ? np : room;
+        ch = ch < 4096 ? ch : 4096;
+        ch = ch > 1 ? ch : 1;
+        l.make(N, T, ppb, warps_per_pose, ch, np, stage);
+        return l;
+    }
+};
+
+// Work item of the multi-ligand local-search kernel: up to poses-per-block
+// genotypes of one ligand against one receptor.
+struct WorkItem {
+    int lig, rec;          // indices into the launch's ligand / receptor tables
+    int count;             // genotypes in this item
+    int gstride;           // floats between consecutive genotypes
+    float *genes;          // first genotype (in: start, out: best)
+    float *energy;         // first best energy
+    const int *iters;      // per-genotype evaluation counts, or null
+    int iters_all;         // evaluation count when iters is null
+    int cost;              // ordering key (host side)
 };
 
 // Launch configuration of the fused kernel.
@@ -142,6 +173,12 @@ cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *
                                  const float *energy, float *genes_out, int *iters, cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
                           cudaStream_t s);
+// Persistent multi-ligand local search over a device table of work items
+// (counter zeroed by the launch itself, so the launch can be replayed).
+cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *ligs,
+                              const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
+                              float rho, float eps, int grid, cudaStream_t s);
+int items_grid(const EvalCfg &cfg, int budget, int device);
 cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M,
                              float *cells, cudaStream_t s);
 cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int n_blocks,

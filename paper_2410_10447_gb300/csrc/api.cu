@@ -31,11 +31,38 @@ struct Ligand {
 
 }  // namespace
 
+namespace {
+// An uneven batch: items of (receptor, ligand, genotype count) run by one
+// persistent multi-ligand launch replayed from a captured CUDA graph.
+struct Batch {
+    std::vector<int> rec_idx, lig_idx, n_poses;  // per item, indices into the tables
+    std::vector<LigDev> ligs;                    // unique ligands
+    std::vector<RecDev> recs;                    // unique receptors
+    std::vector<int> lig_n, lig_t, lig_np;       // sizes of the unique ligands
+    long long total = 0;
+    LigDev *d_ligs = nullptr;
+    RecDev *d_recs = nullptr;
+    int *d_counter = nullptr;                    // [2], re-armed by the kernel
+    WorkItem *d_items = nullptr;
+    int items_cap = 0, n_items = 0;
+    EvalCfg cfg{32, 4, 0, 1, 0};
+    bool tuned = false;
+    cudaGraphExec_t exec = nullptr;
+    // what the captured graph was built for
+    const float *k_genes = nullptr;
+    const float *k_energy = nullptr;
+    int k_iters = -1, k_tpp = 0, k_ppb = 0, k_var = -1, budget = 0, grid = 0;
+    float k_rho = 0.f, k_eps = 0.f;
+};
+}  // namespace
+
 struct adgb_ctx {
     int device = 0;
     adgb_options opts{};
     std::map<int, Receptor> recs;
     std::map<int, Ligand> ligs;
+    std::map<int, Batch> batches;
+    std::map<long long, EvalCfg> tune_table;  // autotuned launch shape by size bucket
     int next_id = 1;
     std::string err;
     cudaStream_t stream = nullptr;  // used by the host-pointer calls
@@ -405,6 +432,14 @@ int adgb_destroy(adgb_ctx *c) {
     if (!c) return ADGB_EINVAL;
     {
         DeviceGuard g(c->device);
+        for (auto &kv : c->batches) {
+            Batch &b = kv.second;
+            if (b.exec) cudaGraphExecDestroy(b.exec);
+            cudaFree(b.d_ligs);
+            cudaFree(b.d_recs);
+            cudaFree(b.d_counter);
+            cudaFree(b.d_items);
+        }
         for (auto &kv : c->recs) cudaFree(kv.second.cells);
         for (auto &kv : c->ligs) cudaFree(kv.second.mem);
         if (c->stage) cudaFree(c->stage);
@@ -964,4 +999,262 @@ extern "C" int dock_noalloc_dev(adgb_ctx *c, int receptor_id, int ligand_id,
     e = launch_dock(R->dev, L->dev, pick_cfg(c, *L, variant), d, best_genes_dev, best_energy_dev,
                     evals_dev, w, (cudaStream_t)stream);
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "dock_noalloc");
+}
+
+
+// ---------------------------------------------------------------------------
+// Uneven batches (one persistent multi-ligand launch, graph-captured, tuned)
+// ---------------------------------------------------------------------------
+namespace {
+
+int batch_budget(const Batch &b, const EvalCfg &cfg) {
+    int budget = 0;
+    for (size_t u = 0; u < b.ligs.size(); u++) {
+        SmemLayout l;
+        const bool stage = 8 * b.lig_np[u] <= 24 * 1024;
+        l.make(b.lig_n[u], b.lig_t[u], cfg.ppb, cfg.tpp / 32, 1, b.lig_np[u], stage);
+        const int fixed = l.total - cfg.ppb * 16;
+        const int want = fixed + cfg.ppb * 16 * std::max(1, std::min(b.lig_np[u], 1024));
+        budget = std::max(budget, want);
+    }
+    return std::min(std::max(budget, 1024), 200 * 1024);
+}
+
+// Items of ppb genotypes of one ligand, longest (most work) first.
+std::vector<WorkItem> batch_items(const Batch &b, const EvalCfg &cfg, float *genes, float *energy,
+                                  int iters) {
+    std::vector<WorkItem> items;
+    long long row = 0;
+    for (size_t i = 0; i < b.n_poses.size(); i++) {
+        const int u = b.lig_idx[i];
+        const int cost = (int)std::min<long long>(INT32_MAX, (long long)(b.lig_np[u] + 8 * b.lig_n[u] + 64));
+        for (int k = 0; k < b.n_poses[i]; k += cfg.ppb) {
+            WorkItem w;
+            w.lig = u;
+            w.rec = b.rec_idx[i];
+            w.count = std::min(cfg.ppb, b.n_poses[i] - k);
+            w.gstride = 6 + ADGB_MAX_TORS;
+            w.genes = genes + (row + k) * (long long)(6 + ADGB_MAX_TORS);
+            w.energy = energy + row + k;
+            w.iters = nullptr;
+            w.iters_all = iters;
+            w.cost = cost;
+            items.push_back(w);
+        }
+        row += b.n_poses[i];
+    }
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem &x, const WorkItem &y) {
+        return x.cost > y.cost || (x.cost == y.cost && x.lig < y.lig);
+    });
+    return items;
+}
+
+cudaError_t upload_items(Batch &b, const std::vector<WorkItem> &items, cudaStream_t s) {
+    if ((int)items.size() > b.items_cap) {
+        if (b.d_items) cudaFree(b.d_items);
+        b.d_items = nullptr;
+        cudaError_t e = cudaMalloc(&b.d_items, sizeof(WorkItem) * std::max<size_t>(items.size(), 1));
+        if (e != cudaSuccess) return e;
+        b.items_cap = (int)items.size();
+    }
+    b.n_items = (int)items.size();
+    cudaError_t e = cudaMemcpyAsync(b.d_items, items.data(), sizeof(WorkItem) * items.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+}
+
+long long tune_key(const Batch &b) {
+    int n = 0, np = 0;
+    for (size_t u = 0; u < b.ligs.size(); u++) {
+        n = std::max(n, b.lig_n[u]);
+        np = std::max(np, b.lig_np[u]);
+    }
+    return ((long long)((n + 31) / 32) << 32) | (long long)((np + 511) / 512);
+}
+
+}  // namespace
+
+extern "C" int batch_create(adgb_ctx *c, int n_items, const int *receptor_ids, const int *ligand_ids,
+                            const int *n_poses, int *batch_id) {
+    if (!c) return ADGB_EINVAL;
+    if (n_items < 1 || !receptor_ids || !ligand_ids || !n_poses || !batch_id)
+        return fail(c, ADGB_EINVAL, "batch_create: bad arguments");
+    Batch b;
+    std::map<int, int> lmap, rmap;
+    for (int i = 0; i < n_items; i++) {
+        if (n_poses[i] < 0) return fail(c, ADGB_EINVAL, "batch_create: item %d has %d genotypes", i, n_poses[i]);
+        Receptor *R = nullptr;
+        Ligand *L = nullptr;
+        int rc = lookup(c, receptor_ids[i], ligand_ids[i], &R, &L);
+        if (rc) return rc;
+        if (!lmap.count(ligand_ids[i])) {
+            lmap[ligand_ids[i]] = (int)b.ligs.size();
+            b.ligs.push_back(L->dev);
+            b.lig_n.push_back(L->n_atoms);
+            b.lig_t.push_back(L->n_tors);
+            b.lig_np.push_back(L->n_pairs);
+        }
+        if (!rmap.count(receptor_ids[i])) {
+            rmap[receptor_ids[i]] = (int)b.recs.size();
+            b.recs.push_back(R->dev);
+        }
+        b.lig_idx.push_back(lmap[ligand_ids[i]]);
+        b.rec_idx.push_back(rmap[receptor_ids[i]]);
+        b.n_poses.push_back(n_poses[i]);
+        b.total += n_poses[i];
+    }
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaMalloc(&b.d_ligs, sizeof(LigDev) * b.ligs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_recs, sizeof(RecDev) * b.recs.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b.d_counter, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b.d_ligs, b.ligs.data(), sizeof(LigDev) * b.ligs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b.d_recs, b.recs.data(), sizeof(RecDev) * b.recs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b.d_counter, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(b.d_ligs);
+        cudaFree(b.d_recs);
+        cudaFree(b.d_counter);
+        return fail(c, ADGB_ENOMEM, "batch_create: %s", cudaGetErrorString(e));
+    }
+    b.cfg.variant = c->opts.reduce_variant;
+    auto it = c->tune_table.find(tune_key(b));
+    if (it != c->tune_table.end()) {
+        b.cfg = it->second;
+        b.tuned = true;
+    }
+    const int id = c->next_id++;
+    c->batches[id] = std::move(b);
+    *batch_id = id;
+    return ADGB_OK;
+}
+
+extern "C" int batch_release(adgb_ctx *c, int batch_id) {
+    if (!c) return ADGB_EINVAL;
+    auto it = c->batches.find(batch_id);
+    if (it == c->batches.end()) return fail(c, ADGB_ENOTFOUND, "unknown batch id %d", batch_id);
+    DeviceGuard g(c->device);
+    Batch &b = it->second;
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    cudaFree(b.d_ligs);
+    cudaFree(b.d_recs);
+    cudaFree(b.d_counter);
+    cudaFree(b.d_items);
+    c->batches.erase(it);
+    return ADGB_OK;
+}
+
+extern "C" int batch_local_search_dev(adgb_ctx *c, int batch_id, float *genes_dev,
+                                      const adgb_ls_params *p, float *best_energy_dev,
+                                      adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant, rc = check_ls(c, p, variant);
+    if (rc) return rc;
+    if (p->flags & ADGB_LS_RESUME) return fail(c, ADGB_EINVAL, "batch_local_search: resume is not supported");
+    auto it = c->batches.find(batch_id);
+    if (it == c->batches.end()) return fail(c, ADGB_ENOTFOUND, "unknown batch id %d", batch_id);
+    Batch &b = it->second;
+    if (b.total > 0 && (!genes_dev || !best_energy_dev)) return fail(c, ADGB_EINVAL, "batch_local_search: null buffers");
+    if (b.total == 0) return ADGB_OK;
+    DeviceGuard g(c->device);
+    EvalCfg cfg = b.cfg;
+    if (!b.tuned || p->reduce_variant >= 0) cfg.variant = variant;
+    cudaError_t e = cudaSuccess;
+    const bool same = b.exec && b.k_genes == genes_dev && b.k_energy == best_energy_dev &&
+                      b.k_iters == p->iters && b.k_rho == p->rho && b.k_eps == p->eps &&
+                      b.k_tpp == cfg.tpp && b.k_ppb == cfg.ppb && b.k_var == cfg.variant;
+    if (!same) {
+        if (b.exec) cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+        b.budget = batch_budget(b, cfg);
+        b.grid = items_grid(cfg, b.budget, c->device);
+        if (b.grid < 1) return fail(c, ADGB_EINVAL, "batch_local_search: launch shape does not fit an SM");
+        e = upload_items(b, batch_items(b, cfg, genes_dev, best_energy_dev, p->iters), c->stream);
+        cudaGraph_t graph = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = launch_eval_items(b.d_items, b.n_items, b.d_ligs, b.d_recs, b.d_counter,
+                                               cfg, b.budget, p->rho, p->eps, b.grid, c->stream);
+            e = cudaStreamEndCapture(c->stream, &graph);
+            if (el != cudaSuccess) e = el;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batch_local_search: graph capture");
+        b.k_genes = genes_dev;
+        b.k_energy = best_energy_dev;
+        b.k_iters = p->iters;
+        b.k_rho = p->rho;
+        b.k_eps = p->eps;
+        b.k_tpp = cfg.tpp;
+        b.k_ppb = cfg.ppb;
+        b.k_var = cfg.variant;
+    }
+    e = cudaGraphLaunch(b.exec, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "batch_local_search: graph launch");
+}
+
+extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev, int iters,
+                              adgb_options *chosen) {
+    if (!c) return ADGB_EINVAL;
+    auto it = c->batches.find(batch_id);
+    if (it == c->batches.end()) return fail(c, ADGB_ENOTFOUND, "unknown batch id %d", batch_id);
+    Batch &b = it->second;
+    if (iters < 1 || (b.total > 0 && !genes_dev)) return fail(c, ADGB_EINVAL, "batch_autotune: bad arguments");
+    DeviceGuard g(c->device);
+    const EvalCfg cands[] = {{32, 4, ADGB_REDUCE_SHFL, 1, 0}, {32, 4, ADGB_REDUCE_MMA_TF32X2, 1, 0},
+                             {32, 4, ADGB_REDUCE_MMA_BF16X3, 1, 0}, {32, 2, ADGB_REDUCE_SHFL, 1, 0},
+                             {64, 2, ADGB_REDUCE_SHFL, 1, 0}, {128, 1, ADGB_REDUCE_SHFL, 1, 0}};
+    const size_t gbytes = sizeof(float) * (size_t)b.total * (6 + ADGB_MAX_TORS);
+    float *tg = nullptr, *te = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&tg, gbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&te, sizeof(float) * (size_t)b.total);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best_ms = INFINITY;
+    EvalCfg best{};
+    for (const EvalCfg &cfg : cands) {
+        if (e != cudaSuccess) break;
+        const int budget = batch_budget(b, cfg);
+        const int grid = items_grid(cfg, budget, c->device);
+        if (grid < 1) continue;
+        float ms_min = INFINITY;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
+            e = cudaMemcpyAsync(tg, genes_dev, gbytes, cudaMemcpyDeviceToDevice, c->stream);
+            if (e == cudaSuccess) e = upload_items(b, batch_items(b, cfg, tg, te, iters), c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            if (e == cudaSuccess)
+                e = launch_eval_items(b.d_items, b.n_items, b.d_ligs, b.d_recs, b.d_counter, cfg, budget,
+                                      0.8f, 1e-2f, grid, c->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        if (e == cudaSuccess && ms_min < best_ms) {
+            best_ms = ms_min;
+            best = cfg;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(tg);
+    cudaFree(te);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch_autotune");
+    if (!(best_ms < INFINITY)) return fail(c, ADGB_EINVAL, "batch_autotune: no launch shape fits");
+    b.cfg = best;
+    b.tuned = true;
+    if (b.exec) {
+        cudaGraphExecDestroy(b.exec);
+        b.exec = nullptr;
+    }
+    c->tune_table[tune_key(b)] = best;
+    if (chosen) {
+        chosen->threads_per_pose = best.tpp;
+        chosen->poses_per_block = best.ppb;
+        chosen->reduce_variant = best.variant;
+    }
+    return ADGB_OK;
 }

@@ -186,29 +186,45 @@ __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage,
 #define ADGB_MIN_BLOCKS 5
 #endif
 
-template <int TPP, int VAR>
-__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const LigDev &lig = a.lig;
-    const RecDev &rec = a.rec;
-    const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
-    float4 *s_ref = reinterpret_cast<float4 *>(sm + a.L.ref);
-    float2 *s_sv = reinterpret_cast<float2 *>(sm + a.L.sv);
-    int *s_type = reinterpret_cast<int *>(sm + a.L.type);
-    int *s_frag = reinterpret_cast<int *>(sm + a.L.frag);
-    int *s_tpar = reinterpret_cast<int *>(sm + a.L.tparent);
-    int4 *s_tat = reinterpret_cast<int4 *>(sm + a.L.tatoms);
-    float4 *s_tax = reinterpret_cast<float4 *>(sm + a.L.taxis);
-    float4 *s_tb = reinterpret_cast<float4 *>(sm + a.L.tbref);
-    float2 *s_tab = reinterpret_cast<float2 *>(sm + a.L.tptab);
-    int *s_incoff = reinterpret_cast<int *>(sm + a.L.incoff);
+// Per-genotype inputs and outputs of search_pose (pointers at that genotype).
+struct PoseIO {
+    const float *genes_in;  // [G] start genotype (unused with resume)
+    float *genes_out;       // [G] best genotype (local search)
+    float *energy;          // [1] energy (score) or best energy (local search)
+    float *grad;            // [G] gene gradient (score) or null
+    float *state;           // [3][G] (Omega, E[g^2], E[d^2]) or null
+    int iters, mode, resume;
+    float rho, eps;
+};
+
+// Where the pair list and incidence lists are read from (shared or global).
+struct StagedLig {
+    const uint32_t *prs;
+    const uint16_t *incl;
+};
+
+// Copies one ligand's constants into shared memory (all threads of the
+// block; the caller synchronises before the first use).
+__device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemLayout &L,
+                                                  const LigDev &lig) {
+    const int N = lig.n_atoms, T = lig.n_tors, NP = lig.n_pairs;
+    float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
+    float2 *s_sv = reinterpret_cast<float2 *>(sm + L.sv);
+    int *s_type = reinterpret_cast<int *>(sm + L.type);
+    int *s_frag = reinterpret_cast<int *>(sm + L.frag);
+    int *s_tpar = reinterpret_cast<int *>(sm + L.tparent);
+    int4 *s_tat = reinterpret_cast<int4 *>(sm + L.tatoms);
+    float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
+    float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
+    float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
+    int *s_incoff = reinterpret_cast<int *>(sm + L.incoff);
     for (int i = threadIdx.x; i <= N; i += blockDim.x) s_incoff[i] = lig.inc_off[i];
     // pair records and incidence lists: shared memory when they fit
     const uint32_t *prs = lig.pairs;
     const uint16_t *incl = lig.inc;
-    if (a.L.pairs_in_smem) {
-        uint32_t *sp = reinterpret_cast<uint32_t *>(sm + a.L.spairs);
-        uint16_t *si = reinterpret_cast<uint16_t *>(sm + a.L.sinc);
+    if (L.pairs_in_smem) {
+        uint32_t *sp = reinterpret_cast<uint32_t *>(sm + L.spairs);
+        uint16_t *si = reinterpret_cast<uint16_t *>(sm + L.sinc);
         for (int p = threadIdx.x; p < NP; p += blockDim.x) sp[p] = lig.pairs[p];
         for (int p = threadIdx.x; p < 2 * NP; p += blockDim.x) si[p] = lig.inc[p];
         prs = sp;
@@ -227,21 +243,38 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
         s_tb[k] = lig.tbref[k];
     }
     for (int k = threadIdx.x; k < TYPE_TAB; k += blockDim.x) s_tab[k] = lig.tptab[k];
-    __syncthreads();
+    return {prs, incl};
+}
 
-    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
-    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
-    if (pose >= a.n) return;
-    unsigned char *P = sm + a.L.pose0 + group * a.L.pose_stride;
-    float4 *xyz = reinterpret_cast<float4 *>(P + a.L.p_xyz);
-    float4 *grd = reinterpret_cast<float4 *>(P + a.L.p_grad);
-    float *genes_s = reinterpret_cast<float *>(P + a.L.p_genes);
-    float *ggrad = reinterpret_cast<float *>(P + a.L.p_ggrad);
-    float2 *sc = reinterpret_cast<float2 *>(P + a.L.p_sc);
-    float *red = reinterpret_cast<float *>(P + a.L.p_red);
-    float *stage = reinterpret_cast<float *>(P + a.L.p_stage) + (gt >> 5) * 32 * 12;
-    float4 *fbuf = reinterpret_cast<float4 *>(P + a.L.p_force);
-    const int CH = a.L.chunk;
+// Whole evaluation loop of one genotype by one pose group (TPP threads).
+template <int TPP, int VAR>
+__device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout &L,
+                                            const LigDev &lig, const RecDev &rec,
+                                            const StagedLig &sl, const int group, const int gt,
+                                            const PoseIO &io) {
+    const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
+    float2 *s_sv = reinterpret_cast<float2 *>(sm + L.sv);
+    float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
+    int *s_type = reinterpret_cast<int *>(sm + L.type);
+    int *s_frag = reinterpret_cast<int *>(sm + L.frag);
+    int *s_tpar = reinterpret_cast<int *>(sm + L.tparent);
+    int4 *s_tat = reinterpret_cast<int4 *>(sm + L.tatoms);
+    float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
+    float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
+    float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
+    int *s_incoff = reinterpret_cast<int *>(sm + L.incoff);
+    const uint32_t *prs = sl.prs;
+    const uint16_t *incl = sl.incl;
+    unsigned char *P = sm + L.pose0 + group * L.pose_stride;
+    float4 *xyz = reinterpret_cast<float4 *>(P + L.p_xyz);
+    float4 *grd = reinterpret_cast<float4 *>(P + L.p_grad);
+    float *genes_s = reinterpret_cast<float *>(P + L.p_genes);
+    float *ggrad = reinterpret_cast<float *>(P + L.p_ggrad);
+    float2 *sc = reinterpret_cast<float2 *>(P + L.p_sc);
+    float *red = reinterpret_cast<float *>(P + L.p_red);
+    float *stage = reinterpret_cast<float *>(P + L.p_stage) + (gt >> 5) * 32 * 12;
+    float4 *fbuf = reinterpret_cast<float4 *>(P + L.p_force);
+    const int CH = L.chunk;
     constexpr int MAXA = ADGB_MAX_ATOMS / TPP;  // atoms owned per thread, at most
 
     constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
@@ -251,19 +284,19 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
         const int j = gt + r * TPP;
         om[r] = eg2[r] = ed2[r] = 0.f;
         if (j < G) {
-            if (a.resume) {
-                const float *st = a.state + (size_t)pose * 3 * G;
+            if (io.resume) {
+                const float *st = io.state;
                 om[r] = st[j];
                 eg2[r] = st[G + j];
                 ed2[r] = st[2 * G + j];
             } else {
-                om[r] = a.genes_in[(size_t)pose * G + j];
+                om[r] = io.genes_in[j];
             }
         }
         best[r] = om[r];
     }
     float best_e = INFINITY;
-    const int iters = a.mode == MODE_SCORE ? 1 : (a.iters_pp ? a.iters_pp[pose] : a.iters);
+    const int iters = io.iters;
 
     for (int it = 0; it < iters; it++) {
         // 1. publish genes, sin and 1 - cos of every angle (half-angle form:
@@ -475,13 +508,13 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
             }
             gj[r] = g;
         }
-        if (a.mode == MODE_SCORE) {
-            if (gt == 0) a.energy[pose] = E;
-            if (a.grad) {
+        if (io.mode == MODE_SCORE) {
+            if (gt == 0) io.energy[0] = E;
+            if (io.grad) {
 #pragma unroll
                 for (int r = 0; r < NG; r++) {
                     const int j = gt + r * TPP;
-                    if (j < G) a.grad[(size_t)pose * G + j] = gj[r];
+                    if (j < G) io.grad[j] = gj[r];
                 }
             }
             return;
@@ -496,30 +529,176 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
             const int j = gt + r * TPP;
             if (j < G) {
                 const float g = gj[r];
-                eg2[r] = a.rho * eg2[r] + (1.f - a.rho) * g * g;
-                const float d = -sqrtf(ed2[r] + a.eps) * rsqrtf(eg2[r] + a.eps) * g;
-                ed2[r] = a.rho * ed2[r] + (1.f - a.rho) * d * d;
+                eg2[r] = io.rho * eg2[r] + (1.f - io.rho) * g * g;
+                const float d = -sqrtf(ed2[r] + io.eps) * rsqrtf(eg2[r] + io.eps) * g;
+                ed2[r] = io.rho * ed2[r] + (1.f - io.rho) * d * d;
                 float w = om[r] + d;
                 if (j >= 6) w -= 2.f * PI_F * floorf((w + PI_F) * (0.5f / PI_F));
                 om[r] = w;
             }
         }
     }
-    if (a.mode == MODE_SCORE) return;  // iters == 0 never reaches here in score mode
+    if (io.mode == MODE_SCORE) return;  // iters == 0 never reaches here in score mode
 #pragma unroll
     for (int r = 0; r < NG; r++) {
         const int j = gt + r * TPP;
         if (j < G) {
-            a.genes_out[(size_t)pose * G + j] = best[r];
-            if (a.state) {
-                float *st = a.state + (size_t)pose * 3 * G;
+            io.genes_out[j] = best[r];
+            if (io.state) {
+                float *st = io.state;
                 st[j] = om[r];
                 st[G + j] = eg2[r];
                 st[2 * G + j] = ed2[r];
             }
         }
     }
-    if (gt == 0) a.energy[pose] = best_e;
+    if (gt == 0) io.energy[0] = best_e;
+}
+
+template <int TPP, int VAR>
+__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const StagedLig sl = stage_ligand(sm, a.L, a.lig);
+    __syncthreads();
+    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
+    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
+    if (pose >= a.n) return;
+    const int G = 6 + a.lig.n_tors;
+    PoseIO io;
+    io.genes_in = a.genes_in ? a.genes_in + (size_t)pose * G : nullptr;
+    io.genes_out = a.genes_out ? a.genes_out + (size_t)pose * G : nullptr;
+    io.energy = a.energy + pose;
+    io.grad = a.grad ? a.grad + (size_t)pose * G : nullptr;
+    io.state = a.state ? a.state + (size_t)pose * 3 * G : nullptr;
+    io.iters = a.mode == MODE_SCORE ? 1 : (a.iters_pp ? a.iters_pp[pose] : a.iters);
+    io.mode = a.mode;
+    io.resume = a.resume;
+    io.rho = a.rho;
+    io.eps = a.eps;
+    search_pose<TPP, VAR>(sm, a.L, a.lig, a.rec, sl, group, gt, io);
+}
+
+// Persistent multi-ligand local search: every block takes work items from a
+// device counter until the table is exhausted; a block re-stages the ligand
+// constants only when the item's ligand differs from its previous one.
+// Items are ordered by decreasing cost on the host (longest first).
+struct ItemsArgs {
+    const WorkItem *items;
+    const LigDev *ligs;
+    const RecDev *recs;
+    int *counter;
+    int n_items, ppb, budget;
+    float rho, eps;
+};
+
+template <int TPP, int VAR>
+__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const ItemsArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_item;
+    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
+    int cur_lig = -1;
+    SmemLayout L;
+    StagedLig sl;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= a.n_items) break;
+        const WorkItem w = a.items[it];
+        if (w.lig != cur_lig) {
+            const LigDev &lg = a.ligs[w.lig];
+            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32, a.budget);
+            sl = stage_ligand(sm, L, lg);
+            cur_lig = w.lig;
+            __syncthreads();
+        }
+        if (group < w.count) {
+            PoseIO io;
+            io.genes_in = w.genes + (size_t)group * w.gstride;
+            io.genes_out = w.genes + (size_t)group * w.gstride;
+            io.energy = w.energy + group;
+            io.grad = nullptr;
+            io.state = nullptr;
+            io.iters = w.iters ? w.iters[group] : w.iters_all;
+            io.mode = MODE_LS;
+            io.resume = 0;
+            io.rho = a.rho;
+            io.eps = a.eps;
+            search_pose<TPP, VAR>(sm, L, a.ligs[w.lig], a.recs[w.rec], sl, group, gt, io);
+        }
+        __syncthreads();  // the item is done before smem or s_item change
+    }
+    // the last block out re-arms the counter so that the launch can be replayed
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int done = atomicAdd(a.counter + 1, 1);
+        if (done == (int)gridDim.x - 1) {
+            a.counter[0] = 0;
+            a.counter[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+template <int TPP, int VAR>
+static cudaError_t launch_items_t(const ItemsArgs &a, int grid, cudaStream_t s) {
+    auto k = eval_items_kernel<TPP, VAR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.budget);
+    if (e != cudaSuccess) return e;
+    k<<<grid, TPP * a.ppb, a.budget, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPP>
+static cudaError_t launch_items_v(const ItemsArgs &a, int variant, int grid, cudaStream_t s) {
+    switch (variant) {
+        case ADGB_REDUCE_SHFL: return launch_items_t<TPP, ADGB_REDUCE_SHFL>(a, grid, s);
+        case ADGB_REDUCE_MMA_TF32X2: return launch_items_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, grid, s);
+        case ADGB_REDUCE_MMA_BF16X3: return launch_items_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *ligs,
+                              const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
+                              float rho, float eps, int grid, cudaStream_t s) {
+    ItemsArgs a;
+    a.items = items;
+    a.ligs = ligs;
+    a.recs = recs;
+    a.counter = counter;
+    a.n_items = n_items;
+    a.ppb = cfg.ppb;
+    a.budget = budget;
+    a.rho = rho;
+    a.eps = eps;
+    switch (cfg.tpp) {
+        case 32: return launch_items_v<32>(a, cfg.variant, grid, s);
+        case 64: return launch_items_v<64>(a, cfg.variant, grid, s);
+        case 128: return launch_items_v<128>(a, cfg.variant, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Resident blocks of the persistent launch: SMs x blocks an SM can hold.
+int items_grid(const EvalCfg &cfg, int budget, int device) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
+    int per_sm = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define ADGB_OCC(TPP, VAR)                                                                   \
+    if (cfg.tpp == TPP && cfg.variant == VAR) {                                              \
+        cudaFuncSetAttribute(eval_items_kernel<TPP, VAR>,                                    \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, budget);           \
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_items_kernel<TPP, VAR>, \
+                                                          TPP * cfg.ppb, budget);           \
+    }
+    ADGB_OCC(32, 0) ADGB_OCC(32, 1) ADGB_OCC(32, 2)
+    ADGB_OCC(64, 0) ADGB_OCC(64, 1) ADGB_OCC(64, 2)
+    ADGB_OCC(128, 0) ADGB_OCC(128, 1) ADGB_OCC(128, 2)
+#undef ADGB_OCC
+    if (e != cudaSuccess || per_sm < 1) return 0;
+    return per_sm * prop.multiProcessorCount;
 }
 
 template <int TPP, int VAR>
