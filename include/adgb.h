@@ -327,6 +327,75 @@ int batch_local_search_dev(adgb_ctx *ctx, int batch_id, float *genes_dev,
 int batch_release(adgb_ctx *ctx, int batch_id);
 
 /*
+ * Serving: continuous batching of docking jobs.
+ *
+ * serve_start creates a server on ctx's device with its own host thread and
+ * stream.  The thread runs ticks; a tick advances every active job by one
+ * step of its Lamarckian GA (initial population, or one generation), runs
+ * ONE multi-ligand local-search launch over the individuals of all active
+ * jobs, updates each job's run bests and evaluation counts, and finishes the
+ * jobs whose runs are done (FP64 rescoring, results copied to host, device
+ * memory released).  Queued jobs are admitted in arrival order whenever
+ * their device memory fits the server's budget and the active-job cap.
+ * Populations, ligands and counters stay on the device between ticks.  A
+ * job's results do not depend on the other jobs in the mix (the same bits
+ * alone or batched).
+ *
+ * dock_submit validates the ligand and parameters on the calling thread and
+ * queues the job (ADGB_EREJECTED if it can never fit the budget or the
+ * server is stopping).  dock_poll reports a job's state; dock_wait blocks
+ * until the job has finished, been cancelled or failed (ADGB_ETIMEOUT after
+ * timeout_ms; < 0 waits without limit); dock_result copies a finished job's
+ * best genotypes [n_runs][6+T], FP64 best energies [n_runs] and evaluation
+ * counts [n_runs] (ADGB_ETIMEOUT while it is queued or running, the job's
+ * error status if it did not finish); dock_cancel asks for cancellation
+ * (queued: dropped; running: dropped at the end of the current tick);
+ * dock_forget frees the host record of a job that is no longer queued or
+ * running.  serve_stop cancels all jobs, joins the thread and frees the
+ * server.  The submit/poll/wait/result/cancel calls may come from any host
+ * threads; receptors must stay uploaded while jobs that use them are
+ * pending, and must not be uploaded or released concurrently with
+ * dock_submit.
+ */
+typedef struct adgb_server adgb_server;
+
+typedef struct {
+    int max_active_jobs;          /* 0: limited by the memory budget only */
+    long long mem_budget_bytes;   /* 0: a quarter of the free device memory at start */
+    int threads_per_pose;         /* 0: 32 */
+    int poses_per_block;          /* 0: 128 / threads_per_pose */
+    int reduce_variant;           /* -1: the context default */
+} adgb_serve_options;
+
+typedef struct {
+    int status;          /* 0 done, 1 queued, 2 running, ADGB_ECANCELLED, ADGB_EDEVICE */
+    int n_runs, n_genes; /* n_genes = 6 + T */
+    int generations;     /* generations completed */
+    long long evals;     /* evaluations of all runs (when done) */
+    double submit_s, start_s, finish_s;  /* server clock, seconds; -1 if not yet */
+} adgb_job_info;
+
+typedef struct {
+    int queued, active;
+    long long ticks, items_run;
+    long long device_bytes_in_use, device_bytes_budget;
+    double busy_s, uptime_s;
+} adgb_serve_stats;
+
+int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **server);
+int serve_stop(adgb_server *server);
+const char *serve_last_error(adgb_server *server);
+int serve_stats(adgb_server *server, adgb_serve_stats *stats);
+int dock_submit(adgb_server *server, int receptor_id, const adgb_ligand_desc *lig,
+                const adgb_dock_params *p, long long *job_id);
+int dock_poll(adgb_server *server, long long job_id, adgb_job_info *info);
+int dock_wait(adgb_server *server, long long job_id, int timeout_ms, adgb_job_info *info);
+int dock_result(adgb_server *server, long long job_id, float *best_genes, double *best_energy,
+                long long *evals);
+int dock_cancel(adgb_server *server, long long job_id);
+int dock_forget(adgb_server *server, long long job_id);
+
+/*
  * reduce4_bench_dev - the reduction test kernel of Sec. 5.2: every thread
  * of a block holds one four-element vector, the block computes the sum and
  * every thread receives it.  in [n_blocks][threads][4] float32, out the same

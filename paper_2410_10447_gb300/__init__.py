@@ -5,6 +5,6 @@ binding and build step.
 """
 from .adgb import (  # noqa: F401
     EXPORTS, LS_RESUME, REDUCE4_PAPER_FS, REDUCE_MMA_BF16X3, REDUCE_MMA_TF32X2, REDUCE_SHFL,
-    VARIANTS, AdgbError, Context, library_path, load, validate_ligand_torsion_tree,
+    VARIANTS, AdgbError, Context, Server, library_path, load, validate_ligand_torsion_tree,
 )
 from .build import build  # noqa: F401

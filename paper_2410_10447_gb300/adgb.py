@@ -33,7 +33,8 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
            "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev",
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
-           "batch_release"]
+           "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
+           "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget"]
 MAX_GENES = 46
 
 
@@ -85,6 +86,25 @@ def dock_params(**kw) -> _DockParams:
     return _DockParams(*[d[f] for f, _ in _DockParams._fields_])
 
 
+class _ServeOptions(C.Structure):
+    _fields_ = [("max_active_jobs", C.c_int), ("mem_budget_bytes", C.c_longlong),
+                ("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
+                ("reduce_variant", C.c_int)]
+
+
+class _JobInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_runs", C.c_int), ("n_genes", C.c_int),
+                ("generations", C.c_int), ("evals", C.c_longlong), ("submit_s", C.c_double),
+                ("start_s", C.c_double), ("finish_s", C.c_double)]
+
+
+class _ServeStats(C.Structure):
+    _fields_ = [("queued", C.c_int), ("active", C.c_int), ("ticks", C.c_longlong),
+                ("items_run", C.c_longlong), ("device_bytes_in_use", C.c_longlong),
+                ("device_bytes_budget", C.c_longlong), ("busy_s", C.c_double),
+                ("uptime_s", C.c_double)]
+
+
 class _LSParams(C.Structure):
     _fields_ = [("iters", C.c_int), ("rho", C.c_float), ("eps", C.c_float),
                 ("reduce_variant", C.c_int), ("flags", C.c_int)]
@@ -129,6 +149,18 @@ def load(build: bool = False):
     L.batch_autotune.argtypes = [vp, C.c_int, vp, C.c_int, C.POINTER(_Options)]
     L.batch_local_search_dev.argtypes = [vp, C.c_int, vp, C.POINTER(_LSParams), vp, vp]
     L.batch_release.argtypes = [vp, C.c_int]
+    L.serve_start.argtypes = [vp, C.POINTER(_ServeOptions), C.POINTER(vp)]
+    L.serve_stop.argtypes = [vp]
+    L.serve_last_error.argtypes = [vp]
+    L.serve_last_error.restype = C.c_char_p
+    L.serve_stats.argtypes = [vp, C.POINTER(_ServeStats)]
+    L.dock_submit.argtypes = [vp, C.c_int, C.POINTER(_Ligand), C.POINTER(_DockParams),
+                              C.POINTER(C.c_longlong)]
+    L.dock_poll.argtypes = [vp, C.c_longlong, C.POINTER(_JobInfo)]
+    L.dock_wait.argtypes = [vp, C.c_longlong, C.c_int, C.POINTER(_JobInfo)]
+    L.dock_result.argtypes = [vp, C.c_longlong, vp, vp, vp]
+    L.dock_cancel.argtypes = [vp, C.c_longlong]
+    L.dock_forget.argtypes = [vp, C.c_longlong]
     L.dock_noalloc_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.ga_init_population_dev.argtypes = [vp, C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int,
                                          vp, vp]
@@ -378,3 +410,84 @@ class Context:
         """Host call on raw host pointers (pinned buffers of the caller)."""
         p = _LSParams(int(iters), float(rho), float(eps), int(variant), 0)
         self._chk(self.lib.local_search(self.h, rid, lid, genes_ptr, n, C.byref(p), best_ptr, None))
+
+
+JOB_DONE, JOB_QUEUED, JOB_RUNNING = 0, 1, 2
+
+
+class Server:
+    """Continuous-batching docking server on a context's device (serve_start)."""
+
+    def __init__(self, ctx: "Context", max_active_jobs=0, mem_budget_bytes=0, threads_per_pose=0,
+                 poses_per_block=0, reduce_variant=-1):
+        self.ctx, self.lib = ctx, ctx.lib
+        self.h = C.c_void_p()
+        o = _ServeOptions(max_active_jobs, mem_budget_bytes, threads_per_pose, poses_per_block,
+                          reduce_variant)
+        rc = self.lib.serve_start(ctx.h, C.byref(o), C.byref(self.h))
+        if rc != ADGB_OK:
+            raise AdgbError(rc, "serve_start")
+        self._genes = {}
+
+    def _chk(self, rc):
+        if rc != ADGB_OK:
+            raise AdgbError(rc, self.lib.serve_last_error(self.h).decode())
+
+    def submit(self, rid, lig: dict, params) -> int:
+        d, keep = _ligand_desc(lig)
+        jid = C.c_longlong()
+        self._chk(self.lib.dock_submit(self.h, rid, C.byref(d), C.byref(params), C.byref(jid)))
+        self._genes[jid.value] = (params.n_runs, 6 + int(lig["n_tors"]))
+        return jid.value
+
+    @staticmethod
+    def _info(i):
+        return dict(status=i.status, n_runs=i.n_runs, n_genes=i.n_genes,
+                    generations=i.generations, evals=i.evals, submit_s=i.submit_s,
+                    start_s=i.start_s, finish_s=i.finish_s)
+
+    def poll(self, jid):
+        i = _JobInfo()
+        self._chk(self.lib.dock_poll(self.h, jid, C.byref(i)))
+        return self._info(i)
+
+    def wait(self, jid, timeout_ms=-1):
+        """Job info once it has finished; None on timeout."""
+        i = _JobInfo()
+        rc = self.lib.dock_wait(self.h, jid, int(timeout_ms), C.byref(i))
+        if rc == -5:
+            return None
+        self._chk(rc)
+        return self._info(i)
+
+    def result(self, jid):
+        runs, G = self._genes[jid]
+        g = np.zeros((runs, G), np.float32)
+        e = np.zeros(runs, np.float64)
+        v = np.zeros(runs, np.int64)
+        rc = self.lib.dock_result(self.h, jid, g.ctypes.data, e.ctypes.data, v.ctypes.data)
+        if rc != ADGB_OK:
+            raise AdgbError(rc, "dock_result(job %d)" % jid)
+        return g, e, v
+
+    def cancel(self, jid):
+        self._chk(self.lib.dock_cancel(self.h, jid))
+
+    def forget(self, jid):
+        self._chk(self.lib.dock_forget(self.h, jid))
+
+    def stats(self):
+        st = _ServeStats()
+        self._chk(self.lib.serve_stats(self.h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in _ServeStats._fields_}
+
+    def stop(self):
+        if self.h:
+            self.lib.serve_stop(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass

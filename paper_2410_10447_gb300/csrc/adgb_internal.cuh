@@ -115,20 +115,17 @@ struct SmemLayout {
         total = pose0 + ppb * pose_stride;
     }
 
-    // Layout of one ligand inside a block of `budget` bytes of dynamic shared
-    // memory: the pair list and incidence lists are staged when they take at
-    // most 24 KB, and the pair-force buffer takes what is left (at most 4096
-    // pairs a chunk).  The same rule runs on the host (to size a launch) and
-    // on the device (per work item of the multi-ligand kernel).
+    // Layout of one ligand for the multi-ligand kernel: the pair list and
+    // incidence lists are staged when they take at most 24 KB, and the
+    // pair-force buffer holds min(pairs, 1024) pairs.  It depends on the
+    // ligand alone, so a genotype's arithmetic is the same whatever other
+    // ligands share the launch.  The host sizes a launch's shared memory to
+    // the largest such layout; the device recomputes it per work item.
     static __host__ __device__ inline SmemLayout choose(int N, int T, int np, int ppb,
-                                                        int warps_per_pose, int budget) {
+                                                        int warps_per_pose) {
         SmemLayout l;
         const bool stage = 8 * np <= 24 * 1024;
-        l.make(N, T, ppb, warps_per_pose, 1, np, stage);
-        int room = (budget - (l.total - ppb * 16)) / (ppb * 16);
-        int ch = np < room ? np : room;
-        ch = ch < 4096 ? ch : 4096;
-        ch = ch > 1 ? ch : 1;
+        const int ch = np < 1024 ? (np > 1 ? np : 1) : 1024;
         l.make(N, T, ppb, warps_per_pose, ch, np, stage);
         return l;
     }
@@ -145,6 +142,7 @@ struct WorkItem {
     const int *iters;      // per-genotype evaluation counts, or null
     int iters_all;         // evaluation count when iters is null
     int cost;              // ordering key (host side)
+    float rho, eps;        // ADADELTA parameters of the item's search
 };
 
 // Launch configuration of the fused kernel.
@@ -171,13 +169,18 @@ cudaError_t launch_init_population(const RecDev &rec, int n_tors, uint64_t seed,
                                    float *genes, int *iters, cudaStream_t s);
 cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *genes,
                                  const float *energy, float *genes_out, int *iters, cudaStream_t s);
+cudaError_t launch_job_start(const RecDev &rec, int n_tors, const DockCfg &d, DockScratch &w,
+                             cudaStream_t s);
+cudaError_t launch_job_ga(const DockCfg &d, int G, int gen, DockScratch &w, int cur, cudaStream_t s);
+cudaError_t launch_job_best(const DockCfg &d, int G, DockScratch &w, int cur, float *best_genes,
+                            cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
                           cudaStream_t s);
 // Persistent multi-ligand local search over a device table of work items
 // (counter zeroed by the launch itself, so the launch can be replayed).
 cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *ligs,
                               const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
-                              float rho, float eps, int grid, cudaStream_t s);
+                              int grid, cudaStream_t s);
 int items_grid(const EvalCfg &cfg, int budget, int device);
 cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M,
                              float *cells, cudaStream_t s);
@@ -185,5 +188,27 @@ cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int 
                                  int reps, float *out, cudaStream_t s);
 
 enum { MODE_SCORE = 0, MODE_LS = 1 };
+
+}  // namespace adgb
+
+#include <string>
+#include <vector>
+
+namespace adgb {
+
+// Host image of a validated ligand's device blob; `rel` holds the blob
+// offsets in its pointer fields until bind_ligand relocates them.
+struct LigandBlob {
+    std::vector<unsigned char> bytes;
+    LigDev rel;
+    int max_type = 0;
+};
+int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &out);
+LigDev bind_ligand(const LigandBlob &b, const unsigned char *mem);
+int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg &d, int &variant,
+                         std::string *err);
+int ctx_device(const adgb_ctx *c);
+int ctx_default_variant(const adgb_ctx *c);
+int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps);
 
 }  // namespace adgb

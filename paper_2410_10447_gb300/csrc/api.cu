@@ -398,6 +398,144 @@ int lookup(adgb_ctx *c, int rid, int lid, Receptor **R, Ligand **L) {
 
 }  // namespace
 
+
+namespace adgb {
+
+int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &out) {
+    HostLigand h;
+    int rc = build_ligand(err, d, h);
+    if (rc) return rc;
+    const int N = h.N, T = h.T, NP = h.NP, NT = d->n_types;
+    const int Tz = T > 0 ? T : 1, NPz = NP > 0 ? NP : 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
+    const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
+    const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
+    const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
+    const size_t o_incoff = take(4 * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
+    const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
+                 o_tsol = take(4 * NT), o_thb = take(4 * NT);
+    std::vector<unsigned char> &buf = out.bytes;
+    buf.assign(off, 0);
+    memcpy(&buf[o_ref], h.ref.data(), 16 * N);
+    memcpy(&buf[o_sv], h.sv.data(), 8 * N);
+    memcpy(&buf[o_type], h.type.data(), 4 * N);
+    memcpy(&buf[o_frag], h.frag.data(), 4 * N);
+    if (T) {
+        memcpy(&buf[o_tpar], h.tparent.data(), 4 * T);
+        memcpy(&buf[o_tat], h.tatoms.data(), 16 * T);
+        memcpy(&buf[o_tax], h.taxis.data(), 16 * T);
+        memcpy(&buf[o_tb], h.tbref.data(), 16 * T);
+    }
+    if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
+    memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
+    memcpy(&buf[o_perm], h.perm.data(), 4 * N);
+    memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (N + 1));
+    if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
+    memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
+    memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
+    memcpy(&buf[o_tvol], h.tvol.data(), 4 * NT);
+    memcpy(&buf[o_tsol], h.tsol.data(), 4 * NT);
+    memcpy(&buf[o_thb], h.thb.data(), 4 * NT);
+    LigDev &v = out.rel;
+    v.n_atoms = N;
+    v.n_tors = T;
+    v.n_pairs = NP;
+    v.n_types = NT;
+    // offsets travel in the pointer fields until bind_ligand relocates them
+    auto at = [](size_t o) { return reinterpret_cast<const unsigned char *>((uintptr_t)o); };
+    v.ref = reinterpret_cast<const float4 *>(at(o_ref));
+    v.sv = reinterpret_cast<const float2 *>(at(o_sv));
+    v.type = reinterpret_cast<const int *>(at(o_type));
+    v.frag = reinterpret_cast<const int *>(at(o_frag));
+    v.tparent = reinterpret_cast<const int *>(at(o_tpar));
+    v.tatoms = reinterpret_cast<const int4 *>(at(o_tat));
+    v.taxis = reinterpret_cast<const float4 *>(at(o_tax));
+    v.tbref = reinterpret_cast<const float4 *>(at(o_tb));
+    v.pairs = reinterpret_cast<const uint32_t *>(at(o_pairs));
+    v.tptab = reinterpret_cast<const float2 *>(at(o_tab));
+    v.perm = reinterpret_cast<const int *>(at(o_perm));
+    v.inc_off = reinterpret_cast<const int *>(at(o_incoff));
+    v.inc = reinterpret_cast<const uint16_t *>(at(o_inc));
+    v.t_R = reinterpret_cast<const float *>(at(o_tR));
+    v.t_eps = reinterpret_cast<const float *>(at(o_teps));
+    v.t_vol = reinterpret_cast<const float *>(at(o_tvol));
+    v.t_sol = reinterpret_cast<const float *>(at(o_tsol));
+    v.t_hb = reinterpret_cast<const int *>(at(o_thb));
+    v.hb_R = d->hb_R;
+    v.hb_eps = d->hb_eps;
+    out.max_type = h.max_type;
+    return ADGB_OK;
+}
+
+LigDev bind_ligand(const LigandBlob &b, const unsigned char *mem) {
+    LigDev v = b.rel;
+    auto mv = [&](auto p) { return reinterpret_cast<decltype(p)>(mem + reinterpret_cast<uintptr_t>(p)); };
+    v.ref = mv(v.ref);
+    v.sv = mv(v.sv);
+    v.type = mv(v.type);
+    v.frag = mv(v.frag);
+    v.tparent = mv(v.tparent);
+    v.tatoms = mv(v.tatoms);
+    v.taxis = mv(v.taxis);
+    v.tbref = mv(v.tbref);
+    v.pairs = mv(v.pairs);
+    v.tptab = mv(v.tptab);
+    v.perm = mv(v.perm);
+    v.inc_off = mv(v.inc_off);
+    v.inc = mv(v.inc);
+    v.t_R = mv(v.t_R);
+    v.t_eps = mv(v.t_eps);
+    v.t_vol = mv(v.t_vol);
+    v.t_sol = mv(v.t_sol);
+    v.t_hb = mv(v.t_hb);
+    return v;
+}
+
+}  // namespace adgb
+
+namespace adgb {
+
+int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg &d, int &variant,
+                         std::string *err) {
+    if (!p) return ferr(err, ADGB_EINVAL, "dock: null parameters");
+    if (p->n_runs < 1 || p->pop < 2 || p->pop > 1024 || p->max_gens < 0 || p->ls_iters < 1 ||
+        p->max_evals < 0 || !(p->ls_rate >= 0.f && p->ls_rate <= 1.f) ||
+        !(p->rho > 0.f && p->rho < 1.f) || !(p->eps > 0.f) || !(p->p_cross >= 0.f && p->p_cross <= 1.f) ||
+        !(p->p_mut >= 0.f && p->p_mut <= 1.f) || !finite(p->mut_trans) || !finite(p->mut_angle) ||
+        (long long)p->n_runs * p->pop > (1 << 26))
+        return ferr(err, ADGB_EINVAL, "dock: bad parameters");
+    variant = p->reduce_variant < 0 ? default_variant : p->reduce_variant;
+    if (variant < 0 || variant >= ADGB_REDUCE_N) return ferr(err, ADGB_EINVAL, "unknown reduce variant %d", variant);
+    d.n_runs = p->n_runs;
+    d.pop = p->pop;
+    d.max_gens = p->max_gens;
+    d.ls_iters = p->ls_iters;
+    d.max_evals = p->max_evals;
+    d.ls_rate = p->ls_rate;
+    d.rho = p->rho;
+    d.eps = p->eps;
+    d.p_cross = p->p_cross;
+    d.p_mut = p->p_mut;
+    d.mut_trans = p->mut_trans;
+    d.mut_angle = p->mut_angle;
+    d.seed = p->seed;
+    return ADGB_OK;
+}
+
+int ctx_device(const adgb_ctx *c) { return c->device; }
+int ctx_default_variant(const adgb_ctx *c) { return c->opts.reduce_variant; }
+
+int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps) {
+    auto it = c->recs.find(rid);
+    if (it == c->recs.end()) return ADGB_ENOTFOUND;
+    *out = it->second.dev;
+    *n_type_maps = it->second.n_type_maps;
+    return ADGB_OK;
+}
+
+}  // namespace adgb
+
 extern "C" {
 
 int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts) {
@@ -513,83 +651,27 @@ int release_receptor(adgb_ctx *c, int id) {
 int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *ligand_id) {
     if (!c) return ADGB_EINVAL;
     if (!ligand_id) return fail(c, ADGB_EINVAL, "ligand: null id pointer");
-    HostLigand h;
-    int rc = build_ligand(&c->err, d, h);
+    LigandBlob blob;
+    int rc = make_ligand_blob(&c->err, d, blob);
     if (rc) return rc;
-    const int N = h.N, T = h.T, NP = h.NP;
-    const int Tz = T > 0 ? T : 1, NPz = NP > 0 ? NP : 1;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = al256(off + bytes); return o; };
-    const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
-    const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
-    const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
-    const size_t o_incoff = take(4 * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
-    const int NT = d->n_types;
-    const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
-                 o_tsol = take(4 * NT), o_thb = take(4 * NT);
-    std::vector<unsigned char> buf(off, 0);
-    memcpy(&buf[o_ref], h.ref.data(), 16 * N);
-    memcpy(&buf[o_sv], h.sv.data(), 8 * N);
-    memcpy(&buf[o_type], h.type.data(), 4 * N);
-    memcpy(&buf[o_frag], h.frag.data(), 4 * N);
-    if (T) {
-        memcpy(&buf[o_tpar], h.tparent.data(), 4 * T);
-        memcpy(&buf[o_tat], h.tatoms.data(), 16 * T);
-        memcpy(&buf[o_tax], h.taxis.data(), 16 * T);
-        memcpy(&buf[o_tb], h.tbref.data(), 16 * T);
-    }
-    if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
-    memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
-    memcpy(&buf[o_perm], h.perm.data(), 4 * N);
-    memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (N + 1));
-    if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
-    memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
-    memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
-    memcpy(&buf[o_tvol], h.tvol.data(), 4 * NT);
-    memcpy(&buf[o_tsol], h.tsol.data(), 4 * NT);
-    memcpy(&buf[o_thb], h.thb.data(), 4 * NT);
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
     unsigned char *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, off);
+    cudaError_t e = cudaMalloc(&mem, blob.bytes.size());
     if (e != cudaSuccess) return fail(c, ADGB_ENOMEM, "ligand: %s", cudaGetErrorString(e));
-    e = cudaMemcpy(mem, buf.data(), off, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(mem, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaFree(mem);
         return cuda_fail(c, e, "ligand upload");
     }
     Ligand L;
     L.mem = mem;
-    L.n_atoms = N;
-    L.n_tors = T;
-    L.n_types = d->n_types;
-    L.n_pairs = NP;
-    L.max_type = h.max_type;
-    LigDev &v = L.dev;
-    v.n_atoms = N;
-    v.n_tors = T;
-    v.n_pairs = NP;
-    v.n_types = d->n_types;
-    v.ref = reinterpret_cast<const float4 *>(mem + o_ref);
-    v.sv = reinterpret_cast<const float2 *>(mem + o_sv);
-    v.type = reinterpret_cast<const int *>(mem + o_type);
-    v.frag = reinterpret_cast<const int *>(mem + o_frag);
-    v.tparent = reinterpret_cast<const int *>(mem + o_tpar);
-    v.tatoms = reinterpret_cast<const int4 *>(mem + o_tat);
-    v.taxis = reinterpret_cast<const float4 *>(mem + o_tax);
-    v.tbref = reinterpret_cast<const float4 *>(mem + o_tb);
-    v.pairs = reinterpret_cast<const uint32_t *>(mem + o_pairs);
-    v.tptab = reinterpret_cast<const float2 *>(mem + o_tab);
-    v.perm = reinterpret_cast<const int *>(mem + o_perm);
-    v.inc_off = reinterpret_cast<const int *>(mem + o_incoff);
-    v.inc = reinterpret_cast<const uint16_t *>(mem + o_inc);
-    v.t_R = reinterpret_cast<const float *>(mem + o_tR);
-    v.t_eps = reinterpret_cast<const float *>(mem + o_teps);
-    v.t_vol = reinterpret_cast<const float *>(mem + o_tvol);
-    v.t_sol = reinterpret_cast<const float *>(mem + o_tsol);
-    v.t_hb = reinterpret_cast<const int *>(mem + o_thb);
-    v.hb_R = d->hb_R;
-    v.hb_eps = d->hb_eps;
+    L.n_atoms = blob.rel.n_atoms;
+    L.n_tors = blob.rel.n_tors;
+    L.n_types = blob.rel.n_types;
+    L.n_pairs = blob.rel.n_pairs;
+    L.max_type = blob.max_type;
+    L.dev = bind_ligand(blob, mem);
     const int id = c->next_id++;
     c->ligs[id] = L;
     *ligand_id = id;
@@ -744,30 +826,7 @@ int local_search(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int 
 }
 
 static int check_dock(adgb_ctx *c, const adgb_dock_params *p, int &variant, DockCfg &d) {
-    if (!p) return fail(c, ADGB_EINVAL, "dock: null parameters");
-    if (p->n_runs < 1 || p->pop < 2 || p->pop > 1024 || p->max_gens < 0 || p->ls_iters < 1 ||
-        p->max_evals < 0 || !(p->ls_rate >= 0.f && p->ls_rate <= 1.f) ||
-        !(p->rho > 0.f && p->rho < 1.f) || !(p->eps > 0.f) || !(p->p_cross >= 0.f && p->p_cross <= 1.f) ||
-        !(p->p_mut >= 0.f && p->p_mut <= 1.f) || !finite(p->mut_trans) || !finite(p->mut_angle) ||
-        (long long)p->n_runs * p->pop > (1 << 26))
-        return fail(c, ADGB_EINVAL, "dock: bad parameters");
-    variant = p->reduce_variant;
-    int rc = check_variant(c, variant);
-    if (rc) return rc;
-    d.n_runs = p->n_runs;
-    d.pop = p->pop;
-    d.max_gens = p->max_gens;
-    d.ls_iters = p->ls_iters;
-    d.max_evals = p->max_evals;
-    d.ls_rate = p->ls_rate;
-    d.rho = p->rho;
-    d.eps = p->eps;
-    d.p_cross = p->p_cross;
-    d.p_mut = p->p_mut;
-    d.mut_trans = p->mut_trans;
-    d.mut_angle = p->mut_angle;
-    d.seed = p->seed;
-    return ADGB_OK;
+    return dock_cfg_from_params(p, c->opts.reduce_variant, d, variant, &c->err);
 }
 
 // stream-ordered working set of one dock call
@@ -1008,21 +1067,16 @@ extern "C" int dock_noalloc_dev(adgb_ctx *c, int receptor_id, int ligand_id,
 namespace {
 
 int batch_budget(const Batch &b, const EvalCfg &cfg) {
-    int budget = 0;
-    for (size_t u = 0; u < b.ligs.size(); u++) {
-        SmemLayout l;
-        const bool stage = 8 * b.lig_np[u] <= 24 * 1024;
-        l.make(b.lig_n[u], b.lig_t[u], cfg.ppb, cfg.tpp / 32, 1, b.lig_np[u], stage);
-        const int fixed = l.total - cfg.ppb * 16;
-        const int want = fixed + cfg.ppb * 16 * std::max(1, std::min(b.lig_np[u], 1024));
-        budget = std::max(budget, want);
-    }
-    return std::min(std::max(budget, 1024), 200 * 1024);
+    int budget = 1024;
+    for (size_t u = 0; u < b.ligs.size(); u++)
+        budget = std::max(budget, SmemLayout::choose(b.lig_n[u], b.lig_t[u], b.lig_np[u], cfg.ppb,
+                                                     cfg.tpp / 32).total);
+    return budget;
 }
 
 // Items of ppb genotypes of one ligand, longest (most work) first.
 std::vector<WorkItem> batch_items(const Batch &b, const EvalCfg &cfg, float *genes, float *energy,
-                                  int iters) {
+                                  int iters, float rho, float eps) {
     std::vector<WorkItem> items;
     long long row = 0;
     for (size_t i = 0; i < b.n_poses.size(); i++) {
@@ -1039,6 +1093,8 @@ std::vector<WorkItem> batch_items(const Batch &b, const EvalCfg &cfg, float *gen
             w.iters = nullptr;
             w.iters_all = iters;
             w.cost = cost;
+            w.rho = rho;
+            w.eps = eps;
             items.push_back(w);
         }
         row += b.n_poses[i];
@@ -1169,12 +1225,13 @@ extern "C" int batch_local_search_dev(adgb_ctx *c, int batch_id, float *genes_de
         b.budget = batch_budget(b, cfg);
         b.grid = items_grid(cfg, b.budget, c->device);
         if (b.grid < 1) return fail(c, ADGB_EINVAL, "batch_local_search: launch shape does not fit an SM");
-        e = upload_items(b, batch_items(b, cfg, genes_dev, best_energy_dev, p->iters), c->stream);
+        e = upload_items(b, batch_items(b, cfg, genes_dev, best_energy_dev, p->iters, p->rho, p->eps),
+                         c->stream);
         cudaGraph_t graph = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaError_t el = launch_eval_items(b.d_items, b.n_items, b.d_ligs, b.d_recs, b.d_counter,
-                                               cfg, b.budget, p->rho, p->eps, b.grid, c->stream);
+                                               cfg, b.budget, b.grid, c->stream);
             e = cudaStreamEndCapture(c->stream, &graph);
             if (el != cudaSuccess) e = el;
         }
@@ -1222,11 +1279,11 @@ extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev,
         float ms_min = INFINITY;
         for (int rep = 0; rep < 2 && e == cudaSuccess; rep++) {
             e = cudaMemcpyAsync(tg, genes_dev, gbytes, cudaMemcpyDeviceToDevice, c->stream);
-            if (e == cudaSuccess) e = upload_items(b, batch_items(b, cfg, tg, te, iters), c->stream);
+            if (e == cudaSuccess) e = upload_items(b, batch_items(b, cfg, tg, te, iters, 0.8f, 1e-2f), c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
             if (e == cudaSuccess)
                 e = launch_eval_items(b.d_items, b.n_items, b.d_ligs, b.d_recs, b.d_counter, cfg, budget,
-                                      0.8f, 1e-2f, grid, c->stream);
+                                      grid, c->stream);
             if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
             float ms = 0.f;

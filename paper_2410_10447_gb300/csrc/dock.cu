@@ -333,6 +333,32 @@ cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *
     return cudaGetLastError();
 }
 
+// The steps of dock() one at a time, for the serving loop, which advances
+// many jobs by one generation per tick.
+cudaError_t launch_job_start(const RecDev &rec, int n_tors, const DockCfg &d, DockScratch &w,
+                             cudaStream_t s) {
+    const int n = d.n_runs * d.pop;
+    init_state_kernel<<<(d.n_runs + 127) / 128, 128, 0, s>>>(d.n_runs, w.best_e, w.evals, w.done);
+    init_pop_kernel<<<(n + 127) / 128, 128, 0, s>>>(rec, n_tors, d.seed, d.n_runs, d.pop,
+                                                     w.genes[0], w.iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_job_ga(const DockCfg &d, int G, int gen, DockScratch &w, int cur, cudaStream_t s) {
+    const int gt = d.pop >= 1024 ? 1024 : ((d.pop + 31) / 32) * 32;
+    const int gsm = (d.pop + 32) * 4 + 32 * 4;
+    ga_kernel<<<d.n_runs, gt, gsm, s>>>(d.pop, G, w.genes[cur], w.energy, d, (uint32_t)gen,
+                                       w.genes[cur ^ 1], w.iters, w.done);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_job_best(const DockCfg &d, int G, DockScratch &w, int cur, float *best_genes,
+                            cudaStream_t s) {
+    best_kernel<<<d.n_runs, 128, 0, s>>>(d.pop, G, w.genes[cur], w.energy, w.iters, best_genes,
+                                         w.best_e, w.evals, w.done, d.max_evals);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rescore_fp64(const RecDev &rec, const LigDev &lig, int n, const float *genes,
                                 double *out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

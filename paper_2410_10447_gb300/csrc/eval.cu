@@ -588,7 +588,6 @@ struct ItemsArgs {
     const RecDev *recs;
     int *counter;
     int n_items, ppb, budget;
-    float rho, eps;
 };
 
 template <int TPP, int VAR>
@@ -607,7 +606,7 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
         const WorkItem w = a.items[it];
         if (w.lig != cur_lig) {
             const LigDev &lg = a.ligs[w.lig];
-            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32, a.budget);
+            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32);
             sl = stage_ligand(sm, L, lg);
             cur_lig = w.lig;
             __syncthreads();
@@ -622,8 +621,8 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
             io.iters = w.iters ? w.iters[group] : w.iters_all;
             io.mode = MODE_LS;
             io.resume = 0;
-            io.rho = a.rho;
-            io.eps = a.eps;
+            io.rho = w.rho;
+            io.eps = w.eps;
             search_pose<TPP, VAR>(sm, L, a.ligs[w.lig], a.recs[w.rec], sl, group, gt, io);
         }
         __syncthreads();  // the item is done before smem or s_item change
@@ -661,7 +660,7 @@ static cudaError_t launch_items_v(const ItemsArgs &a, int variant, int grid, cud
 
 cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *ligs,
                               const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
-                              float rho, float eps, int grid, cudaStream_t s) {
+                              int grid, cudaStream_t s) {
     ItemsArgs a;
     a.items = items;
     a.ligs = ligs;
@@ -670,8 +669,6 @@ cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *
     a.n_items = n_items;
     a.ppb = cfg.ppb;
     a.budget = budget;
-    a.rho = rho;
-    a.eps = eps;
     switch (cfg.tpp) {
         case 32: return launch_items_v<32>(a, cfg.variant, grid, s);
         case 64: return launch_items_v<64>(a, cfg.variant, grid, s);
