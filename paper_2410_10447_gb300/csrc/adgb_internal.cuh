@@ -16,6 +16,8 @@ constexpr float MS_LAMBDA = 0.003627f;
 constexpr float MS_K = 7.7839f;
 
 constexpr int MAX_GENES = 6 + ADGB_MAX_TORS;
+constexpr int PAIR_CHUNK = 1024;   // pairs per force-buffer chunk (fixed: a ligand's arithmetic
+                                   // does not depend on the launch it runs in)
 constexpr int TYPE_TAB = ADGB_MAX_TYPES * ADGB_MAX_TYPES;
 
 // Receptor as the kernels see it.  cells[((iz*(ny-1)+iy)*(nx-1)+ix)][m][c]
@@ -44,8 +46,11 @@ struct LigDev {
     const uint32_t *pairs;    // [Np] i | j << 8 | (ti*16+tj) << 16 | hb << 24
     const float2 *tptab;      // [256] (A, B): E = A r^-12 - B r^-m, m = 10 if hb else 6
     const int *perm;          // [N] internal index -> caller's index
-    const int *inc_off;       // [N+1] incidence list of atom i: inc[inc_off[i] .. inc_off[i+1])
-    const uint16_t *inc;      // [2 Np] (pair index << 1) | (atom is the pair's second atom), ascending
+    int n_chunks;             // ceil(Np / PAIR_CHUNK)
+    const int *inc_off;       // [n_chunks][N+1]: atom i's pairs in chunk q are
+                              // inc[inc_off[q*(N+1)+i] .. inc_off[q*(N+1)+i+1])
+    const uint16_t *inc;      // [2 Np] (pair index - q*PAIR_CHUNK) << 1 | (atom is the pair's
+                              // second atom), ordered by chunk, atom, pair
     // the caller's per-type parameters, kept for the FP64 rescoring
     const float *t_R, *t_eps, *t_vol, *t_sol;
     const int *t_hb;
@@ -78,7 +83,7 @@ struct SmemLayout {
     int spairs, sinc, pairs_in_smem;   // optional copies of the pair list and incidence lists
     int pose0, pose_stride;          // first pose block, bytes per pose
     // offsets inside one pose block
-    int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage, p_force;
+    int p_xyz, p_grad, p_genes, p_ggrad, p_sc, p_red, p_stage, p_force, p_tq, p_seg;
     int chunk;                       // pairs per force-buffer chunk
     int total;
 
@@ -86,6 +91,7 @@ struct SmemLayout {
 
     __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose, int ch,
                                          int np = 0, bool stage_pairs = false) {
+        const int nch = (np + PAIR_CHUNK - 1) / PAIR_CHUNK;
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
         sv = o;      o = al16(o + 8 * N);
@@ -96,7 +102,7 @@ struct SmemLayout {
         taxis = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tbref = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tptab = o;   o = al16(o + 8 * TYPE_TAB);
-        incoff = o;  o = al16(o + 4 * (N + 1));
+        incoff = o;  if (stage_pairs) o = al16(o + 4 * nch * (N + 1));
         pairs_in_smem = stage_pairs ? 1 : 0;
         spairs = o;  if (stage_pairs) o = al16(o + 4 * np);
         sinc = o;    if (stage_pairs) o = al16(o + 4 * np);
@@ -111,6 +117,8 @@ struct SmemLayout {
         p_stage = q; q = al16(q + 4 * 32 * 12 * warps_per_pose);
         chunk = ch > 0 ? ch : 1;
         p_force = q; q = al16(q + 16 * chunk);
+        p_tq = q;    q = al16(q + (N > 32 ? 16 * N : 0));
+        p_seg = q;   q = al16(q + (N > 32 ? 4 * 8 * ((N + 31) / 32) : 0));
         pose_stride = q;
         total = pose0 + ppb * pose_stride;
     }
@@ -125,7 +133,7 @@ struct SmemLayout {
                                                         int warps_per_pose) {
         SmemLayout l;
         const bool stage = 8 * np <= 24 * 1024;
-        const int ch = np < 1024 ? (np > 1 ? np : 1) : 1024;
+        const int ch = np < PAIR_CHUNK ? (np > 1 ? np : 1) : PAIR_CHUNK;
         l.make(N, T, ppb, warps_per_pose, ch, np, stage);
         return l;
     }

@@ -311,19 +311,31 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         h.pairs[p] = (uint32_t)inv[i] | (uint32_t)inv[j] << 8 |
                      (uint32_t)(ti * ADGB_MAX_TYPES + tj) << 16 | hb << 24;
     }
-    // incidence lists: for every atom the pairs it belongs to, ascending
-    h.inc_off.assign(N + 1, 0);
-    for (int p = 0; p < NP; p++) {
-        h.inc_off[(h.pairs[p] & 255) + 1]++;
-        h.inc_off[((h.pairs[p] >> 8) & 255) + 1]++;
-    }
-    for (int i = 0; i < N; i++) h.inc_off[i + 1] += h.inc_off[i];
-    h.inc.assign(2 * (size_t)NP, 0);
+    // incidence lists per chunk of PAIR_CHUNK pairs: for every chunk and atom
+    // the chunk's pairs it belongs to, ascending (chunk-local index, side)
     {
-        std::vector<int> fill(h.inc_off.begin(), h.inc_off.end() - 1);
-        for (int p = 0; p < NP; p++) {
-            h.inc[fill[h.pairs[p] & 255]++] = (uint16_t)(p << 1);
-            h.inc[fill[(h.pairs[p] >> 8) & 255]++] = (uint16_t)((p << 1) | 1);
+        const int nch = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
+        h.inc_off.assign((size_t)nch * (N + 1), 0);
+        h.inc.assign(2 * (size_t)NP, 0);
+        int pos = 0;
+        for (int q = 0; q < nch; q++) {
+            const int p0 = q * PAIR_CHUNK, p1 = std::min(NP, p0 + PAIR_CHUNK);
+            std::vector<int> cnt(N, 0);
+            for (int p = p0; p < p1; p++) {
+                cnt[h.pairs[p] & 255]++;
+                cnt[(h.pairs[p] >> 8) & 255]++;
+            }
+            std::vector<int> fill(N);
+            for (int a = 0; a < N; a++) {
+                h.inc_off[(size_t)q * (N + 1) + a] = pos;
+                fill[a] = pos;
+                pos += cnt[a];
+            }
+            h.inc_off[(size_t)q * (N + 1) + N] = pos;
+            for (int p = p0; p < p1; p++) {
+                h.inc[fill[h.pairs[p] & 255]++] = (uint16_t)((p - p0) << 1);
+                h.inc[fill[(h.pairs[p] >> 8) & 255]++] = (uint16_t)(((p - p0) << 1) | 1);
+            }
         }
     }
     h.tR.assign(d->R, d->R + NT);
@@ -355,21 +367,18 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
 EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     EvalCfg cfg;
     cfg.variant = variant;
-    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : 32;
+    // one warp a genotype for small ligands, more threads for large ones
+    const int by_size = L.n_atoms <= 32 ? 32 : (L.n_atoms <= 96 ? 64 : 128);
+    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : by_size;
     int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
     while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;
-    // the pair list (4 B a pair) and incidence lists (4 B a pair) are copied
-    // to shared memory when they take at most 24 KB
     cfg.stage_pairs = 8 * L.n_pairs <= 24 * 1024;
-    // shared memory per block kept near 48 KB so that four 128-thread blocks
-    // fit an SM; the pair-force buffer takes what the per-pose arrays leave
-    const int budget = 48 * 1024;
+    cfg.chunk = std::max(1, std::min(L.n_pairs, PAIR_CHUNK));
+    // keep a block's shared memory within 100 KB so that two blocks fit an SM
     SmemLayout lay;
     for (;; ppb--) {
-        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, 1, L.n_pairs, cfg.stage_pairs);
-        const int room = (budget - lay.total) / ppb / 16;
-        cfg.chunk = std::max(1, std::min(L.n_pairs, std::min(room, 4096)));
-        if (room >= 256 || room >= L.n_pairs || ppb == 1) break;
+        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, cfg.chunk, L.n_pairs, cfg.stage_pairs);
+        if (lay.total <= 100 * 1024 || ppb == 1) break;
     }
     cfg.ppb = ppb;
     return cfg;
@@ -412,7 +421,8 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
     const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
     const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
-    const size_t o_incoff = take(4 * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
+    const int NCH = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
+    const size_t o_incoff = take(4 * (size_t)(NCH > 0 ? NCH : 1) * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
     const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
                  o_tsol = take(4 * NT), o_thb = take(4 * NT);
     std::vector<unsigned char> &buf = out.bytes;
@@ -430,7 +440,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
     memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
     memcpy(&buf[o_perm], h.perm.data(), 4 * N);
-    memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (N + 1));
+    if (NCH) memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (size_t)NCH * (N + 1));
     if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
     memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
     memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
@@ -442,6 +452,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     v.n_tors = T;
     v.n_pairs = NP;
     v.n_types = NT;
+    v.n_chunks = NCH;
     // offsets travel in the pointer fields until bind_ligand relocates them
     auto at = [](size_t o) { return reinterpret_cast<const unsigned char *>((uintptr_t)o); };
     v.ref = reinterpret_cast<const float4 *>(at(o_ref));

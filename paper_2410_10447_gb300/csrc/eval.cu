@@ -201,6 +201,7 @@ struct PoseIO {
 struct StagedLig {
     const uint32_t *prs;
     const uint16_t *incl;
+    const int *incoff;   // [n_chunks][N+1]
 };
 
 // Copies one ligand's constants into shared memory (all threads of the
@@ -217,18 +218,20 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
     float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
     float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
     float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
-    int *s_incoff = reinterpret_cast<int *>(sm + L.incoff);
-    for (int i = threadIdx.x; i <= N; i += blockDim.x) s_incoff[i] = lig.inc_off[i];
-    // pair records and incidence lists: shared memory when they fit
+    // pair records, incidence lists and their offsets: shared memory when they fit
     const uint32_t *prs = lig.pairs;
     const uint16_t *incl = lig.inc;
+    const int *incoff = lig.inc_off;
     if (L.pairs_in_smem) {
         uint32_t *sp = reinterpret_cast<uint32_t *>(sm + L.spairs);
         uint16_t *si = reinterpret_cast<uint16_t *>(sm + L.sinc);
+        int *so = reinterpret_cast<int *>(sm + L.incoff);
         for (int p = threadIdx.x; p < NP; p += blockDim.x) sp[p] = lig.pairs[p];
         for (int p = threadIdx.x; p < 2 * NP; p += blockDim.x) si[p] = lig.inc[p];
+        for (int p = threadIdx.x; p < lig.n_chunks * (N + 1); p += blockDim.x) so[p] = lig.inc_off[p];
         prs = sp;
         incl = si;
+        incoff = so;
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_ref[i] = lig.ref[i];
@@ -243,7 +246,7 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
         s_tb[k] = lig.tbref[k];
     }
     for (int k = threadIdx.x; k < TYPE_TAB; k += blockDim.x) s_tab[k] = lig.tptab[k];
-    return {prs, incl};
+    return {prs, incl, incoff};
 }
 
 // Whole evaluation loop of one genotype by one pose group (TPP threads).
@@ -262,7 +265,6 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
     float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
     float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
     float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
-    int *s_incoff = reinterpret_cast<int *>(sm + L.incoff);
     const uint32_t *prs = sl.prs;
     const uint16_t *incl = sl.incl;
     unsigned char *P = sm + L.pose0 + group * L.pose_stride;
@@ -274,7 +276,6 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
     float *red = reinterpret_cast<float *>(P + L.p_red);
     float *stage = reinterpret_cast<float *>(P + L.p_stage) + (gt >> 5) * 32 * 12;
     float4 *fbuf = reinterpret_cast<float4 *>(P + L.p_force);
-    const int CH = L.chunk;
     constexpr int MAXA = ADGB_MAX_ATOMS / TPP;  // atoms owned per thread, at most
 
     constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
@@ -348,18 +349,14 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         }
         group_sync<TPP>(group);
 
-        // 3. intramolecular pairs, chunk by chunk: every pair's force goes to
-        //    its own slot of the force buffer, then each atom's owner adds the
-        //    forces of its pairs (incidence list, ascending pair index).  No
-        //    two threads ever write the same word.
-        int cur[MAXA];
-#pragma unroll
-        for (int m = 0; m < MAXA; m++) {
-            const int i = gt + m * TPP;
-            cur[m] = i < N ? s_incoff[i] : 0;
-        }
-        for (int c0 = 0; c0 < NP; c0 += CH) {
-            const int c1 = min(NP, c0 + CH);
+        // 3. intramolecular pairs, chunk by chunk (PAIR_CHUNK pairs): every
+        //    pair's force goes to its own slot of the force buffer, then each
+        //    atom's owner adds the forces of its pairs in the chunk (per-chunk
+        //    incidence lists with known bounds).  No two threads ever write
+        //    the same word.
+        for (int q = 0; q < lig.n_chunks; q++) {
+            const int c0 = q * PAIR_CHUNK, c1 = min(NP, c0 + PAIR_CHUNK);
+#pragma unroll 2
             for (int p = c0 + gt; p < c1; p += TPP) {
                 const uint32_t pr = prs[p];
                 const int i = pr & 255, j = (pr >> 8) & 255;
@@ -369,56 +366,44 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                 fbuf[p - c0] = make_float4(f.x, f.y, f.z, 0.f);
             }
             group_sync<TPP>(group);
+            const int *off = sl.incoff + q * (N + 1);
 #pragma unroll
             for (int m = 0; m < MAXA; m++) {
                 const int i = gt + m * TPP;
                 if (i < N) {
-                    const int end = s_incoff[i + 1];
-                    int c = cur[m];
+                    const int cb = off[i], ce = off[i + 1];
                     float ax = 0.f, ay = 0.f, az = 0.f;
-                    if (c1 == NP && c0 == 0) {
-                        // the whole list is in this chunk: no bound test
 #pragma unroll 4
-                        for (; c < end; c++) {
-                            const uint32_t e = incl[c];
-                            const float4 f = fbuf[e >> 1];
-                            const float sg = (e & 1) ? -1.f : 1.f;
-                            ax += sg * f.x;
-                            ay += sg * f.y;
-                            az += sg * f.z;
-                        }
-                    } else {
-                        for (; c < end; c++) {
-                            const uint32_t e = incl[c];
-                            const int p = (int)(e >> 1);
-                            if (p >= c1) break;
-                            const float4 f = fbuf[p - c0];
-                            const float sg = (e & 1) ? -1.f : 1.f;
-                            ax += sg * f.x;
-                            ay += sg * f.y;
-                            az += sg * f.z;
-                        }
+                    for (int c = cb; c < ce; c++) {
+                        const uint32_t e = incl[c];
+                        const float4 f = fbuf[e >> 1];
+                        const float sg = (e & 1) ? -1.f : 1.f;
+                        ax += sg * f.x;
+                        ay += sg * f.y;
+                        az += sg * f.z;
                     }
-                    cur[m] = c;
-                    float4 g = grd[i];
+                    const float4 g = grd[i];
                     grd[i] = make_float4(g.x + ax, g.y + ay, g.z + az, 0.f);
                 }
             }
             group_sync<TPP>(group);
         }
-        if (NP == 0) group_sync<TPP>(group);
 
         // 4. partial sums of (E, sum g, torque about the centre); torsion gradients
         float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float4 *tq = reinterpret_cast<float4 *>(P + L.p_tq);
         for (int i = gt; i < N; i += TPP) {
             const float4 g = grd[i], x = xyz[i];
             const float3 d = make_float3(x.x - tr.x, x.y - tr.y, x.z - tr.z);
+            const float3 c = make_float3(d.y * g.z - d.z * g.y, d.z * g.x - d.x * g.z,
+                                         d.x * g.y - d.y * g.x);
             v[1] += g.x;
             v[2] += g.y;
             v[3] += g.z;
-            v[4] += d.y * g.z - d.z * g.y;
-            v[5] += d.z * g.x - d.x * g.z;
-            v[6] += d.x * g.y - d.y * g.x;
+            v[4] += c.x;
+            v[5] += c.y;
+            v[6] += c.z;
+            if (N > 32) tq[i] = make_float4(c.x, c.y, c.z, 0.f);
         }
         if (N <= 32) {
             // one atom per lane of the group's first warp; atoms are in
@@ -463,21 +448,68 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                     }
                 }
             }
-        } else
-        for (int k = gt; k < T; k += TPP) {
-            const int4 ta = s_tat[k];
-            const float4 xa = xyz[ta.x], xb = xyz[ta.y];
-            float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
-            const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
-            float3 acc = make_float3(0.f, 0.f, 0.f);
-            for (int i = ta.z; i < ta.w; i++) {
-                const float4 x = xyz[i], g = grd[i];
-                const float3 d = make_float3(x.x - xb.x, x.y - xb.y, x.z - xb.z);
-                acc.x += d.y * g.z - d.z * g.y;
-                acc.y += d.z * g.x - d.x * g.z;
-                acc.z += d.x * g.y - d.y * g.x;
+        } else {
+            // any N: two-level inclusive scan of (g, (x - t) x g) over the
+            // depth-first atom order (32-atom segments by warp shuffles,
+            // then segment offsets), then range differences per torsion
+            group_sync<TPP>(group);
+            float *seg = reinterpret_cast<float *>(P + L.p_seg);
+            const int nseg = (N + 31) >> 5, lane = gt & 31;
+            for (int sgi = gt >> 5; sgi < nseg; sgi += TPP / 32) {
+                const int i = 32 * sgi + lane;
+                float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (i < N) {
+                    const float4 g4 = grd[i], t4 = tq[i];
+                    w[0] = g4.x; w[1] = g4.y; w[2] = g4.z;
+                    w[3] = t4.x; w[4] = t4.y; w[5] = t4.z;
+                }
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) {
+                        const float y = __shfl_up_sync(0xffffffffu, w[c], off);
+                        if (lane >= off) w[c] += y;
+                    }
+                }
+                if (i < N) {
+                    grd[i] = make_float4(w[0], w[1], w[2], 0.f);
+                    tq[i] = make_float4(w[3], w[4], w[5], 0.f);
+                }
+                if (lane == 31) {
+#pragma unroll
+                    for (int c = 0; c < 6; c++) seg[8 * sgi + c] = w[c];
+                }
             }
-            ggrad[6 + k] = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
+            group_sync<TPP>(group);
+            for (int k = gt; k < T; k += TPP) {
+                const int4 ta = s_tat[k];
+                float gk = 0.f;
+                if (ta.w > ta.z) {
+                    float sm6[6];
+                    const int hi = ta.w - 1, lo = ta.z - 1;
+                    const float4 gh = grd[hi], th = tq[hi];
+                    sm6[0] = gh.x; sm6[1] = gh.y; sm6[2] = gh.z;
+                    sm6[3] = th.x; sm6[4] = th.y; sm6[5] = th.z;
+                    for (int s2 = 0; s2 < (hi >> 5); s2++)
+                        for (int c = 0; c < 6; c++) sm6[c] += seg[8 * s2 + c];
+                    if (lo >= 0) {
+                        const float4 gl = grd[lo], tl = tq[lo];
+                        sm6[0] -= gl.x; sm6[1] -= gl.y; sm6[2] -= gl.z;
+                        sm6[3] -= tl.x; sm6[4] -= tl.y; sm6[5] -= tl.z;
+                        for (int s2 = 0; s2 < (lo >> 5); s2++)
+                            for (int c = 0; c < 6; c++) sm6[c] -= seg[8 * s2 + c];
+                    }
+                    const float4 xa = xyz[ta.x], xb = xyz[ta.y];
+                    const float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
+                    const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
+                    const float3 bt = make_float3(xb.x - tr.x, xb.y - tr.y, xb.z - tr.z);
+                    const float3 acc = make_float3(sm6[3] - (bt.y * sm6[2] - bt.z * sm6[1]),
+                                                   sm6[4] - (bt.z * sm6[0] - bt.x * sm6[2]),
+                                                   sm6[5] - (bt.x * sm6[1] - bt.y * sm6[0]));
+                    gk = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
+                }
+                ggrad[6 + k] = gk;
+            }
         }
 
         // 5. one reduce-and-broadcast of the 8-vector

@@ -1,0 +1,57 @@
+"""Reduction micro-benchmark (the test kernel of Sec. 5.2): every thread of a
+block holds one four-element vector and the block computes the sum that every
+thread receives.  Times each variant for block sizes 64..1024 and reports the
+speed-up over the per-component shuffle + shared-atomic reduction profiled in
+Sec. 3.
+
+    python -m paper_2410_10447_gb300.reduce_bench [--reps 1000] [--waves 4]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    import torch
+
+    import paper_2410_10447_gb300 as P
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--reps", type=int, default=1000, help="reductions per launch")
+    ap.add_argument("--waves", type=int, default=4, help="blocks = 152 x waves")
+    ap.add_argument("--threads", default="64,128,256,512,1024")
+    a = ap.parse_args(argv)
+    P.load(build=True)
+    ctx = P.Context(0)
+    names = {"paper_reducefs": P.REDUCE4_PAPER_FS, "shfl": 0, "mma_tf32x2": 1, "mma_bf16x3": 2}
+    res = {}
+    for th in map(int, a.threads.split(",")):
+        nb = 152 * a.waves
+        x = torch.randn(nb * th * 4, device="cuda")
+        row = {}
+        for name, v in names.items():
+            out = ctx.reduce4_bench_dev(v, x, th, reps=a.reps)
+            ms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.reduce4_bench_dev(v, x, th, reps=a.reps, out=out)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row[name] = min(ms) * 1e3 / a.reps   # microseconds per block-wide reduction wave
+        base = row["paper_reducefs"]
+        res[th] = {k: {"us_per_reduction": v, "speedup_vs_reducefs": base / v} for k, v in row.items()}
+        print(th, {k: round(base / v, 2) for k, v in row.items()}, flush=True)
+    print(json.dumps({"blocks": 152 * a.waves, "reps": a.reps, "results": res}), flush=True)
+
+
+if __name__ == "__main__":
+    main()
