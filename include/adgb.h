@@ -332,8 +332,8 @@ int batch_release(adgb_ctx *ctx, int batch_id);
  * serve_start creates a server on ctx's device with its own host thread and
  * stream.  The thread runs ticks; a tick advances every active job by one
  * step of its Lamarckian GA (initial population, or one generation), runs
- * ONE multi-ligand local-search launch over the individuals of all active
- * jobs, updates each job's run bests and evaluation counts, and finishes the
+ * one multi-ligand local-search launch per ligand-size class over the
+ * individuals of all active jobs, updates each job's run bests and evaluation counts, and finishes the
  * jobs whose runs are done (FP64 rescoring, results copied to host, device
  * memory released).  Queued jobs are admitted in arrival order whenever
  * their device memory fits the server's budget and the active-job cap.
@@ -362,7 +362,7 @@ typedef struct adgb_server adgb_server;
 typedef struct {
     int max_active_jobs;          /* 0: limited by the memory budget only */
     long long mem_budget_bytes;   /* 0: a quarter of the free device memory at start */
-    int threads_per_pose;         /* 0: 32 */
+    int threads_per_pose;         /* 0: by ligand size (32 up to 32 atoms, 64 up to 96, else 128) */
     int poses_per_block;          /* 0: 128 / threads_per_pose */
     int reduce_variant;           /* -1: the context default */
 } adgb_serve_options;

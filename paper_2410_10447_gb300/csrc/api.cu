@@ -311,6 +311,22 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         h.pairs[p] = (uint32_t)inv[i] | (uint32_t)inv[j] << 8 |
                      (uint32_t)(ti * ADGB_MAX_TYPES + tj) << 16 | hb << 24;
     }
+    // A pair list longer than one chunk is stored in a fixed pseudo-random
+    // order (sorted by a 64-bit mix of the atom indices), so that every chunk
+    // touches the atoms about evenly and no owner thread carries a chunk's
+    // gather alone.  One chunk keeps the caller's order.
+    if (NP > PAIR_CHUNK) {
+        auto mix = [](uint64_t x) {   // splitmix64 finaliser
+            x += 0x9E3779B97F4A7C15ull;
+            x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+            x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+            return x ^ (x >> 31);
+        };
+        std::vector<std::pair<uint64_t, uint32_t>> keyed(NP);
+        for (int p = 0; p < NP; p++) keyed[p] = {mix(h.pairs[p] & 0xffff), h.pairs[p]};
+        std::sort(keyed.begin(), keyed.end());
+        for (int p = 0; p < NP; p++) h.pairs[p] = keyed[p].second;
+    }
     // incidence lists per chunk of PAIR_CHUNK pairs: for every chunk and atom
     // the chunk's pairs it belongs to, ascending (chunk-local index, side)
     {

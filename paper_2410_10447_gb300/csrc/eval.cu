@@ -72,41 +72,51 @@ __device__ __forceinline__ void rotate_about(float3 &p, float4 k4, float4 b4, fl
     p.z += c.x * kv.z + c.y * kkv.z;
 }
 
-// Intermolecular term of one atom: the atom type's map plus q times e plus
-// |q| times d, trilinearly interpolated at the point clamped onto the grid;
-// a point outside pays W_OUT times its squared distance to the grid.
-__device__ __forceinline__ float inter_atom(const RecDev &R, int t, float q, float3 x,
-                                            float3 &g) {
+// Grid cell of a point: clamped onto the grid, cell origin index, fractional
+// position, inside flags, and the out-of-grid penalty and its gradient.
+struct CellPos {
+    size_t cell;
+    float f[3], gout[3], pen;
+    bool ins[3];
+};
+
+__device__ __forceinline__ CellPos locate(const RecDev &R, float3 x) {
     const float xs[3] = {x.x, x.y, x.z};
     const int n[3] = {R.nx, R.ny, R.nz};
-    float f[3], gout[3], pen = 0.f;
-    bool ins[3];
+    CellPos c;
+    c.pen = 0.f;
     int i0[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         const float xc = fminf(fmaxf(xs[d], R.lo[d]), R.hi[d]);
-        ins[d] = xs[d] >= R.lo[d] && xs[d] <= R.hi[d];
+        c.ins[d] = xs[d] >= R.lo[d] && xs[d] <= R.hi[d];
         const float dd = xs[d] - xc;
-        pen += dd * dd;
-        gout[d] = 2.f * ADGB_W_OUT * dd;
+        c.pen += dd * dd;
+        c.gout[d] = 2.f * ADGB_W_OUT * dd;
         const float u = (xc - R.lo[d]) * R.inv_h;
-        int c = (int)u;  // u >= 0
-        c = c > n[d] - 2 ? n[d] - 2 : c;
-        i0[d] = c;
-        f[d] = u - (float)c;
+        int k = (int)u;  // u >= 0
+        k = k > n[d] - 2 ? n[d] - 2 : k;
+        i0[d] = k;
+        c.f[d] = u - (float)k;
     }
-    const size_t cell = ((size_t)i0[2] * (R.ny - 1) + i0[1]) * (R.nx - 1) + i0[0];
-    const float4 *cp = reinterpret_cast<const float4 *>(R.cells + cell * (size_t)R.M * 8);
-    const float4 t0 = __ldg(cp + 2 * t), t1 = __ldg(cp + 2 * t + 1);
-    const float4 e0 = __ldg(cp + 2 * (R.M - 2)), e1 = __ldg(cp + 2 * (R.M - 2) + 1);
-    const float4 d0 = __ldg(cp + 2 * (R.M - 1)), d1 = __ldg(cp + 2 * (R.M - 1) + 1);
+    c.cell = ((size_t)i0[2] * (R.ny - 1) + i0[1]) * (R.nx - 1) + i0[0];
+    return c;
+}
+
+// Intermolecular term of one atom from its cell's corner values (type map
+// t0/t1, e map e0/e1, d map d0/d1; corner c = cx + 2 cy + 4 cz): the type's
+// map plus q times e plus |q| times d, trilinearly interpolated at the point
+// clamped onto the grid; a point outside pays W_OUT times its squared
+// distance to the grid.
+__device__ __forceinline__ float inter_from_corners(const RecDev &R, const CellPos &c, float q,
+                                                    float4 t0, float4 t1, float4 e0, float4 e1,
+                                                    float4 d0, float4 d1, float3 &g) {
     const float aq = fabsf(q);
-    // corner c = cx + 2 cy + 4 cz; w = map_t + q e + |q| d at that corner
     const float w0 = t0.x + q * e0.x + aq * d0.x, w1 = t0.y + q * e0.y + aq * d0.y;
     const float w2 = t0.z + q * e0.z + aq * d0.z, w3 = t0.w + q * e0.w + aq * d0.w;
     const float w4 = t1.x + q * e1.x + aq * d1.x, w5 = t1.y + q * e1.y + aq * d1.y;
     const float w6 = t1.z + q * e1.z + aq * d1.z, w7 = t1.w + q * e1.w + aq * d1.w;
-    const float fx = f[0], fy = f[1], fz = f[2];
+    const float fx = c.f[0], fy = c.f[1], fz = c.f[2];
     const float x00 = w1 - w0, x10 = w3 - w2, x01 = w5 - w4, x11 = w7 - w6;
     const float c00 = w0 + fx * x00, c10 = w2 + fx * x10;
     const float c01 = w4 + fx * x01, c11 = w6 + fx * x11;
@@ -117,10 +127,23 @@ __device__ __forceinline__ float inter_atom(const RecDev &R, int t, float q, flo
     const float dfx = dx0 + fz * (dx1 - dx0);
     const float dfy = y0 + fz * (y1 - y0);
     const float dfz = c1 - c0;
-    g.x = (ins[0] ? dfx * R.inv_h : 0.f) + gout[0];
-    g.y = (ins[1] ? dfy * R.inv_h : 0.f) + gout[1];
-    g.z = (ins[2] ? dfz * R.inv_h : 0.f) + gout[2];
-    return val + ADGB_W_OUT * pen;
+    g.x = (c.ins[0] ? dfx * R.inv_h : 0.f) + c.gout[0];
+    g.y = (c.ins[1] ? dfy * R.inv_h : 0.f) + c.gout[1];
+    g.z = (c.ins[2] ? dfz * R.inv_h : 0.f) + c.gout[2];
+    return val + ADGB_W_OUT * c.pen;
+}
+
+__device__ __forceinline__ const float4 *cell_ptr(const RecDev &R, size_t cell) {
+    return reinterpret_cast<const float4 *>(R.cells + cell * (size_t)R.M * 8);
+}
+
+// Grid term read straight from global memory (L2).
+__device__ __forceinline__ float inter_atom(const RecDev &R, int t, float q, float3 x, float3 &g) {
+    const CellPos c = locate(R, x);
+    const float4 *cp = cell_ptr(R, c.cell);
+    return inter_from_corners(R, c, q, __ldg(cp + 2 * t), __ldg(cp + 2 * t + 1),
+                              __ldg(cp + 2 * (R.M - 2)), __ldg(cp + 2 * (R.M - 2) + 1),
+                              __ldg(cp + 2 * (R.M - 1)), __ldg(cp + 2 * (R.M - 1) + 1), g);
 }
 
 // One intramolecular pair: 12-6 (12-10 for donor-acceptor pairs) with

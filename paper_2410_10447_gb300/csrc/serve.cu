@@ -96,6 +96,7 @@ struct adgb_server {
     int device = 0;
     adgb_serve_options opts{};
     EvalCfg cfg{32, 4, 0, 1, 0};
+    bool forced_shape = false;   // threads/poses a block set by the caller: one class
     size_t budget = 0, used = 0;
     std::thread th;
     std::mutex mu;
@@ -181,50 +182,78 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
             if (e != cudaSuccess) return e;
         }
     }
-    // one multi-ligand local-search launch over every active individual
-    int n_items = 0;
-    for (Job *j : act) n_items += (j->d.n_runs * j->d.pop + s->cfg.ppb - 1) / s->cfg.ppb;
-    e = grow_tables(s, n_items, (int)act.size());
-    if (e != cudaSuccess) return e;
-    int budget = 1024, k = 0;
-    for (size_t u = 0; u < act.size(); u++) {
-        Job *j = act[u];
-        const int src = j->gen < 0 ? 0 : (j->cur ^ 1);   // population the LS works on
-        s->h_ligs[u] = j->lig;
-        s->h_recs[u] = j->rec;
-        budget = std::max(budget, SmemLayout::choose(j->lig.n_atoms, j->lig.n_tors, j->lig.n_pairs,
-                                                     s->cfg.ppb, s->cfg.tpp / 32).total);
-        const int n = j->d.n_runs * j->d.pop;
-        const int cost = j->lig.n_pairs + 8 * j->lig.n_atoms + 64;
-        for (int p = 0; p < n; p += s->cfg.ppb) {
-            WorkItem &w = s->h_items[k++];
-            w.lig = (int)u;
-            w.rec = (int)u;
-            w.count = std::min(s->cfg.ppb, n - p);
-            w.gstride = j->G;
-            w.genes = j->w.genes[src] + (size_t)p * j->G;
-            w.energy = j->w.energy + p;
-            w.iters = j->w.iters + p;
-            w.iters_all = 0;
-            w.cost = cost;
-            w.rho = j->d.rho;
-            w.eps = j->d.eps;
+    // multi-ligand local-search launches over every active individual: one
+    // per size class (one warp a genotype up to 32 atoms, 64 threads up to
+    // 96, 128 above), each a persistent launch over that class's work items
+    // (a job's class depends on its ligand alone)
+    std::vector<int> cls(act.size());
+    EvalCfg ccfg[3];
+    for (int c = 0; c < 3; c++) {
+        ccfg[c] = s->cfg;
+        if (!s->forced_shape) {
+            ccfg[c].tpp = c == 0 ? 32 : (c == 1 ? 64 : 128);
+            ccfg[c].ppb = 128 / ccfg[c].tpp;
         }
     }
-    std::stable_sort(s->h_items, s->h_items + n_items, [](const WorkItem &x, const WorkItem &y) {
-        return x.cost > y.cost;
-    });
+    int n_items = 0;
+    for (size_t u = 0; u < act.size(); u++) {
+        const int N = act[u]->lig.n_atoms;
+        cls[u] = s->forced_shape ? 0 : (N <= 32 ? 0 : (N <= 96 ? 1 : 2));
+        n_items += (act[u]->d.n_runs * act[u]->d.pop + ccfg[cls[u]].ppb - 1) / ccfg[cls[u]].ppb;
+    }
+    e = grow_tables(s, n_items, (int)act.size());
+    if (e != cudaSuccess) return e;
+    for (size_t u = 0; u < act.size(); u++) {
+        s->h_ligs[u] = act[u]->lig;
+        s->h_recs[u] = act[u]->rec;
+    }
+    int k = 0, first[3], count[3], budget[3];
+    for (int c = 0; c < 3; c++) {
+        first[c] = k;
+        budget[c] = 1024;
+        const EvalCfg &cf = ccfg[c];
+        for (size_t u = 0; u < act.size(); u++) {
+            if (cls[u] != c) continue;
+            Job *j = act[u];
+            const int src = j->gen < 0 ? 0 : (j->cur ^ 1);   // population the LS works on
+            budget[c] = std::max(budget[c], SmemLayout::choose(j->lig.n_atoms, j->lig.n_tors,
+                                                               j->lig.n_pairs, cf.ppb, cf.tpp / 32).total);
+            const int n = j->d.n_runs * j->d.pop;
+            const int cost = j->lig.n_pairs + 8 * j->lig.n_atoms + 64;
+            for (int p = 0; p < n; p += cf.ppb) {
+                WorkItem &w = s->h_items[k++];
+                w.lig = (int)u;
+                w.rec = (int)u;
+                w.count = std::min(cf.ppb, n - p);
+                w.gstride = j->G;
+                w.genes = j->w.genes[src] + (size_t)p * j->G;
+                w.energy = j->w.energy + p;
+                w.iters = j->w.iters + p;
+                w.iters_all = 0;
+                w.cost = cost;
+                w.rho = j->d.rho;
+                w.eps = j->d.eps;
+            }
+        }
+        count[c] = k - first[c];
+        std::stable_sort(s->h_items + first[c], s->h_items + k, [](const WorkItem &x, const WorkItem &y) {
+            return x.cost > y.cost;
+        });
+    }
     e = cudaMemcpyAsync(s->d_items, s->h_items, sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_ligs, s->h_ligs, sizeof(LigDev) * act.size(), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_recs, s->h_recs, sizeof(RecDev) * act.size(), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return e;
-    const int grid = items_grid(s->cfg, budget, s->device);
-    if (grid < 1) return cudaErrorInvalidConfiguration;
-    e = launch_eval_items(s->d_items, n_items, s->d_ligs, s->d_recs, s->d_counter, s->cfg, budget,
-                          grid, s->stream);
-    if (e != cudaSuccess) return e;
+    for (int c = 0; c < 3; c++) {
+        if (!count[c]) continue;
+        const int grid = items_grid(ccfg[c], budget[c], s->device);
+        if (grid < 1) return cudaErrorInvalidConfiguration;
+        e = launch_eval_items(s->d_items + first[c], count[c], s->d_ligs, s->d_recs, s->d_counter,
+                              ccfg[c], budget[c], grid, s->stream);
+        if (e != cudaSuccess) return e;
+    }
     s->items_run += n_items;
     // accounting per job
     for (Job *j : act) {
@@ -371,6 +400,7 @@ int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out
         return ADGB_EINVAL;
     }
     s->cfg = EvalCfg{tpp, ppb, variant, 1, 0};
+    s->forced_shape = s->opts.threads_per_pose > 0 || s->opts.poses_per_block > 0;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
