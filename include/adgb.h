@@ -401,13 +401,24 @@ int dock_forget(adgb_server *server, long long job_id);
  * every thread receives it.  in [n_blocks][threads][4] float32, out the same
  * shape (each thread's copy of its block's sum).  The reduction is repeated
  * `reps` times inside the kernel (every repetition reduces the same input),
- * so that its own cost dominates a timing.  variant: ADGB_REDUCE_* or
- * ADGB_REDUCE4_PAPER_FS, the per-component shuffle + shared-memory atomic
- * reduction that Sec. 3 profiles (three barriers per component).
+ * so that its own cost dominates a timing.  variant:
+ *   ADGB_REDUCE_SHFL / _MMA_TF32X2 / _MMA_BF16X3 - this library's warp-level
+ *     forms (the local search's reductions) applied at warp and block level;
+ *   ADGB_REDUCE4_PAPER_FS - the per-component shuffle + shared-memory atomic
+ *     reduction that Sec. 3 profiles (three barriers per component);
+ *   ADGB_REDUCE4_PAPER_HALF - the matrix form of Sec. 4.2 as the paper runs
+ *     it: operands and accumulators V = A.P, W = Q.V in FP16 (about three
+ *     significant digits; a total above 65504 in magnitude becomes inf);
+ *   ADGB_REDUCE4_TCGEN05_TF32X2 - one block-wide tcgen05.mma chain on the
+ *     fifth-generation tensor cores (split TF32 operands, FP32 accumulation
+ *     in tensor memory); needs threads to be a multiple of 64.  Should the
+ *     wait for the tensor core ever give up, the block's outputs are NaN.
  * threads: 32..1024, a multiple of 32; reps >= 1.
  * Errors: EINVAL, EDEVICE.
  */
 #define ADGB_REDUCE4_PAPER_FS 100
+#define ADGB_REDUCE4_PAPER_HALF 101
+#define ADGB_REDUCE4_TCGEN05_TF32X2 102
 int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
                       int threads, int n_blocks, int reps, float *out_dev,
                       adgb_stream stream);

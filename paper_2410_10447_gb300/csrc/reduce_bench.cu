@@ -6,12 +6,22 @@
 //  - this library's FP32 shuffle form (reduce-scatter inside each warp, one
 //    barrier, every warp finishes the cross-warp sum itself);
 //  - the tensor-core forms (warp_sum8 with TF32x2 / BF16x3 operands) at
-//    both levels, also with a single barrier.
+//    both levels, also with a single barrier;
+//  - the paper's own matrix form (Sec. 4.2) in FP16: V <- A.P + V over
+//    64-vector chunks, then W <- Q.V, with FP16 operands and accumulators,
+//    one warp issuing the products and two barriers;
+//  - a block-wide fifth-generation tensor-core form: every thread's split
+//    TF32 vector goes into one shared-memory operand, a single thread issues
+//    tcgen05.mma with an all-ones TMEM operand, and each thread reads the
+//    totals from its own TMEM row (one barrier and one mbarrier wait).
 // `reps` repeats the reduction inside the kernel so that its cost, not the
 // loads and stores around it, dominates the measured time; with tiny = 0
 // every repetition reduces the same input.
 #include "adgb_internal.cuh"
 #include "reduce.cuh"
+#include "tcgen05.cuh"
+
+#include <cuda_fp16.h>
 
 namespace adgb {
 
@@ -72,6 +82,211 @@ __global__ void __launch_bounds__(1024) reduce4_kernel(const float4 *in, float4 
     out[idx] = tot;
 }
 
+// ---------------------------------------------------------------------------
+// Sec. 4.2 in FP16.  Thread t stores (x, y, z, e) of its vector as four
+// halves at A[4t..4t+3], so every 64 threads fill one 16x16 column-major
+// matrix A (column j = vectors 4j..4j+3).  Warp 0 forms V <- A.P + V over
+// the chunks (P all ones, only its first 8 columns are needed because all
+// columns of V are equal) and W <- Q.V (Q = 4x4 blocks of I4), both with
+// FP16 accumulators; W's first column holds the four totals.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mma_f16acc_16x8x16(uint32_t d[2], uint32_t a0, uint32_t a1,
+                                                   uint32_t a2, uint32_t a3, uint32_t b0,
+                                                   uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f16.f16.f16.f16 "
+        "{%0,%1}, {%2,%3,%4,%5}, {%6,%7}, {%0,%1};\n"
+        : "+r"(d[0]), "+r"(d[1])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t pack_h2(__half lo, __half hi) {
+    return (uint32_t)__half_as_ushort(lo) | ((uint32_t)__half_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ uint32_t q_pair(int r, int s) {  // (Q[r][s], Q[r][s+1])
+    const __half one = __ushort_as_half(0x3C00), zero = __ushort_as_half(0);
+    return pack_h2((r & 3) == (s & 3) ? one : zero, (r & 3) == ((s + 1) & 3) ? one : zero);
+}
+
+__global__ void __launch_bounds__(1024) reduce4_half_kernel(const float4 *in, float4 *out,
+                                                            int reps, float tiny) {
+    extern __shared__ __align__(16) unsigned char hsm[];
+    const int chunks = (blockDim.x + 63) >> 6;
+    __half *A = reinterpret_cast<__half *>(hsm);     // [chunks][16][16] column-major
+    __half *res = A + chunks * 256;                  // W[0..3][0]
+    const int tid = threadIdx.x, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    for (int i = blockDim.x * 4 + tid; i < chunks * 256; i += blockDim.x) A[i] = __float2half(0.f);
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + tid;
+    const float4 x0 = in[idx];
+    float4 x = x0, tot = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < reps; r++) {
+        uint2 h;
+        h.x = pack_h2(__float2half_rn(x.x), __float2half_rn(x.y));
+        h.y = pack_h2(__float2half_rn(x.z), __float2half_rn(x.w));
+        reinterpret_cast<uint2 *>(A)[tid] = h;
+        __syncthreads();
+        if (tid < 32) {
+            const uint32_t ones = 0x3C003C00u;
+            uint32_t v[2] = {0u, 0u};
+            for (int q = 0; q < chunks; q++) {
+                const __half *Aq = A + q * 256;
+                auto at = [&](int row, int col) { return Aq[col * 16 + row]; };
+                const uint32_t a0 = pack_h2(at(g, 2 * t), at(g, 2 * t + 1));
+                const uint32_t a1 = pack_h2(at(g + 8, 2 * t), at(g + 8, 2 * t + 1));
+                const uint32_t a2 = pack_h2(at(g, 2 * t + 8), at(g, 2 * t + 9));
+                const uint32_t a3 = pack_h2(at(g + 8, 2 * t + 8), at(g + 8, 2 * t + 9));
+                mma_f16acc_16x8x16(v, a0, a1, a2, a3, ones, ones);
+            }
+            // B operand of Q.V: rows 2t, 2t+1 (and +8) of V, any column; row
+            // k of V sits in lanes 4k..4k+3 (k < 8: v[0], else v[1]).
+            const uint32_t r0 = __shfl_sync(0xffffffffu, v[0], 8 * t);
+            const uint32_t r1 = __shfl_sync(0xffffffffu, v[0], 8 * t + 4);
+            const uint32_t r8 = __shfl_sync(0xffffffffu, v[1], 8 * t);
+            const uint32_t r9 = __shfl_sync(0xffffffffu, v[1], 8 * t + 4);
+            const uint32_t b0 = (r0 & 0xFFFFu) | (r1 << 16);
+            const uint32_t b1 = (r8 & 0xFFFFu) | (r9 << 16);
+            uint32_t w[2] = {0u, 0u};
+            mma_f16acc_16x8x16(w, q_pair(g, 2 * t), q_pair(g + 8, 2 * t), q_pair(g, 2 * t + 8),
+                               q_pair(g + 8, 2 * t + 8), b0, b1);
+            if (t == 0 && g < 4) res[g] = __ushort_as_half((unsigned short)(w[0] & 0xFFFFu));
+        }
+        __syncthreads();
+        tot = make_float4(__half2float(res[0]), __half2float(res[1]), __half2float(res[2]),
+                          __half2float(res[3]));
+        x.x = x0.x + tot.x * tiny;
+        x.y = x0.y + tot.y * tiny;
+        x.z = x0.z + tot.z * tiny;
+        x.w = x0.w + tot.w * tiny;
+    }
+    out[idx] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide reduction on the fifth-generation tensor cores.
+//
+// D[128 x N] = A[128 x K] . B[N x K]^T with A all ones (in TMEM) and B the
+// block's data: K runs over threads, so every row of D holds column sums of
+// B, and row m of D sits in TMEM lane m.  Each warp reads the rows of its
+// own lane quadrant, so every thread receives the totals without a second
+// stage or a broadcast.  Each thread contributes 8 rows' worth of one K
+// column: its four components as TF32 hi and lo terms (hi = x rounded to
+// TF32, lo = (x - hi) rounded to TF32); products with 1.0 are exact and D
+// accumulates in FP32.  The block's threads are split into NG groups (one
+// group = an 8-row atom along N), warp w filling K columns 32(w / NG) ..
+// +31 of group w % NG, so N = 8 NG and K = blockDim / NG.
+//
+// B uses the 128-byte swizzled K-major layout: a warp's 32 threads x 8 rows
+// fill exactly one 1024-byte atom, row r of thread (lane) at chunk
+// (lane / 4) ^ r, which makes each of the 8 per-thread stores free of bank
+// conflicts.  MMA s covers K columns 8s .. 8s+7: atom column s / 4 and a
+// 32-byte offset (s % 4) inside the atom rows.
+//
+// A completion wait that gives up (it never should) turns the outputs into
+// NaN; the TMEM is still released.
+// ---------------------------------------------------------------------------
+constexpr int TC_WAIT_LIMIT = 1 << 20;
+
+template <int NG>
+struct TcShape {
+    static constexpr int N = 8 * NG;
+    static constexpr int NCOLS = N + 8 <= 32 ? 32 : (N + 8 <= 64 ? 64 : 128);
+};
+
+__host__ __device__ constexpr int tc_smem_bytes(int threads) { return 16 + 1024 + 32 * threads; }
+
+template <int NG>
+__global__ void __launch_bounds__(1024) reduce4_tc05_kernel(const float4 *in, float4 *out,
+                                                            int reps, float tiny) {
+    constexpr int N = TcShape<NG>::N, NCOLS = TcShape<NG>::NCOLS;
+    extern __shared__ __align__(16) unsigned char tsm[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm);
+    uint32_t *slot = reinterpret_cast<uint32_t *>(tsm + 8);
+    const uint32_t base_s = tc05::smem_u32(tsm);
+    const uint32_t b_s = (base_s + 16u + 1023u) & ~1023u;
+    unsigned char *bbuf = tsm + (b_s - base_s);
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int n_mma = blockDim.x / (8 * NG);
+
+    if (w == 0) {
+        tc05::alloc(slot, NCOLS);
+        tc05::relinquish();
+    }
+    if (tid == 0) tc05::mbar_init(mbar, 1);
+    tc05::fence_before();
+    __syncthreads();
+    tc05::fence_after();
+    const uint32_t taddr = *slot;
+    if (w < 4) {   // A = ones in columns [N, NCOLS) of this warp's lane quadrant
+        uint32_t one[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) one[i] = 0x3F800000u;
+        for (int c = N; c < NCOLS; c += 16) tc05::st16(tc05::lane_addr(taddr, w, c), one);
+        tc05::wait_st();
+    }
+
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + tid;
+    const float4 x0 = in[idx];
+    float4 x = x0, tot = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned char *mine = bbuf + (w / NG) * (NG * 1024) + (w % NG) * 1024 + (lane & 3) * 4;
+    const int cq = lane >> 2;
+    const uint32_t idesc = tc05::idesc_tf32(128, N);
+    bool bad = false;
+    int r = 0;
+    for (; r < reps; r++) {
+        const float v[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const uint32_t hi = to_tf32(v[c]);
+            const uint32_t lo = to_tf32(v[c] - __uint_as_float(hi));
+            *reinterpret_cast<uint32_t *>(mine + c * 128 + ((cq ^ c) << 4)) = hi;
+            *reinterpret_cast<uint32_t *>(mine + (c + 4) * 128 + ((cq ^ (c + 4)) << 4)) = lo;
+        }
+        tc05::fence_proxy_async_smem();
+        tc05::fence_before();
+        if (__syncthreads_or(bad)) break;
+        if (tid == 0) {
+            tc05::fence_after();
+            for (int s = 0; s < n_mma; s++) {
+                const uint32_t bs = b_s + (uint32_t)((s >> 2) * NG * 1024 + (s & 3) * 32);
+                tc05::mma_tf32_ts(taddr, taddr + N, tc05::desc_sw128(bs, 1024), idesc, s > 0);
+            }
+            tc05::commit(mbar);
+        }
+        if (!__all_sync(0xffffffffu, tc05::mbar_wait(mbar, r & 1, TC_WAIT_LIMIT))) {
+            bad = true;
+            continue;
+        }
+        tc05::fence_after();
+        float hs[4] = {0.f, 0.f, 0.f, 0.f}, ls[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < N / 16; j++) {
+            float d[16];
+            tc05::ld16_wait(tc05::lane_addr(taddr, w & 3, 16 * j), d);
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                hs[c] += d[c] + d[8 + c];
+                ls[c] += d[4 + c] + d[12 + c];
+            }
+        }
+        tc05::fence_before();
+        tot = make_float4(hs[0] + ls[0], hs[1] + ls[1], hs[2] + ls[2], hs[3] + ls[3]);
+        x.x = x0.x + tot.x * tiny;
+        x.y = x0.y + tot.y * tiny;
+        x.z = x0.z + tot.z * tiny;
+        x.w = x0.w + tot.w * tiny;
+    }
+    if (bad) {   // let the MMAs in flight finish (bounded) before TMEM is released
+        (void)tc05::mbar_wait(mbar, (r - 1) & 1, TC_WAIT_LIMIT);   // phase r - 1 gave up
+        tot = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
+                          __int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    }
+    __syncthreads();
+    tc05::fence_after();
+    if (w == 0) tc05::dealloc(taddr, NCOLS);
+    out[idx] = tot;
+}
+
 template <int VAR>
 static cudaError_t launch_r(const float *in, int threads, int n_blocks, int reps, float *out,
                             cudaStream_t s) {
@@ -82,6 +297,46 @@ static cudaError_t launch_r(const float *in, int threads, int n_blocks, int reps
     k<<<n_blocks, threads, smem, s>>>(reinterpret_cast<const float4 *>(in),
                                       reinterpret_cast<float4 *>(out), reps, 0.f);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_half(const float *in, int threads, int n_blocks, int reps, float *out,
+                               cudaStream_t s) {
+    const int smem = (((threads + 63) / 64) * 256 + 8) * 2;
+    reduce4_half_kernel<<<n_blocks, threads, smem, s>>>(reinterpret_cast<const float4 *>(in),
+                                                        reinterpret_cast<float4 *>(out), reps, 0.f);
+    return cudaGetLastError();
+}
+
+// Shared memory is padded so that no more CTAs are resident on an SM than
+// its 512 TMEM columns can serve at once (tcgen05.alloc would otherwise
+// wait for a resident CTA to finish).
+template <int NG>
+static cudaError_t launch_tc(const float *in, int threads, int n_blocks, int reps, float *out,
+                             cudaStream_t s) {
+    int dev = 0, sm_smem = 0, reserved = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e != cudaSuccess) return e;
+    const int fit = 512 / TcShape<NG>::NCOLS;
+    int smem = tc_smem_bytes(threads);
+    const int floor_smem = sm_smem / (fit + 1) - reserved + 16;
+    if (smem < floor_smem) smem = floor_smem;
+    auto k = reduce4_tc05_kernel<NG>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<n_blocks, threads, smem, s>>>(reinterpret_cast<const float4 *>(in),
+                                      reinterpret_cast<float4 *>(out), reps, 0.f);
+    return cudaGetLastError();
+}
+
+// Thread groups for the tcgen05 form: the most (up to 8) that divide the
+// block's warps evenly; a block needs an even number of warps (N >= 16).
+static int tc_groups(int threads) {
+    const int W = threads / 32;
+    return W % 8 == 0 ? 8 : (W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 0));
 }
 
 cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int n_blocks,
@@ -95,6 +350,15 @@ cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int 
             return launch_r<ADGB_REDUCE_MMA_TF32X2>(in, threads, n_blocks, reps, out, s);
         case ADGB_REDUCE_MMA_BF16X3:
             return launch_r<ADGB_REDUCE_MMA_BF16X3>(in, threads, n_blocks, reps, out, s);
+        case ADGB_REDUCE4_PAPER_HALF:
+            return launch_half(in, threads, n_blocks, reps, out, s);
+        case ADGB_REDUCE4_TCGEN05_TF32X2:
+            switch (tc_groups(threads)) {
+                case 8: return launch_tc<8>(in, threads, n_blocks, reps, out, s);
+                case 4: return launch_tc<4>(in, threads, n_blocks, reps, out, s);
+                case 2: return launch_tc<2>(in, threads, n_blocks, reps, out, s);
+            }
+            return cudaErrorInvalidValue;
     }
     return cudaErrorInvalidValue;
 }

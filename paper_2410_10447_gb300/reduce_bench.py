@@ -30,14 +30,24 @@ def main(argv=None):
     a = ap.parse_args(argv)
     P.load(build=True)
     ctx = P.Context(0)
-    names = {"paper_reducefs": P.REDUCE4_PAPER_FS, "shfl": 0, "mma_tf32x2": 1, "mma_bf16x3": 2}
+    names = {"paper_reducefs": P.REDUCE4_PAPER_FS, "paper_half": P.REDUCE4_PAPER_HALF,
+             "shfl": 0, "mma_tf32x2": 1, "mma_bf16x3": 2,
+             "tcgen05_tf32x2": P.REDUCE4_TCGEN05_TF32X2}
     res = {}
     for th in map(int, a.threads.split(",")):
         nb = 152 * a.waves
         x = torch.randn(nb * th * 4, device="cuda")
-        row = {}
+        xd = x.double().view(nb, th, 4)
+        exact = xd.sum(dim=1)
+        mag = xd.abs().sum(dim=1)
+        row, err = {}, {}
         for name, v in names.items():
-            out = ctx.reduce4_bench_dev(v, x, th, reps=a.reps)
+            if name == "tcgen05_tf32x2" and th % 64:
+                continue
+            out = ctx.reduce4_bench_dev(v, x, th, reps=1)
+            got = out.view(nb, th, 4)[:, 0, :].double()
+            err[name] = float(((got - exact).abs() / mag).max())
+            ctx.reduce4_bench_dev(v, x, th, reps=a.reps, out=out)
             ms = []
             for _ in range(3):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -48,7 +58,8 @@ def main(argv=None):
                 ms.append(e0.elapsed_time(e1))
             row[name] = min(ms) * 1e3 / a.reps   # microseconds per block-wide reduction wave
         base = row["paper_reducefs"]
-        res[th] = {k: {"us_per_reduction": v, "speedup_vs_reducefs": base / v} for k, v in row.items()}
+        res[th] = {k: {"us_per_reduction": v, "speedup_vs_reducefs": base / v,
+                       "max_err_over_sum_abs": err[k]} for k, v in row.items()}
         print(th, {k: round(base / v, 2) for k, v in row.items()}, flush=True)
     print(json.dumps({"blocks": 152 * a.waves, "reps": a.reps, "results": res}), flush=True)
 

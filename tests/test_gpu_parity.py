@@ -315,17 +315,21 @@ def test_lga_n32_full_batch_sampled(pkg, torch):
 
 
 # --------------------------------------------------------------- reduction
-@pytest.mark.parametrize("variant", [100, 0, 1, 2])
-@pytest.mark.parametrize("threads", [64, 256, 1024])
-def test_reduce4_bench_parity(pkg, torch, variant, threads):
-    ctx = make_ctx(pkg)
-    rng = np.random.default_rng(threads + variant)
-    nb = 19
+def _reduce_inputs(seed, nb, threads):
+    rng = np.random.default_rng(seed)
     x = rng.normal(size=(nb, threads, 4)) * 10.0 ** rng.integers(-3, 4, (nb, threads, 4))
     x[0, :, 1] = 1.0                          # exact small integers
     x[1, ::2, 2] = 1e6                        # cancelling outliers
     x[1, 1::2, 2] = -1e6
-    x = x.astype(np.float32)
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("variant", [100, 0, 1, 2, 102])
+@pytest.mark.parametrize("threads", [64, 192, 256, 384, 1024])
+def test_reduce4_bench_parity(pkg, torch, variant, threads):
+    ctx = make_ctx(pkg)
+    nb = 19
+    x = _reduce_inputs(threads + variant, nb, threads)
     xt = torch.from_numpy(x).cuda()
     out = ctx.reduce4_bench_dev(variant, xt, threads, reps=3).cpu().numpy()
     ref = np.array([[oracle.sum_neumaier(x[b, :, c]) for c in range(4)] for b in range(nb)])
@@ -335,4 +339,47 @@ def test_reduce4_bench_parity(pkg, torch, variant, threads):
         assert np.all(out[b] == out[b, 0]), "every thread gets the same sum"
         assert np.all(np.abs(out[b, 0] - ref[b]) <= tol * scale[b]), (b, out[b, 0], ref[b])
     assert np.all(out[0, 0, 1] == threads)
+    ctx.close()
+
+
+@pytest.mark.parametrize("threads", [32, 64, 96, 256, 1024])
+def test_reduce4_paper_half_within_fp16_bound(pkg, torch, threads):
+    """Sec. 4.2 in FP16: inputs rounded to FP16 (2^-11 relative each), V
+    accumulated over ceil(T/64) chunk products and W = Q.V rounded once more;
+    every rounding is bounded by 2^-11 of the sum of magnitudes it covers,
+    and up to 16 roundings are allowed inside each product."""
+    ctx = make_ctx(pkg)
+    rng = np.random.default_rng(threads)
+    nb = 19
+    x = rng.normal(size=(nb, threads, 4)).astype(np.float32)
+    x[0, :, 1] = 1.0                              # exact in FP16 up to 2048
+    xt = torch.from_numpy(x).cuda()
+    out = ctx.reduce4_bench_dev(pkg.REDUCE4_PAPER_HALF, xt, threads, reps=2).cpu().numpy()
+    ref = x.astype(np.float64).sum(axis=1)
+    scale = np.abs(x.astype(np.float64)).sum(axis=1)
+    n_round = 2 + (threads + 63) // 64 + 16
+    for b in range(nb):
+        assert np.all(out[b] == out[b, 0])
+        assert np.all(np.abs(out[b, 0] - ref[b]) <= n_round * 2.0 ** -11 * scale[b]), b
+    assert np.all(out[0, :, 1] == threads)
+    ctx.close()
+
+
+def test_reduce4_paper_half_overflows_above_fp16_range(pkg, torch):
+    """A total beyond 65504 is not representable in the paper's FP16 V / W."""
+    ctx = make_ctx(pkg)
+    x = np.full((2, 1024, 4), 100.0, np.float32)      # totals 102400
+    x[1] = 1.0                                         # totals 1024: exact
+    out = ctx.reduce4_bench_dev(pkg.REDUCE4_PAPER_HALF, torch.from_numpy(x).cuda(), 1024,
+                                reps=1).cpu().numpy()
+    assert np.all(np.isinf(out[0]))
+    assert np.all(out[1] == 1024.0)
+    ctx.close()
+
+
+def test_reduce4_tcgen05_rejects_odd_warp_counts(pkg, torch):
+    ctx = make_ctx(pkg)
+    x = torch.zeros(96 * 4, device="cuda")
+    with pytest.raises(pkg.AdgbError):
+        ctx.reduce4_bench_dev(pkg.REDUCE4_TCGEN05_TF32X2, x, 96, reps=1)
     ctx.close()
