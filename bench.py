@@ -143,7 +143,7 @@ def profile_traffic(kernel_sha):
 
 def kernel_sha():
     h = hashlib.sha1()
-    for f in ("eval.cu", "reduce.cuh", "adgb_internal.cuh"):
+    for f in ("eval.cu", "reduce.cuh", "tcgen05.cuh", "adgb_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2410_10447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

@@ -54,7 +54,9 @@ enum {
     ADGB_REDUCE_SHFL = 0,       /* FP32 warp shuffles (reduce-scatter + all-gather) */
     ADGB_REDUCE_MMA_TF32X2 = 1, /* tensor-core sum, operands split into 2 TF32 terms, FP32 accumulate */
     ADGB_REDUCE_MMA_BF16X3 = 2, /* tensor-core sum, operands split into 3 BF16 terms, FP32 accumulate */
-    ADGB_REDUCE_N = 3
+    ADGB_REDUCE_TCGEN05 = 3,    /* fifth-generation tensor cores (tcgen05.mma, accumulator in tensor
+                                   memory), operands split into 2 TF32 terms, FP32 accumulate */
+    ADGB_REDUCE_N = 4
 };
 
 /* Limits of one ligand. */

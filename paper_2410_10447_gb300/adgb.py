@@ -20,11 +20,12 @@ _lib = None
 ADGB_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ENOTFOUND", -4: "EDEVICE", -5: "ETIMEOUT",
           -6: "EREJECTED", -7: "ECANCELLED"}
-REDUCE_SHFL, REDUCE_MMA_TF32X2, REDUCE_MMA_BF16X3 = 0, 1, 2
+REDUCE_SHFL, REDUCE_MMA_TF32X2, REDUCE_MMA_BF16X3, REDUCE_TCGEN05 = 0, 1, 2, 3
 REDUCE4_PAPER_FS = 100
 REDUCE4_PAPER_HALF = 101
 REDUCE4_TCGEN05_TF32X2 = 102
-VARIANTS = {"shfl": REDUCE_SHFL, "mma_tf32x2": REDUCE_MMA_TF32X2, "mma_bf16x3": REDUCE_MMA_BF16X3}
+VARIANTS = {"shfl": REDUCE_SHFL, "mma_tf32x2": REDUCE_MMA_TF32X2, "mma_bf16x3": REDUCE_MMA_BF16X3,
+            "tcgen05": REDUCE_TCGEN05}
 LS_RESUME = 1
 
 # the C ABI's exported entry points (checked against include/adgb.h by the tests)

@@ -89,8 +89,10 @@ struct SmemLayout {
 
     static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
+    // mma_stage: room for the mma.sync reductions' per-warp staging tile.
     __host__ __device__ inline void make(int N, int T, int ppb, int warps_per_pose, int ch,
-                                         int np = 0, bool stage_pairs = false) {
+                                         int np = 0, bool stage_pairs = false,
+                                         bool mma_stage = true) {
         const int nch = (np + PAIR_CHUNK - 1) / PAIR_CHUNK;
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
@@ -114,7 +116,7 @@ struct SmemLayout {
         p_ggrad = q; q = al16(q + 4 * MAX_GENES);
         p_sc = q;    q = al16(q + 8 * (ADGB_MAX_TORS + 4));
         p_red = q;   q = al16(q + 4 * 8 * warps_per_pose);
-        p_stage = q; q = al16(q + 4 * 32 * 12 * warps_per_pose);
+        p_stage = q; q = al16(q + (mma_stage ? 4 * 32 * 12 * warps_per_pose : 0));
         chunk = ch > 0 ? ch : 1;
         p_force = q; q = al16(q + 16 * chunk);
         p_tq = q;    q = al16(q + (N > 32 ? 16 * N : 0));
@@ -130,14 +132,20 @@ struct SmemLayout {
     // ligands share the launch.  The host sizes a launch's shared memory to
     // the largest such layout; the device recomputes it per work item.
     static __host__ __device__ inline SmemLayout choose(int N, int T, int np, int ppb,
-                                                        int warps_per_pose) {
+                                                        int warps_per_pose, bool mma_stage) {
         SmemLayout l;
         const bool stage = 8 * np <= 24 * 1024;
         const int ch = np < PAIR_CHUNK ? (np > 1 ? np : 1) : PAIR_CHUNK;
-        l.make(N, T, ppb, warps_per_pose, ch, np, stage);
+        l.make(N, T, ppb, warps_per_pose, ch, np, stage, mma_stage);
         return l;
     }
 };
+
+// Reduction variants that stage each warp's values in shared memory for
+// mma.sync.
+__host__ __device__ inline bool uses_mma_stage(int variant) {
+    return variant == ADGB_REDUCE_MMA_TF32X2 || variant == ADGB_REDUCE_MMA_BF16X3;
+}
 
 // Work item of the multi-ligand local-search kernel: up to poses-per-block
 // genotypes of one ligand against one receptor.

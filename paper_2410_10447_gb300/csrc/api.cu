@@ -393,7 +393,8 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     // keep a block's shared memory within 100 KB so that two blocks fit an SM
     SmemLayout lay;
     for (;; ppb--) {
-        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, cfg.chunk, L.n_pairs, cfg.stage_pairs);
+        lay.make(L.n_atoms, L.n_tors, ppb, cfg.tpp / 32, cfg.chunk, L.n_pairs, cfg.stage_pairs,
+                 uses_mma_stage(variant));
         if (lay.total <= 100 * 1024 || ppb == 1) break;
     }
     cfg.ppb = ppb;
@@ -1100,7 +1101,7 @@ int batch_budget(const Batch &b, const EvalCfg &cfg) {
     int budget = 1024;
     for (size_t u = 0; u < b.ligs.size(); u++)
         budget = std::max(budget, SmemLayout::choose(b.lig_n[u], b.lig_t[u], b.lig_np[u], cfg.ppb,
-                                                     cfg.tpp / 32).total);
+                                                     cfg.tpp / 32, uses_mma_stage(cfg.variant)).total);
     return budget;
 }
 
@@ -1290,8 +1291,9 @@ extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev,
     if (iters < 1 || (b.total > 0 && !genes_dev)) return fail(c, ADGB_EINVAL, "batch_autotune: bad arguments");
     DeviceGuard g(c->device);
     const EvalCfg cands[] = {{32, 4, ADGB_REDUCE_SHFL, 1, 0}, {32, 4, ADGB_REDUCE_MMA_TF32X2, 1, 0},
-                             {32, 4, ADGB_REDUCE_MMA_BF16X3, 1, 0}, {32, 2, ADGB_REDUCE_SHFL, 1, 0},
-                             {64, 2, ADGB_REDUCE_SHFL, 1, 0}, {128, 1, ADGB_REDUCE_SHFL, 1, 0}};
+                             {32, 4, ADGB_REDUCE_MMA_BF16X3, 1, 0}, {32, 4, ADGB_REDUCE_TCGEN05, 1, 0},
+                             {32, 2, ADGB_REDUCE_SHFL, 1, 0}, {64, 2, ADGB_REDUCE_SHFL, 1, 0},
+                             {128, 1, ADGB_REDUCE_SHFL, 1, 0}};
     const size_t gbytes = sizeof(float) * (size_t)b.total * (6 + ADGB_MAX_TORS);
     float *tg = nullptr, *te = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;

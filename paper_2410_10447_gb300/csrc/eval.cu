@@ -183,8 +183,11 @@ __device__ __forceinline__ float pair_term(float4 xi, float4 xj, float2 svi, flo
 
 template <int TPP, int VAR>
 __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage, int group,
-                                           int gt) {
-    warp_sum8<VAR>(v, stage);
+                                           int gt, Tc05Warp &tw) {
+    if constexpr (VAR == ADGB_REDUCE_TCGEN05)
+        warp_sum8_tc05(v, tw);
+    else
+        warp_sum8<VAR>(v, stage);
     if constexpr (TPP > 32) {
         const int w = gt >> 5;
         if ((gt & 31) == 0) {
@@ -208,6 +211,82 @@ __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage,
 #ifndef ADGB_MIN_BLOCKS
 #define ADGB_MIN_BLOCKS 5
 #endif
+
+// ------------------------------------------------- tcgen05 block set-up
+// The tcgen05 reduction's shared-memory region sits at the front of the
+// (1024-byte aligned) dynamic shared memory, before the ligand layout: one
+// 2 KB B operand per warp at [0, 8192), the all-ones A operand at
+// [8192, 10496), one mbarrier per warp at [10496, 10528) and the TMEM base
+// address at [10528, 10532).  A block holds at most 4 warps (128 threads).
+// The A operand (128 x 8 TF32) is read with 128-byte strides both ways, so
+// its core matrices overlap inside 2304 bytes of ones.
+constexpr int TC_B = 0, TC_A = 8192, TC_MBAR = 10496, TC_SLOT = 10528;
+constexpr int TC_REGION = 10560;
+
+template <int VAR>
+__host__ __device__ constexpr int tc_front() { return VAR == ADGB_REDUCE_TCGEN05 ? TC_REGION : 0; }
+
+// The multi-ligand kernel keeps its current work-item index in the 16 bytes
+// before the ligand layout (inside the tcgen05 region's tail for that
+// variant).
+template <int VAR>
+__host__ __device__ constexpr int items_front() {
+    return VAR == ADGB_REDUCE_TCGEN05 ? TC_REGION : 16;
+}
+
+__host__ __device__ constexpr int tc_ncols(int warps) {   // 16 D columns a warp
+    return 16 * warps <= 32 ? 32 : (16 * warps <= 64 ? 64 : 128);
+}
+
+// Allocates the block's TMEM, writes the ones operand and fills `tw` (all
+// threads; contains block barriers).  R is the front of the dynamic shared
+// memory.
+template <int VAR>
+__device__ __forceinline__ void tc_begin(unsigned char *R, Tc05Warp &tw) {
+    if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
+        uint64_t *mb = reinterpret_cast<uint64_t *>(R + TC_MBAR);
+        uint32_t *slot = reinterpret_cast<uint32_t *>(R + TC_SLOT);
+        const int w = threadIdx.x >> 5, W = blockDim.x >> 5;
+        const uint32_t ncols = tc_ncols(W);
+        const uint32_t rs = tc05::smem_u32(R);
+        uint32_t *ones = reinterpret_cast<uint32_t *>(R + TC_A);
+        for (int i = threadIdx.x; i < (TC_MBAR - TC_A) / 4; i += blockDim.x) ones[i] = 0x3F800000u;
+        tc05::fence_proxy_async_smem();
+        if (w == 0) {
+            tc05::alloc(slot, ncols);
+            tc05::relinquish();
+        }
+        if ((int)threadIdx.x < W) tc05::mbar_init(mb + threadIdx.x, 1);
+        tc05::fence_before();
+        __syncthreads();
+        tc05::fence_after();
+        const uint32_t taddr = *slot;
+        tw.a_desc = tc05::desc_plain(rs + TC_A, 128, 128);
+        tw.b_s = rs + TC_B + 2048u * w;
+        tw.b = R + TC_B + 2048 * w;
+        tw.mbar = mb + w;
+        tw.d_col = taddr + 16u * w;
+        tw.d_lane = tc05::lane_addr(taddr, w & 3, 16 * w);
+        tw.taddr = taddr;
+        tw.ncols = ncols;
+        tw.phase = 0;
+        tw.ok = (rs & 1023u) == 0;   // the swizzled B atoms need 1024-byte alignment
+    }
+}
+
+// Releases the block's TMEM once every warp's MMAs have completed (all
+// threads; a warp whose wait gave up first waits, bounded, once more).
+template <int VAR>
+__device__ __forceinline__ void tc_end(Tc05Warp &tw) {
+    if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
+        if (!tw.ok && tw.phase > 0)
+            (void)tc05::mbar_wait(tw.mbar, (tw.phase - 1) & 1, TC05_WAIT_LIMIT);
+        tc05::fence_before();
+        __syncthreads();
+        tc05::fence_after();
+        if ((threadIdx.x >> 5) == 0) tc05::dealloc(tw.taddr, tw.ncols);
+    }
+}
 
 // Per-genotype inputs and outputs of search_pose (pointers at that genotype).
 struct PoseIO {
@@ -277,7 +356,7 @@ template <int TPP, int VAR>
 __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout &L,
                                             const LigDev &lig, const RecDev &rec,
                                             const StagedLig &sl, const int group, const int gt,
-                                            const PoseIO &io) {
+                                            const PoseIO &io, Tc05Warp &tw) {
     const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
     float2 *s_sv = reinterpret_cast<float2 *>(sm + L.sv);
     float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
@@ -536,7 +615,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         }
 
         // 5. one reduce-and-broadcast of the 8-vector
-        group_sum8<TPP, VAR>(v, red, stage, group, gt);
+        group_sum8<TPP, VAR>(v, red, stage, group, gt, tw);
         group_sync<TPP>(group);  // torsion gradients visible
 
         // 6. gene gradient, best tracking, ADADELTA
@@ -611,13 +690,8 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
 }
 
 template <int TPP, int VAR>
-__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const StagedLig sl = stage_ligand(sm, a.L, a.lig);
-    __syncthreads();
-    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
-    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
-    if (pose >= a.n) return;
+__device__ __forceinline__ void eval_one(const EvalArgs &a, const StagedLig &sl, unsigned char *sm,
+                                         int group, int gt, int pose, Tc05Warp &tw) {
     const int G = 6 + a.lig.n_tors;
     PoseIO io;
     io.genes_in = a.genes_in ? a.genes_in + (size_t)pose * G : nullptr;
@@ -630,7 +704,21 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
     io.resume = a.resume;
     io.rho = a.rho;
     io.eps = a.eps;
-    search_pose<TPP, VAR>(sm, a.L, a.lig, a.rec, sl, group, gt, io);
+    search_pose<TPP, VAR>(sm, a.L, a.lig, a.rec, sl, group, gt, io, tw);
+}
+
+template <int TPP, int VAR>
+__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + tc_front<VAR>();
+    const StagedLig sl = stage_ligand(sm, a.L, a.lig);
+    Tc05Warp tw;
+    tc_begin<VAR>(smem_raw, tw);
+    __syncthreads();
+    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
+    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
+    if (pose < a.n) eval_one<TPP, VAR>(a, sl, sm, group, gt, pose, tw);
+    tc_end<VAR>(tw);
 }
 
 // Persistent multi-ligand local search: every block takes work items from a
@@ -647,12 +735,15 @@ struct ItemsArgs {
 
 template <int TPP, int VAR>
 __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const ItemsArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ int s_item;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + items_front<VAR>();
+    int &s_item = *reinterpret_cast<int *>(sm - 16);
     const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
     int cur_lig = -1;
     SmemLayout L;
     StagedLig sl;
+    Tc05Warp tw;
+    tc_begin<VAR>(smem_raw, tw);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(a.counter, 1);
         __syncthreads();
@@ -661,7 +752,8 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
         const WorkItem w = a.items[it];
         if (w.lig != cur_lig) {
             const LigDev &lg = a.ligs[w.lig];
-            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32);
+            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32,
+                                   uses_mma_stage(VAR));
             sl = stage_ligand(sm, L, lg);
             cur_lig = w.lig;
             __syncthreads();
@@ -678,10 +770,11 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
             io.resume = 0;
             io.rho = w.rho;
             io.eps = w.eps;
-            search_pose<TPP, VAR>(sm, L, a.ligs[w.lig], a.recs[w.rec], sl, group, gt, io);
+            search_pose<TPP, VAR>(sm, L, a.ligs[w.lig], a.recs[w.rec], sl, group, gt, io, tw);
         }
         __syncthreads();  // the item is done before smem or s_item change
     }
+    tc_end<VAR>(tw);
     // the last block out re-arms the counter so that the launch can be replayed
     if (threadIdx.x == 0) {
         __threadfence();
@@ -694,21 +787,44 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
     }
 }
 
+// Dynamic shared memory of an eval launch whose layout needs `layout_bytes`:
+// the tcgen05 variant puts its region in front and pads the total so that
+// no more blocks are resident on an SM than its 512 TMEM columns serve at
+// once (tcgen05.alloc would otherwise wait for a resident block to finish).
+int eval_smem_bytes(int layout_bytes, const EvalCfg &cfg, int device, bool items) {
+    if (cfg.variant != ADGB_REDUCE_TCGEN05) return layout_bytes + (items ? 16 : 0);
+    int total = TC_REGION + layout_bytes;
+    int sm_smem = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) !=
+            cudaSuccess)
+        return -1;
+    const int fit = 512 / tc_ncols(cfg.tpp * cfg.ppb / 32);
+    const int floor_bytes = sm_smem / (fit + 1) - reserved + 16;
+    return total < floor_bytes ? floor_bytes : total;
+}
+
 template <int TPP, int VAR>
-static cudaError_t launch_items_t(const ItemsArgs &a, int grid, cudaStream_t s) {
+static cudaError_t launch_items_t(const ItemsArgs &a, int smem, int grid, cudaStream_t s) {
     auto k = eval_items_kernel<TPP, VAR>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.budget);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, TPP * a.ppb, a.budget, s>>>(a);
+    k<<<grid, TPP * a.ppb, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TPP>
-static cudaError_t launch_items_v(const ItemsArgs &a, int variant, int grid, cudaStream_t s) {
+static cudaError_t launch_items_v(const ItemsArgs &a, int variant, int smem, int grid,
+                                  cudaStream_t s) {
     switch (variant) {
-        case ADGB_REDUCE_SHFL: return launch_items_t<TPP, ADGB_REDUCE_SHFL>(a, grid, s);
-        case ADGB_REDUCE_MMA_TF32X2: return launch_items_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, grid, s);
-        case ADGB_REDUCE_MMA_BF16X3: return launch_items_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, grid, s);
+        case ADGB_REDUCE_SHFL: return launch_items_t<TPP, ADGB_REDUCE_SHFL>(a, smem, grid, s);
+        case ADGB_REDUCE_MMA_TF32X2:
+            return launch_items_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, smem, grid, s);
+        case ADGB_REDUCE_MMA_BF16X3:
+            return launch_items_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, smem, grid, s);
+        case ADGB_REDUCE_TCGEN05:
+            return launch_items_t<TPP, ADGB_REDUCE_TCGEN05>(a, smem, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -724,10 +840,15 @@ cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *
     a.n_items = n_items;
     a.ppb = cfg.ppb;
     a.budget = budget;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int smem = eval_smem_bytes(budget, cfg, dev, true);
+    if (smem < 0) return cudaErrorInvalidValue;
     switch (cfg.tpp) {
-        case 32: return launch_items_v<32>(a, cfg.variant, grid, s);
-        case 64: return launch_items_v<64>(a, cfg.variant, grid, s);
-        case 128: return launch_items_v<128>(a, cfg.variant, grid, s);
+        case 32: return launch_items_v<32>(a, cfg.variant, smem, grid, s);
+        case 64: return launch_items_v<64>(a, cfg.variant, smem, grid, s);
+        case 128: return launch_items_v<128>(a, cfg.variant, smem, grid, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -737,39 +858,43 @@ int items_grid(const EvalCfg &cfg, int budget, int device) {
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
     int per_sm = 0;
+    const int smem = eval_smem_bytes(budget, cfg, device, true);
+    if (smem < 0) return 0;
     cudaError_t e = cudaErrorInvalidValue;
 #define ADGB_OCC(TPP, VAR)                                                                   \
     if (cfg.tpp == TPP && cfg.variant == VAR) {                                              \
         cudaFuncSetAttribute(eval_items_kernel<TPP, VAR>,                                    \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, budget);           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);             \
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_items_kernel<TPP, VAR>, \
-                                                          TPP * cfg.ppb, budget);           \
+                                                          TPP * cfg.ppb, smem);             \
     }
-    ADGB_OCC(32, 0) ADGB_OCC(32, 1) ADGB_OCC(32, 2)
-    ADGB_OCC(64, 0) ADGB_OCC(64, 1) ADGB_OCC(64, 2)
-    ADGB_OCC(128, 0) ADGB_OCC(128, 1) ADGB_OCC(128, 2)
+    ADGB_OCC(32, 0) ADGB_OCC(32, 1) ADGB_OCC(32, 2) ADGB_OCC(32, 3)
+    ADGB_OCC(64, 0) ADGB_OCC(64, 1) ADGB_OCC(64, 2) ADGB_OCC(64, 3)
+    ADGB_OCC(128, 0) ADGB_OCC(128, 1) ADGB_OCC(128, 2) ADGB_OCC(128, 3)
 #undef ADGB_OCC
     if (e != cudaSuccess || per_sm < 1) return 0;
     return per_sm * prop.multiProcessorCount;
 }
 
 template <int TPP, int VAR>
-static cudaError_t launch_t(const EvalArgs &a, int ppb, cudaStream_t s) {
+static cudaError_t launch_t(const EvalArgs &a, int ppb, int smem, cudaStream_t s) {
     auto k = eval_kernel<TPP, VAR>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         a.L.total);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int blocks = (a.n + ppb - 1) / ppb;
-    k<<<blocks, TPP * ppb, a.L.total, s>>>(a);
+    k<<<blocks, TPP * ppb, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TPP>
-static cudaError_t launch_v(const EvalArgs &a, int ppb, int variant, cudaStream_t s) {
+static cudaError_t launch_v(const EvalArgs &a, int ppb, int variant, int smem, cudaStream_t s) {
     switch (variant) {
-        case ADGB_REDUCE_SHFL: return launch_t<TPP, ADGB_REDUCE_SHFL>(a, ppb, s);
-        case ADGB_REDUCE_MMA_TF32X2: return launch_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, ppb, s);
-        case ADGB_REDUCE_MMA_BF16X3: return launch_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, ppb, s);
+        case ADGB_REDUCE_SHFL: return launch_t<TPP, ADGB_REDUCE_SHFL>(a, ppb, smem, s);
+        case ADGB_REDUCE_MMA_TF32X2:
+            return launch_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, ppb, smem, s);
+        case ADGB_REDUCE_MMA_BF16X3:
+            return launch_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, ppb, smem, s);
+        case ADGB_REDUCE_TCGEN05: return launch_t<TPP, ADGB_REDUCE_TCGEN05>(a, ppb, smem, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -784,7 +909,7 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     a.rec = rec;
     a.lig = lig;
     a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk, lig.n_pairs,
-             cfg.stage_pairs != 0);
+             cfg.stage_pairs != 0, uses_mma_stage(cfg.variant));
     a.genes_in = genes_in;
     a.genes_out = genes_out;
     a.energy = energy;
@@ -796,10 +921,15 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     a.mode = mode;
     a.rho = rho;
     a.eps = eps;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int smem = eval_smem_bytes(a.L.total, cfg, dev, false);
+    if (smem < 0) return cudaErrorInvalidValue;
     switch (cfg.tpp) {
-        case 32: return launch_v<32>(a, cfg.ppb, cfg.variant, s);
-        case 64: return launch_v<64>(a, cfg.ppb, cfg.variant, s);
-        case 128: return launch_v<128>(a, cfg.ppb, cfg.variant, s);
+        case 32: return launch_v<32>(a, cfg.ppb, cfg.variant, smem, s);
+        case 64: return launch_v<64>(a, cfg.ppb, cfg.variant, smem, s);
+        case 128: return launch_v<128>(a, cfg.ppb, cfg.variant, smem, s);
     }
     return cudaErrorInvalidValue;
 }

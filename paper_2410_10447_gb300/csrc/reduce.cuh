@@ -14,6 +14,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "adgb.h"
+#include "tcgen05.cuh"
+
 namespace adgb {
 
 __device__ __forceinline__ float shfl_xor(float v, int m) {
@@ -173,6 +176,8 @@ __device__ __forceinline__ void warp_sum8_mma_bf16x3(float v[8], float *stage) {
 
 template <int VAR>
 __device__ __forceinline__ void warp_sum8(float v[8], float *stage) {
+    static_assert(VAR == ADGB_REDUCE_SHFL || VAR == ADGB_REDUCE_MMA_TF32X2 ||
+                  VAR == ADGB_REDUCE_MMA_BF16X3, "warp_sum8: register / mma.sync variants only");
     if constexpr (VAR == ADGB_REDUCE_SHFL) {
         warp_sum8_shfl(v);
     } else if constexpr (VAR == ADGB_REDUCE_MMA_TF32X2) {
@@ -180,6 +185,71 @@ __device__ __forceinline__ void warp_sum8(float v[8], float *stage) {
     } else {
         warp_sum8_mma_bf16x3(v, stage);
     }
+}
+
+// ------------------------------------------------------- tcgen05 warp form
+// Per-warp state of the fifth-generation tensor-core reduction.  Each warp
+// owns a 2 KB shared-memory B operand (two 128-byte-swizzled 8-row atoms:
+// rows 0-7 the TF32 hi terms of the 8 values, rows 8-15 the lo terms; K =
+// the 32 lanes), an mbarrier, and 16 TMEM columns for its D = ones . B^T
+// (M = 128, N = 16); the all-ones A operand (128 x 8 TF32, 4 KB of shared
+// memory) is shared by the block's warps.  Every row of D holds the column
+// sums, and each warp reads them from its own lane quadrant.
+struct Tc05Warp {
+    unsigned char *b;     // generic address of this warp's B operand
+    uint64_t *mbar;       // completion barrier of this warp's MMAs
+    uint32_t b_s;         // shared-window address of the B operand
+    uint32_t d_col;       // TMEM address of D (lane 0, first column)
+    uint32_t d_lane;      // TMEM address of D in this warp's lane quadrant
+    uint64_t a_desc;      // descriptor of the shared all-ones A operand
+    uint32_t taddr, ncols;
+    uint32_t phase;       // completed reductions (mbarrier phase)
+    int ok;               // 0 once a completion wait gave up (results NaN)
+};
+
+constexpr int TC05_WAIT_LIMIT = 1 << 16;   // mbarrier probes, each suspending up to a time limit
+
+__device__ __forceinline__ void warp_sum8_tc05(float v[8], Tc05Warp &t) {
+    const int lane = threadIdx.x & 31, cq = lane >> 2;
+    if (!t.ok) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) v[c] = __int_as_float(0x7fc00000);
+        return;
+    }
+    unsigned char *mine = t.b + (lane & 3) * 4;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const uint32_t hi = to_tf32(v[c]);
+        const uint32_t lo = to_tf32(v[c] - __uint_as_float(hi));
+        *reinterpret_cast<uint32_t *>(mine + c * 128 + ((cq ^ c) << 4)) = hi;
+        *reinterpret_cast<uint32_t *>(mine + 1024 + c * 128 + ((cq ^ c) << 4)) = lo;
+    }
+    tc05::fence_proxy_async_smem();
+    tc05::fence_before();
+    __syncwarp();
+    if (lane == 0) {
+        tc05::fence_after();
+        constexpr uint32_t idesc = tc05::idesc_tf32(128, 16);
+#pragma unroll
+        for (int s = 0; s < 4; s++)   // K = 32 lanes in four K = 8 slices
+            tc05::mma_tf32_ss(t.d_col, t.a_desc, tc05::desc_sw128(t.b_s + 32u * s, 1024), idesc,
+                              s > 0);
+        tc05::commit(t.mbar);
+    }
+    const bool done = __all_sync(0xffffffffu, tc05::mbar_wait(t.mbar, t.phase & 1, TC05_WAIT_LIMIT));
+    t.phase++;
+    if (!done) {
+        t.ok = 0;
+#pragma unroll
+        for (int c = 0; c < 8; c++) v[c] = __int_as_float(0x7fc00000);
+        return;
+    }
+    tc05::fence_after();
+    float d[16];
+    tc05::ld16_wait(t.d_lane, d);
+#pragma unroll
+    for (int c = 0; c < 8; c++) v[c] = d[c] + d[8 + c];
+    tc05::fence_before();   // these TMEM reads precede the warp's next MMA
 }
 
 }  // namespace adgb

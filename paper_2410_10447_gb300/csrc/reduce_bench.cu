@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(1024) reduce4_half_kernel(const float4 *in, fl
 // A completion wait that gives up (it never should) turns the outputs into
 // NaN; the TMEM is still released.
 // ---------------------------------------------------------------------------
-constexpr int TC_WAIT_LIMIT = 1 << 20;
+constexpr int TC_WAIT_LIMIT = 1 << 16;   // probes, each suspending up to a time limit
 
 template <int NG>
 struct TcShape {

@@ -217,7 +217,8 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
             Job *j = act[u];
             const int src = j->gen < 0 ? 0 : (j->cur ^ 1);   // population the LS works on
             budget[c] = std::max(budget[c], SmemLayout::choose(j->lig.n_atoms, j->lig.n_tors,
-                                                               j->lig.n_pairs, cf.ppb, cf.tpp / 32).total);
+                                                               j->lig.n_pairs, cf.ppb, cf.tpp / 32,
+                                                               uses_mma_stage(cf.variant)).total);
             const int n = j->d.n_runs * j->d.pop;
             const int cost = j->lig.n_pairs + 8 * j->lig.n_atoms + 64;
             for (int p = 0; p < n; p += cf.ppb) {

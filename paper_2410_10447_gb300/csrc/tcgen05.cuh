@@ -96,6 +96,16 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t sbo) {
          | ((uint64_t)2 << 61);
 }
 
+// K-major operand without swizzling: 8-row x 16-byte core matrices of 128
+// contiguous bytes, `lbo` bytes apart along K and `sbo` bytes apart along
+// M/N.
+__device__ __forceinline__ uint64_t desc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4)
+         | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16)
+         | ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32)
+         | ((uint64_t)1 << 46);
+}
+
 // kind::tf32, D in FP32, A and B K-major, dense, no negation.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17)
@@ -112,6 +122,16 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
+// D[tmem] (+)= A[smem] . B[smem]^T, issued by one thread for the CTA.
+__device__ __forceinline__ void mma_tf32_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                            uint32_t idesc, int accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on the mbarrier when every MMA this thread issued so far has
 // completed (its operand reads included).
 __device__ __forceinline__ void commit(uint64_t *mbar) {
@@ -125,10 +145,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *mbar, uint32_t count) {
                  : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-__device__ __forceinline__ bool mbar_test(uint64_t *mbar, uint32_t parity) {
+// One potentially blocking probe: the hardware suspends the thread until the
+// phase with the given parity completes or a system-dependent time limit
+// passes.
+__device__ __forceinline__ bool mbar_try(uint64_t *mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
         "selp.b32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(smem_u32(mbar)), "r"(parity)
@@ -136,12 +159,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *mbar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait for the phase with the given parity to complete; false after
-// `limit` polls.
+// `limit` probes.
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int limit) {
-    for (int i = 0; i < limit; i++) {
-        if (mbar_test(mbar, parity)) return true;
-        if (i > 64) __nanosleep(32);
-    }
+    for (int i = 0; i < limit; i++)
+        if (mbar_try(mbar, parity)) return true;
     return false;
 }
 

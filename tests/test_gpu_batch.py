@@ -65,8 +65,8 @@ def test_batch_scores_match_single_ligand_calls(pkg, torch, setup):
     ctx.close()
 
 
-@pytest.mark.parametrize("autotune", [False, True])
-def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune):
+@pytest.mark.parametrize("autotune, variant", [(False, -1), (True, -1), (False, 3)])
+def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune, variant):
     rec, ligs, n_poses, genes = setup
     ctx = pkg.Context(0)
     rid = ctx.upload_receptor_grids(rec)
@@ -79,12 +79,12 @@ def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune):
         assert np.array_equal(g0.cpu().numpy(), pack(genes))      # autotune leaves genes alone
     g = g0.clone()
     e = torch.empty(g.shape[0], device="cuda")
-    ctx.batch_local_search_dev(bid, g, e, 40)        # captured
+    ctx.batch_local_search_dev(bid, g, e, 40, variant=variant)        # captured
     g2 = g0.clone()
     e2 = torch.empty_like(e)
-    ctx.batch_local_search_dev(bid, g2, e2, 40)      # other buffers: captured again
+    ctx.batch_local_search_dev(bid, g2, e2, 40, variant=variant)      # other buffers: captured again
     g2.copy_(g0)
-    ctx.batch_local_search_dev(bid, g2, e2, 40)      # same buffers: graph replayed
+    ctx.batch_local_search_dev(bid, g2, e2, 40, variant=variant)      # same buffers: graph replayed
     assert np.array_equal(e.cpu().numpy(), e2.cpu().numpy())
     assert np.array_equal(g.cpu().numpy(), g2.cpu().numpy())
     be = e.cpu().numpy()

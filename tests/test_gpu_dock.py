@@ -119,12 +119,14 @@ def test_fp64_rescoring_matches_oracle(pkg, torch):
         ctx.close()
 
 
-def test_dock_results_and_accounting(pkg, torch, w):
+@pytest.mark.parametrize("variant", [-1, 3])
+def test_dock_results_and_accounting(pkg, torch, w, variant):
     ctx = pkg.Context(0)
     rid = ctx.upload_receptor_grids(w["receptor"])
     lid = ctx.upload_ligand_torsion_tree(w["ligand"])
     runs, pop, gens, it = 3, 24, 4, 30
-    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, max_gens=gens, ls_iters=it, ls_rate=1.0, seed=5)
+    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, max_gens=gens, ls_iters=it, ls_rate=1.0, seed=5,
+                              reduce_variant=variant)
     bg, be, ev = ctx.dock(rid, lid, gp)
     assert np.all(ev == pop + gens * pop * it)
     R, L = oracle.Receptor(w["receptor"]), oracle.Ligand(w["ligand"])

@@ -18,7 +18,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 E_REL, E_ABS, G_REL, G_REL_MMA, X_ABS = 1e-4, 1e-3, 1e-3, 2e-3, 1e-5
-VARIANT_TOL = {0: G_REL, 1: G_REL_MMA, 2: G_REL_MMA}
+VARIANT_TOL = {0: G_REL, 1: G_REL_MMA, 2: G_REL_MMA, 3: G_REL_MMA}
 
 
 @pytest.fixture(scope="module")
@@ -119,7 +119,7 @@ def test_zero_pose_is_exact_on_gpu(pkg, torch, cfg1):
 
 
 # ----------------------------------------------------------------- scoring
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("tpp", [32, 64, 128])
 def test_score_parity_cfg0(pkg, torch, cfg0, variant, tpp):
     ctx = make_ctx(pkg, threads_per_pose=tpp)
@@ -134,7 +134,7 @@ def test_score_parity_cfg0(pkg, torch, cfg0, variant, tpp):
     ctx.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_score_parity_cfg1(pkg, torch, cfg1, variant):
     ctx = make_ctx(pkg)
     rid = ctx.upload_receptor_grids(cfg1["receptor"])
@@ -211,7 +211,7 @@ def test_host_and_device_calls_agree(pkg, torch, cfg1):
 
 
 # ------------------------------------------------------------ local search
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_local_search_teacher_forced_step(pkg, torch, cfg1, variant):
     """One ADADELTA step from the GPU's own state at step t equals the
     oracle's step from that same state (the trajectory itself is chaotic).
