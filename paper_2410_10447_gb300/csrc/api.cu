@@ -327,8 +327,52 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         std::sort(keyed.begin(), keyed.end());
         for (int p = 0; p < NP; p++) h.pairs[p] = keyed[p].second;
     }
+    // Within every chunk the pairs are re-ordered for the shared-memory
+    // banks: the pair loop gives consecutive pairs to consecutive lanes, and a
+    // quarter-warp's 16-byte coordinate loads (or a half-warp's 8-byte
+    // parameter loads) conflict when two lanes read different atoms (type
+    // pairs) in the same bank group.  A greedy pass appends, from the next 64
+    // pairs in line, the one that adds the fewest such collisions.
+    for (int p0 = 0; p0 < NP; p0 += PAIR_CHUNK) {
+        const int p1 = std::min(NP, p0 + PAIR_CHUNK);
+        std::vector<uint32_t> rem(h.pairs.begin() + p0, h.pairs.begin() + p1), out;
+        out.reserve(rem.size());
+        constexpr int WIN = 64;
+        while (!rem.empty()) {
+            const int pos = (int)out.size();
+            const int q0 = pos - pos % 8, hw0 = pos - pos % 16;
+            int best = 0, best_c = INT32_MAX;
+            const int lim = std::min<int>(WIN, (int)rem.size());
+            for (int t = 0; t < lim && best_c > 0; t++) {
+                const uint32_t c = rem[t];
+                const int i = c & 255, j = (c >> 8) & 255, tp = (c >> 16) & 255;
+                int cost = 0;
+                for (int r = hw0; r < pos; r++) {
+                    const uint32_t o = out[r];
+                    const int oi = o & 255, oj = (o >> 8) & 255, otp = (o >> 16) & 255;
+                    if (r >= q0) {   // same quarter-warp: 16-byte atom coordinates
+                        cost += 2 * (oi != i && (oi & 7) == (i & 7));
+                        cost += 2 * (oj != j && (oj & 7) == (j & 7));
+                    }
+                    cost += (oi != i && (oi & 15) == (i & 15));    // 8-byte atom parameters
+                    cost += (oj != j && (oj & 15) == (j & 15));
+                    cost += (otp != tp && (otp & 15) == (tp & 15));  // 8-byte type-pair terms
+                }
+                if (cost < best_c) {
+                    best_c = cost;
+                    best = t;
+                }
+            }
+            out.push_back(rem[best]);
+            rem.erase(rem.begin() + best);
+        }
+        std::copy(out.begin(), out.end(), h.pairs.begin() + p0);
+    }
     // incidence lists per chunk of PAIR_CHUNK pairs: for every chunk and atom
-    // the chunk's pairs it belongs to, ascending (chunk-local index, side)
+    // the chunk's pairs it belongs to as (chunk-local index, side).  Owners of
+    // atoms i read their k-th entries together, lane i % 32; each list is
+    // ordered so that the 8 lanes of a quarter-warp read force slots in
+    // different 16-byte bank groups at every k where they can (greedy).
     {
         const int nch = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
         h.inc_off.assign((size_t)nch * (N + 1), 0);
@@ -336,22 +380,44 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         int pos = 0;
         for (int q = 0; q < nch; q++) {
             const int p0 = q * PAIR_CHUNK, p1 = std::min(NP, p0 + PAIR_CHUNK);
-            std::vector<int> cnt(N, 0);
+            std::vector<std::vector<uint16_t>> lists(N);
             for (int p = p0; p < p1; p++) {
-                cnt[h.pairs[p] & 255]++;
-                cnt[(h.pairs[p] >> 8) & 255]++;
+                lists[h.pairs[p] & 255].push_back((uint16_t)((p - p0) << 1));
+                lists[(h.pairs[p] >> 8) & 255].push_back((uint16_t)(((p - p0) << 1) | 1));
             }
-            std::vector<int> fill(N);
+            std::vector<std::vector<uint16_t>> ordered(N);
+            for (int a0 = 0; a0 < N; a0 += 8) {
+                const int a1 = std::min(N, a0 + 8);
+                for (;;) {
+                    int order[8], n_left = 0;
+                    for (int a = a0; a < a1; a++)
+                        if (!lists[a].empty()) order[n_left++] = a;
+                    if (!n_left) break;
+                    std::sort(order, order + n_left, [&](int x, int y) {
+                        return lists[x].size() != lists[y].size() ? lists[x].size() > lists[y].size() : x < y;
+                    });
+                    int used[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                    for (int u = 0; u < n_left; u++) {
+                        std::vector<uint16_t> &L = lists[order[u]];
+                        int pick = 0, pick_c = INT32_MAX;
+                        for (int t = 0; t < (int)L.size() && pick_c > 0; t++) {
+                            const int c = used[(L[t] >> 1) & 7];
+                            if (c < pick_c) {
+                                pick_c = c;
+                                pick = t;
+                            }
+                        }
+                        used[(L[pick] >> 1) & 7]++;
+                        ordered[order[u]].push_back(L[pick]);
+                        L.erase(L.begin() + pick);
+                    }
+                }
+            }
             for (int a = 0; a < N; a++) {
                 h.inc_off[(size_t)q * (N + 1) + a] = pos;
-                fill[a] = pos;
-                pos += cnt[a];
+                for (uint16_t e : ordered[a]) h.inc[pos++] = e;
             }
             h.inc_off[(size_t)q * (N + 1) + N] = pos;
-            for (int p = p0; p < p1; p++) {
-                h.inc[fill[h.pairs[p] & 255]++] = (uint16_t)((p - p0) << 1);
-                h.inc[fill[(h.pairs[p] >> 8) & 255]++] = (uint16_t)(((p - p0) << 1) | 1);
-            }
         }
     }
     h.tR.assign(d->R, d->R + NT);
