@@ -45,12 +45,15 @@ struct LigDev {
     const float4 *tbref;      // [T] reference position of b
     const uint32_t *pairs;    // [Np] i | j << 8 | (ti*16+tj) << 16 | hb << 24
     const float2 *tptab;      // [256] (A, B): E = A r^-12 - B r^-m, m = 10 if hb else 6
+    const float4 *pconst;     // [Np] per pair, in pair order: (A, B, w_el 332.06 q_i q_j,
+                              // w_ds (S_i V_j + S_j V_i))
     const int *perm;          // [N] internal index -> caller's index
     int n_chunks;             // ceil(Np / PAIR_CHUNK)
     const int *inc_off;       // [n_chunks][N+1]: atom i's pairs in chunk q are
                               // inc[inc_off[q*(N+1)+i] .. inc_off[q*(N+1)+i+1])
     const uint16_t *inc;      // [2 Np] (pair index - q*PAIR_CHUNK) << 1 | (atom is the pair's
-                              // second atom), ordered by chunk, atom, pair
+                              // second atom), ordered by chunk and atom (within an atom's
+                              // list, in the order that spreads reads over the banks)
     // the caller's per-type parameters, kept for the FP64 rescoring
     const float *t_R, *t_eps, *t_vol, *t_sol;
     const int *t_hb;
@@ -79,7 +82,7 @@ struct DockScratch {
 // per-ligand constants once, then per-pose working arrays.  All offsets in
 // bytes, 16-byte aligned.
 struct SmemLayout {
-    int ref, sv, type, frag, tparent, tatoms, taxis, tbref, tptab, incoff;
+    int ref, type, frag, tparent, tatoms, taxis, tbref, incoff;
     int spairs, sinc, pairs_in_smem;   // optional copies of the pair list and incidence lists
     int pose0, pose_stride;          // first pose block, bytes per pose
     // offsets inside one pose block
@@ -96,14 +99,12 @@ struct SmemLayout {
         const int nch = (np + PAIR_CHUNK - 1) / PAIR_CHUNK;
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
-        sv = o;      o = al16(o + 8 * N);
         type = o;    o = al16(o + 4 * N);
         frag = o;    o = al16(o + 4 * N);
         tparent = o; o = al16(o + 4 * (T > 0 ? T : 1));
         tatoms = o;  o = al16(o + 16 * (T > 0 ? T : 1));
         taxis = o;   o = al16(o + 16 * (T > 0 ? T : 1));
         tbref = o;   o = al16(o + 16 * (T > 0 ? T : 1));
-        tptab = o;   o = al16(o + 8 * TYPE_TAB);
         incoff = o;  if (stage_pairs) o = al16(o + 4 * nch * (N + 1));
         pairs_in_smem = stage_pairs ? 1 : 0;
         spairs = o;  if (stage_pairs) o = al16(o + 4 * np);

@@ -156,6 +156,7 @@ struct HostLigand {
     std::vector<float4> taxis, tbref;
     std::vector<uint32_t> pairs;
     std::vector<float2> tptab;
+    std::vector<float4> pconst;
     std::vector<int> inc_off;
     std::vector<uint16_t> inc;
     std::vector<float> tR, teps, tvol, tsol;
@@ -443,6 +444,17 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
             }
             h.tptab[ti * ADGB_MAX_TYPES + tj] = make_float2((float)A, (float)B);
         }
+    // per-pair constants in pair order: what the pair term needs besides the
+    // two positions, so that the pair loop reads one contiguous record
+    h.pconst.resize(NP);
+    for (int p = 0; p < NP; p++) {
+        const uint32_t c = h.pairs[p];
+        const int i = c & 255, j = (c >> 8) & 255;
+        const float2 ab = h.tptab[(c >> 16) & 255];
+        const double qq = (double)ADGB_W_EL * (double)ADGB_ELEC_KCAL * (double)h.ref[i].w * (double)h.ref[j].w;
+        const double ds = (double)h.sv[i].x * h.sv[j].y + (double)h.sv[j].x * h.sv[i].y;
+        h.pconst[p] = make_float4(ab.x, ab.y, (float)qq, (float)ds);
+    }
     return ADGB_OK;
 }
 
@@ -504,6 +516,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     const size_t o_ref = take(16 * N), o_sv = take(8 * N), o_type = take(4 * N), o_frag = take(4 * N);
     const size_t o_tpar = take(4 * Tz), o_tat = take(16 * Tz), o_tax = take(16 * Tz), o_tb = take(16 * Tz);
     const size_t o_pairs = take(4 * NPz), o_tab = take(8 * TYPE_TAB), o_perm = take(4 * N);
+    const size_t o_pconst = take(16 * NPz);
     const int NCH = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
     const size_t o_incoff = take(4 * (size_t)(NCH > 0 ? NCH : 1) * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
     const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
@@ -521,6 +534,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
         memcpy(&buf[o_tb], h.tbref.data(), 16 * T);
     }
     if (NP) memcpy(&buf[o_pairs], h.pairs.data(), 4 * NP);
+    if (NP) memcpy(&buf[o_pconst], h.pconst.data(), 16 * (size_t)NP);
     memcpy(&buf[o_tab], h.tptab.data(), 8 * TYPE_TAB);
     memcpy(&buf[o_perm], h.perm.data(), 4 * N);
     if (NCH) memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (size_t)NCH * (N + 1));
@@ -548,6 +562,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     v.tbref = reinterpret_cast<const float4 *>(at(o_tb));
     v.pairs = reinterpret_cast<const uint32_t *>(at(o_pairs));
     v.tptab = reinterpret_cast<const float2 *>(at(o_tab));
+    v.pconst = reinterpret_cast<const float4 *>(at(o_pconst));
     v.perm = reinterpret_cast<const int *>(at(o_perm));
     v.inc_off = reinterpret_cast<const int *>(at(o_incoff));
     v.inc = reinterpret_cast<const uint16_t *>(at(o_inc));
@@ -575,6 +590,7 @@ LigDev bind_ligand(const LigandBlob &b, const unsigned char *mem) {
     v.tbref = mv(v.tbref);
     v.pairs = mv(v.pairs);
     v.tptab = mv(v.tptab);
+    v.pconst = mv(v.pconst);
     v.perm = mv(v.perm);
     v.inc_off = mv(v.inc_off);
     v.inc = mv(v.inc);

@@ -40,7 +40,6 @@ struct EvalArgs {
     float rho, eps;
 };
 
-constexpr float KQQ = ADGB_W_EL * ADGB_ELEC_KCAL;
 constexpr float INV_SIG2 = 1.0f / (ADGB_DS_SIGMA * ADGB_DS_SIGMA);
 constexpr float HALF_INV_SIG2 = 0.5f / (ADGB_DS_SIGMA * ADGB_DS_SIGMA);
 constexpr float RMIN2 = ADGB_R_MIN * ADGB_R_MIN;
@@ -148,9 +147,9 @@ __device__ __forceinline__ float inter_atom(const RecDev &R, int t, float q, flo
 
 // One intramolecular pair: 12-6 (12-10 for donor-acceptor pairs) with
 // A r^-12 - B r^-m, Coulomb with the Mehler-Solmajer dielectric, and
-// desolvation.  Returns the energy; f = dE/dx_i (atom j gets -f).
-__device__ __forceinline__ float pair_term(float4 xi, float4 xj, float2 svi, float2 svj,
-                                           float2 ab, bool hb, float3 &f) {
+// desolvation.  pc = (A, B, w_el 332.06 q_i q_j, w_ds (S_i V_j + S_j V_i)).
+// Returns the energy; f = dE/dx_i (atom j gets -f).
+__device__ __forceinline__ float pair_term(float4 xi, float4 xj, float4 pc, bool hb, float3 &f) {
     const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     const bool live = r2 >= RMIN2;
@@ -162,19 +161,19 @@ __device__ __forceinline__ float pair_term(float4 xi, float4 xj, float2 svi, flo
     const float r12i = r6i * r6i;
     const float rmi = hb ? r6i * r2i * r2i : r6i;
     const float m = hb ? 10.f : 6.f;
-    const float evdw = ab.x * r12i - ab.y * rmi;
-    const float dvdw = (-12.f * ab.x * r12i + m * ab.y * rmi) * rinv;
+    const float evdw = pc.x * r12i - pc.y * rmi;
+    const float dvdw = (-12.f * pc.x * r12i + m * pc.y * rmi) * rinv;
     // eps(r) = num / den with den = 1 + k e^{-lambda B r}, num = A den + B;
     // 1/eps = den^2 r and eps'/eps = B k lambda B e^{..} r with r = 1/(den num):
     // one reciprocal for the whole dielectric.
-    const float C = KQQ * xi.w * xj.w;
+    const float C = pc.z;
     const float ex = __expf(-MS_LAMBDA * MS_B * rc);
     const float den = 1.f + MS_K * ex;
     const float num = MS_A * den + MS_B;
     const float rr = __fdividef(1.f, den * num);
     const float eel = C * rinv * (den * den * rr);
     const float del = -eel * (rinv + (MS_B * MS_K * MS_LAMBDA * MS_B) * ex * rr);
-    const float eds = (svi.x * svj.y + svj.x * svi.y) * __expf(-r2 * HALF_INV_SIG2);
+    const float eds = pc.w * __expf(-r2 * HALF_INV_SIG2);
     const float fr = live ? (dvdw + del) * rinv : 0.f;
     const float fd = -eds * INV_SIG2;
     f = make_float3((fr + fd) * dx, (fr + fd) * dy, (fr + fd) * dz);
@@ -312,14 +311,12 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
                                                   const LigDev &lig) {
     const int N = lig.n_atoms, T = lig.n_tors, NP = lig.n_pairs;
     float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
-    float2 *s_sv = reinterpret_cast<float2 *>(sm + L.sv);
     int *s_type = reinterpret_cast<int *>(sm + L.type);
     int *s_frag = reinterpret_cast<int *>(sm + L.frag);
     int *s_tpar = reinterpret_cast<int *>(sm + L.tparent);
     int4 *s_tat = reinterpret_cast<int4 *>(sm + L.tatoms);
     float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
     float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
-    float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
     // pair records, incidence lists and their offsets: shared memory when they fit
     const uint32_t *prs = lig.pairs;
     const uint16_t *incl = lig.inc;
@@ -337,7 +334,6 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
     }
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         s_ref[i] = lig.ref[i];
-        s_sv[i] = lig.sv[i];
         s_type[i] = lig.type[i];
         s_frag[i] = lig.frag[i];
     }
@@ -347,7 +343,6 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
         s_tax[k] = lig.taxis[k];
         s_tb[k] = lig.tbref[k];
     }
-    for (int k = threadIdx.x; k < TYPE_TAB; k += blockDim.x) s_tab[k] = lig.tptab[k];
     return {prs, incl, incoff};
 }
 
@@ -358,7 +353,6 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                                             const StagedLig &sl, const int group, const int gt,
                                             const PoseIO &io, Tc05Warp &tw) {
     const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
-    float2 *s_sv = reinterpret_cast<float2 *>(sm + L.sv);
     float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
     int *s_type = reinterpret_cast<int *>(sm + L.type);
     int *s_frag = reinterpret_cast<int *>(sm + L.frag);
@@ -366,7 +360,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
     int4 *s_tat = reinterpret_cast<int4 *>(sm + L.tatoms);
     float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
     float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
-    float2 *s_tab = reinterpret_cast<float2 *>(sm + L.tptab);
+    const float4 *pconst = lig.pconst;
     const uint32_t *prs = sl.prs;
     const uint16_t *incl = sl.incl;
     unsigned char *P = sm + L.pose0 + group * L.pose_stride;
@@ -463,8 +457,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                 const uint32_t pr = prs[p];
                 const int i = pr & 255, j = (pr >> 8) & 255;
                 float3 f;
-                e_part += pair_term(xyz[i], xyz[j], s_sv[i], s_sv[j], s_tab[(pr >> 16) & 255],
-                                    (pr >> 24) & 1, f);
+                e_part += pair_term(xyz[i], xyz[j], __ldg(pconst + p), (pr >> 24) & 1, f);
                 fbuf[p - c0] = make_float4(f.x, f.y, f.z, 0.f);
             }
             group_sync<TPP>(group);
