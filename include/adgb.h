@@ -228,6 +228,16 @@ typedef struct {
     float mut_angle;         /* angle mutation amplitude (rad) */
     unsigned long long seed;
     int reduce_variant;      /* ADGB_REDUCE_* or -1 for the context default */
+    /* Early stopping (convergence detection; Sec. 5.3 discusses runs that do
+     * or do not converge, the paper does not define the test).  The library's
+     * test: after every conv_every-th generation a run stops once the
+     * population standard deviation of its conv_top lowest energies (the
+     * energies of that generation's evaluations) is below conv_tol kcal/mol,
+     * computed in double precision from the float energies.  conv_every = 0
+     * switches it off; otherwise 2 <= conv_top <= pop and conv_tol > 0. */
+    int conv_every;
+    int conv_top;
+    float conv_tol;
 } adgb_dock_params;
 
 /*
@@ -238,7 +248,8 @@ typedef struct {
  * individuals, run-best and evaluation accounting.  At the end each run's
  * best genotype is rescored in FP64 on the GPU.
  * best_genes [n_runs][6+T] float32 out; best_energy [n_runs] FP64 out;
- * evals [n_runs] out or NULL (evaluations each run spent).
+ * evals [n_runs] out or NULL (evaluations each run spent; a run stopped by
+ * the evaluation budget or by early stopping spends no more).
  * The device working set (2 populations, energies, counters, about
  * 8 * n_runs * pop * (7 + T) bytes) is allocated stream-ordered per call.
  * Errors: EINVAL, ENOTFOUND, ENOMEM, EDEVICE.
@@ -284,6 +295,17 @@ int ga_init_population_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, unsign
 int ga_generation_dev(adgb_ctx *ctx, int ligand_id, const adgb_dock_params *p, int generation,
                       const float *genes_dev, const float *energy_dev, float *genes_out_dev,
                       int *iters_out_dev, adgb_stream stream);
+
+/*
+ * ga_converged_dev - the early-stopping test of adgb_dock_params applied to
+ * n_runs populations: energy [n_runs * pop] float32 in, converged [n_runs]
+ * out (1 when the population standard deviation of the run's conv_top
+ * lowest energies, in double precision, is below conv_tol; 0 otherwise,
+ * when one of them is not finite, or when an energy of the run is NaN).  p->n_runs, p->pop, p->conv_top and
+ * p->conv_tol are used (conv_every is not).  Errors: EINVAL, EDEVICE.
+ */
+int ga_converged_dev(adgb_ctx *ctx, const adgb_dock_params *p, const float *energy_dev,
+                     int *converged_dev, adgb_stream stream);
 
 /*
  * rescore_fp64_dev - energies of n genotypes recomputed in double precision

@@ -208,12 +208,13 @@ class DockParams(C.Structure):
                 ("max_evals", C.c_longlong), ("ls_iters", C.c_int), ("ls_rate", C.c_double),
                 ("rho", C.c_double), ("eps", C.c_double), ("p_cross", C.c_double),
                 ("p_mut", C.c_double), ("mut_trans", C.c_double), ("mut_angle", C.c_double),
-                ("seed", C.c_ulonglong)]
+                ("seed", C.c_ulonglong), ("conv_every", C.c_int), ("conv_top", C.c_int),
+                ("conv_tol", C.c_double)]
 
 
 DOCK_DEFAULTS = dict(n_runs=1, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
                      ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
-                     mut_angle=np.pi / 2, seed=2410)
+                     mut_angle=np.pi / 2, seed=2410, conv_every=0, conv_top=15, conv_tol=0.15)
 
 
 def dock_params(**kw) -> DockParams:
@@ -249,6 +250,13 @@ def ga_generation(genes, energies, params: DockParams, run, gen):
     lib().orc_ga_generation(C.c_int(G), C.c_int(pop), _pd(g), _pd(e), C.byref(params),
                             C.c_int(run), C.c_int(gen), _pd(out), _pi(fl))
     return out, fl
+
+
+def converged(energies, top, tol) -> bool:
+    """Early-stopping test: population standard deviation of the `top`
+    lowest energies below tol (this project's reading)."""
+    e = _d(energies).reshape(-1)
+    return bool(lib().orc_converged(C.c_int(len(e)), _pd(e), C.c_int(top), C.c_double(tol)))
 
 
 def dock(rec, lig, params: DockParams, nthreads=0):

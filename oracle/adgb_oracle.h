@@ -77,6 +77,8 @@ typedef struct {
     double ls_rate, rho, eps;
     double p_cross, p_mut, mut_trans, mut_angle;
     unsigned long long seed;
+    int conv_every, conv_top;  /* early stopping: test every conv_every generations (0: off) */
+    double conv_tol;
 } orc_dock_params;
 
 void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);
@@ -85,6 +87,7 @@ int orc_init_individual(const orc_receptor *R, int n_tors, unsigned long long se
 int orc_ga_generation(int G, int pop, const double *genes_old, const double *energy_old,
                       const orc_dock_params *p, int run, int gen, double *genes_new,
                       int *ls_flag);
+int orc_converged(int pop, const double *energy, int top, double tol);
 int orc_dock(const orc_receptor *R, const orc_ligand *L, const orc_dock_params *p,
              double *best_genes, double *best_energy, long long *evals, int nthreads);
 double orc_sum_naive(const double *x, long n, long stride);

@@ -34,7 +34,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "validate_ligand_torsion_tree",
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
-           "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev",
+           "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev", "ga_converged_dev",
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget"]
@@ -75,12 +75,14 @@ class _DockParams(C.Structure):
                 ("max_evals", C.c_longlong), ("ls_iters", C.c_int), ("ls_rate", C.c_float),
                 ("rho", C.c_float), ("eps", C.c_float), ("p_cross", C.c_float),
                 ("p_mut", C.c_float), ("mut_trans", C.c_float), ("mut_angle", C.c_float),
-                ("seed", C.c_ulonglong), ("reduce_variant", C.c_int)]
+                ("seed", C.c_ulonglong), ("reduce_variant", C.c_int),
+                ("conv_every", C.c_int), ("conv_top", C.c_int), ("conv_tol", C.c_float)]
 
 
 DOCK_DEFAULTS = dict(n_runs=20, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
                      ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
-                     mut_angle=float(np.pi / 2), seed=2410, reduce_variant=-1)
+                     mut_angle=float(np.pi / 2), seed=2410, reduce_variant=-1,
+                     conv_every=0, conv_top=15, conv_tol=0.15)
 
 
 def dock_params(**kw) -> _DockParams:
@@ -169,6 +171,7 @@ def load(build: bool = False):
                                          vp, vp]
     L.ga_generation_dev.argtypes = [vp, C.c_int, C.POINTER(_DockParams), C.c_int, vp, vp, vp, vp,
                                     vp]
+    L.ga_converged_dev.argtypes = [vp, C.POINTER(_DockParams), vp, vp, vp]
     _lib = L
     return L
 
@@ -364,6 +367,12 @@ class Context:
         self._chk(self.lib.ga_generation_dev(self.h, lid, C.byref(params), gen, _ptr(genes),
                                              _ptr(energy), _ptr(genes_out), _ptr(iters_out),
                                              _stream()))
+
+    def ga_converged_dev(self, params, energy, converged):
+        """Early-stopping test of params (conv_top, conv_tol) on energy
+        [n_runs * pop] -> converged [n_runs] int32 (1 = converged)."""
+        self._chk(self.lib.ga_converged_dev(self.h, C.byref(params), _ptr(energy), _ptr(converged),
+                                            _stream()))
 
     # -------------------------------------------------------- host calls
     def dock(self, rid, lid, params):

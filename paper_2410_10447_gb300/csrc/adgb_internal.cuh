@@ -66,6 +66,8 @@ struct DockCfg {
     long long max_evals;
     float ls_rate, rho, eps, p_cross, p_mut, mut_trans, mut_angle;
     uint64_t seed;
+    int conv_every, conv_top;   // early stopping (conv_every = 0: off)
+    float conv_tol;
 };
 
 // Device working set of one dock call.
@@ -189,8 +191,10 @@ cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *
 cudaError_t launch_job_start(const RecDev &rec, int n_tors, const DockCfg &d, DockScratch &w,
                              cudaStream_t s);
 cudaError_t launch_job_ga(const DockCfg &d, int G, int gen, DockScratch &w, int cur, cudaStream_t s);
-cudaError_t launch_job_best(const DockCfg &d, int G, DockScratch &w, int cur, float *best_genes,
-                            cudaStream_t s);
+cudaError_t launch_job_best(const DockCfg &d, int G, int gen, DockScratch &w, int cur,
+                            float *best_genes, cudaStream_t s);
+cudaError_t launch_ga_converged(int n_runs, int pop, int top, float tol, const float *energy,
+                                int *converged, cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
                           cudaStream_t s);
 // Persistent multi-ligand local search over a device table of work items

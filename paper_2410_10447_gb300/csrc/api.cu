@@ -615,6 +615,10 @@ int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg
         !(p->p_mut >= 0.f && p->p_mut <= 1.f) || !finite(p->mut_trans) || !finite(p->mut_angle) ||
         (long long)p->n_runs * p->pop > (1 << 26))
         return ferr(err, ADGB_EINVAL, "dock: bad parameters");
+    if (p->conv_every < 0 ||
+        (p->conv_every > 0 && (p->conv_top < 2 || p->conv_top > p->pop || !(p->conv_tol > 0.f) ||
+                               !finite(p->conv_tol))))
+        return ferr(err, ADGB_EINVAL, "dock: bad early-stopping parameters");
     variant = p->reduce_variant < 0 ? default_variant : p->reduce_variant;
     if (variant < 0 || variant >= ADGB_REDUCE_N) return ferr(err, ADGB_EINVAL, "unknown reduce variant %d", variant);
     d.n_runs = p->n_runs;
@@ -630,6 +634,9 @@ int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg
     d.mut_trans = p->mut_trans;
     d.mut_angle = p->mut_angle;
     d.seed = p->seed;
+    d.conv_every = p->conv_every;
+    d.conv_top = p->conv_top;
+    d.conv_tol = p->conv_tol;
     return ADGB_OK;
 }
 
@@ -1049,6 +1056,18 @@ int ga_generation_dev(adgb_ctx *c, int ligand_id, const adgb_dock_params *p, int
     cudaError_t e = launch_ga_generation(d, 6 + L->n_tors, generation, genes_dev, energy_dev,
                                          genes_out_dev, iters_out_dev, (cudaStream_t)stream);
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ga_generation");
+}
+
+int ga_converged_dev(adgb_ctx *c, const adgb_dock_params *p, const float *energy_dev,
+                     int *converged_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (!p || !energy_dev || !converged_dev || p->n_runs < 1 || p->pop < 2 || p->pop > 1024 ||
+        p->conv_top < 2 || p->conv_top > p->pop || !(p->conv_tol > 0.f) || !finite(p->conv_tol))
+        return fail(c, ADGB_EINVAL, "ga_converged: bad arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_ga_converged(p->n_runs, p->pop, p->conv_top, p->conv_tol, energy_dev,
+                                        converged_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ga_converged");
 }
 
 int rescore_fp64_dev(adgb_ctx *c, int receptor_id, int ligand_id, const float *genes_dev, int n,

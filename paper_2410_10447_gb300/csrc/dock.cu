@@ -14,7 +14,10 @@
 //  - each individual gets a local search of ls_iters evaluations with
 //    probability ls_rate, otherwise one scoring evaluation;
 //  - a run stops after max_gens generations or once its evaluation count
-//    reaches max_evals.
+//    reaches max_evals;
+//  - early stopping (optional): after every conv_every-th generation a run
+//    stops once the population standard deviation of its conv_top lowest
+//    energies is below conv_tol (double precision from the float energies).
 #include <math.h>
 
 #include "adgb_internal.cuh"
@@ -142,13 +145,82 @@ __global__ void ga_kernel(int pop, int G, const float *go, const float *eo, cons
     }
 }
 
-// After an evaluation pass: evaluation count, run best, stop flag.
+// A run evaluated in this pass (runs stopped before it have all iters 0).
+__device__ __forceinline__ bool kk_eval_flag(const int *iters, size_t base, int pop) {
+    return pop > 0 && iters[base] > 0;
+}
+
+// Sum of one double over the block (all threads get it).
+__device__ double block_sum_f64(double v, double *s_d) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, W = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) s_d[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < W; i++) t += s_d[i];
+    __syncthreads();
+    return t;
+}
+
+// Early-stopping test of one run (whole block): the population standard
+// deviation of the `top` lowest of e[0..pop) is below tol; never with a NaN
+// energy in the population or a non-finite one among the lowest.  An
+// energy's rank is the number of energies below it (ties by index), so the
+// top set is the same multiset whatever the order; mean and spread in double.
+__device__ bool run_converged(const float *e, int pop, int top, float tol, double *s_d) {
+    double s = 0.0;
+    int bad = 0;
+    for (int k = threadIdx.x; k < pop; k += blockDim.x) {
+        const float v = e[k];
+        if (isnan(v)) bad = 1;
+        int rank = 0;
+        for (int j = 0; j < pop; j++) {
+            const float u = e[j];
+            rank += (u < v) || (u == v && j < k);
+        }
+        if (rank < top) {
+            if (!isfinite(v)) bad = 1;
+            s += (double)v;
+        }
+    }
+    bad = __syncthreads_or(bad);
+    const double mean = block_sum_f64(s, s_d) / top;
+    double q = 0.0;
+    for (int k = threadIdx.x; k < pop; k += blockDim.x) {
+        const float v = e[k];
+        int rank = 0;
+        for (int j = 0; j < pop; j++) {
+            const float u = e[j];
+            rank += (u < v) || (u == v && j < k);
+        }
+        if (rank < top) q += ((double)v - mean) * ((double)v - mean);
+    }
+    const double var = block_sum_f64(q, s_d) / top;
+    return !bad && var < (double)tol * (double)tol;
+}
+
+// ga_converged_dev: one block per run.
+__global__ void conv_kernel(int pop, int top, float tol, const float *energy, int *converged) {
+    __shared__ float s_e[1024];
+    __shared__ double s_d[32];
+    const int run = blockIdx.x;
+    for (int k = threadIdx.x; k < pop; k += blockDim.x) s_e[k] = energy[(size_t)run * pop + k];
+    __syncthreads();
+    const bool c = run_converged(s_e, pop, top, tol, s_d);
+    if (threadIdx.x == 0) converged[run] = c ? 1 : 0;
+}
+
+// After an evaluation pass: evaluation count, run best, stop flag (budget,
+// or early stopping after every conv_every-th generation gen >= 1).
 __global__ void best_kernel(int pop, int G, const float *genes, const float *energy,
                             const int *iters, float *best_genes, float *best_e,
-                            long long *evals, int *done, long long max_evals) {
+                            long long *evals, int *done, long long max_evals, int gen,
+                            int conv_every, int conv_top, float conv_tol) {
     __shared__ float s_we[32];
     __shared__ int s_wk[32];
     __shared__ long long s_n[32];
+    __shared__ float s_e[1024];
+    __shared__ double s_d[32];
     const int run = blockIdx.x;
     const size_t base = (size_t)run * pop;
     float e = INFINITY;
@@ -183,6 +255,13 @@ __global__ void best_kernel(int pop, int G, const float *genes, const float *ene
         const int k = s_wk[0];
         for (int j = threadIdx.x; j < G; j += blockDim.x)
             best_genes[(size_t)run * G + j] = genes[(base + k) * G + j];
+    }
+    // the run is evaluated this generation (not stopped before it) and due a test
+    if (conv_every > 0 && gen >= 1 && gen % conv_every == 0 && kk_eval_flag(iters, base, pop)) {
+        for (int k = threadIdx.x; k < pop; k += blockDim.x) s_e[k] = energy[base + k];
+        __syncthreads();
+        const bool c = run_converged(s_e, pop, conv_top, conv_tol, s_d);
+        if (threadIdx.x == 0 && c) done[run] = 1;
     }
 }
 
@@ -352,10 +431,17 @@ cudaError_t launch_job_ga(const DockCfg &d, int G, int gen, DockScratch &w, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_job_best(const DockCfg &d, int G, DockScratch &w, int cur, float *best_genes,
-                            cudaStream_t s) {
+cudaError_t launch_job_best(const DockCfg &d, int G, int gen, DockScratch &w, int cur,
+                            float *best_genes, cudaStream_t s) {
     best_kernel<<<d.n_runs, 128, 0, s>>>(d.pop, G, w.genes[cur], w.energy, w.iters, best_genes,
-                                         w.best_e, w.evals, w.done, d.max_evals);
+                                         w.best_e, w.evals, w.done, d.max_evals, gen, d.conv_every,
+                                         d.conv_top, d.conv_tol);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ga_converged(int n_runs, int pop, int top, float tol, const float *energy,
+                                int *converged, cudaStream_t s) {
+    conv_kernel<<<n_runs, 128, 0, s>>>(pop, top, tol, energy, converged);
     return cudaGetLastError();
 }
 
@@ -382,7 +468,8 @@ cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
         return e;
     const int bt = 128;
     best_kernel<<<d.n_runs, bt, 0, s>>>(d.pop, G, w.genes[0], w.energy, w.iters, best_genes,
-                                       w.best_e, w.evals, w.done, d.max_evals);
+                                       w.best_e, w.evals, w.done, d.max_evals, 0, d.conv_every,
+                                       d.conv_top, d.conv_tol);
     int cur = 0;
     const int gt = d.pop >= 1024 ? 1024 : ((d.pop + 31) / 32) * 32;
     const int gsm = (d.pop + 32) * 4 + 32 * 4;
@@ -394,7 +481,8 @@ cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                              d.eps, 0, w.energy, nullptr, nullptr, s, w.iters)) != cudaSuccess)
             return e;
         best_kernel<<<d.n_runs, bt, 0, s>>>(d.pop, G, w.genes[cur], w.energy, w.iters,
-                                           best_genes, w.best_e, w.evals, w.done, d.max_evals);
+                                           best_genes, w.best_e, w.evals, w.done, d.max_evals,
+                                           gen, d.conv_every, d.conv_top, d.conv_tol);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = launch_rescore_fp64(rec, lig, d.n_runs, best_genes, best_energy, s)) != cudaSuccess)

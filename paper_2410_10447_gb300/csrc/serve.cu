@@ -52,7 +52,7 @@ struct Job {
     DockScratch w{};
     float *d_best_genes = nullptr;
     double *d_best_e = nullptr;
-    long long *h_evals = nullptr;   // pinned, per run
+    long long *h_evals = nullptr;   // pinned, per run; followed by the runs' stop flags (int)
     std::vector<float> best_genes;
     std::vector<double> best_e;
     std::vector<long long> evals;
@@ -173,7 +173,8 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
                 job_layout(*j, j->mem);
                 e = cudaMemcpyAsync(j->mem, j->blob.bytes.data(), j->blob.bytes.size(),
                                     cudaMemcpyHostToDevice, s->stream);
-                if (e == cudaSuccess) e = cudaHostAlloc((void **)&j->h_evals, 8 * j->d.n_runs, cudaHostAllocDefault);
+                if (e == cudaSuccess)
+                    e = cudaHostAlloc((void **)&j->h_evals, 12 * (size_t)j->d.n_runs, cudaHostAllocDefault);
                 if (e == cudaSuccess) e = launch_job_start(j->rec, j->lig.n_tors, j->d, j->w, s->stream);
                 if (e != cudaSuccess) return e;
             }
@@ -259,9 +260,13 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     // accounting per job
     for (Job *j : act) {
         const int src = j->gen < 0 ? 0 : (j->cur ^ 1);
-        e = launch_job_best(j->d, j->G, j->w, src, j->d_best_genes, s->stream);
+        e = launch_job_best(j->d, j->G, j->gen < 0 ? 0 : j->gen + 1, j->w, src, j->d_best_genes,
+                            s->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(j->h_evals, j->w.evals, 8 * j->d.n_runs, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(j->h_evals + j->d.n_runs, j->w.done, 4 * j->d.n_runs,
+                                cudaMemcpyDeviceToHost, s->stream);
         if (e != cudaSuccess) return e;
     }
     e = cudaStreamSynchronize(s->stream);
@@ -273,10 +278,12 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     return cudaSuccess;
 }
 
+// Every run has stopped: generation limit, evaluation budget or early stopping.
 bool job_finished(const Job *j) {
     if (j->gen >= j->d.max_gens) return true;
+    const int *stopped = reinterpret_cast<const int *>(j->h_evals + j->d.n_runs);
     for (int r = 0; r < j->d.n_runs; r++)
-        if (j->h_evals[r] < j->d.max_evals) return false;
+        if (j->h_evals[r] < j->d.max_evals && !stopped[r]) return false;
     return true;
 }
 
@@ -347,7 +354,8 @@ void server_loop(adgb_server *s) {
             finished = act;
         }
         for (Job *j : finished) {
-            j->status = e != cudaSuccess ? ADGB_EDEVICE : (j->cancel ? ADGB_ECANCELLED : JOB_DONE);
+            j->status = e != cudaSuccess ? (int)ADGB_EDEVICE
+                                         : (j->cancel ? (int)ADGB_ECANCELLED : (int)JOB_DONE);
             j->t_finish = now_s(s->t0);
             s->used -= j->bytes;
             s->active.erase(std::find(s->active.begin(), s->active.end(), j));

@@ -46,7 +46,8 @@ def oracle_params(gp):
                               ls_rate=f32(gp.ls_rate), rho=f32(gp.rho), eps=f32(gp.eps),
                               p_cross=f32(gp.p_cross), p_mut=f32(gp.p_mut),
                               mut_trans=f32(gp.mut_trans), mut_angle=f32(gp.mut_angle),
-                              seed=gp.seed)
+                              seed=gp.seed, conv_every=gp.conv_every, conv_top=gp.conv_top,
+                              conv_tol=f32(gp.conv_tol))
 
 
 def ang(a, b):
@@ -160,4 +161,80 @@ def test_dock_matches_oracle_statistically(pkg, torch, w):
     _, be_ref, _ = oracle.dock(w["receptor"], w["ligand"], oracle_params(gp))
     med, med_ref = np.median(be), np.median(be_ref)
     assert abs(med - med_ref) <= 0.15 * abs(med_ref) + 1.0, (be, be_ref)
+    ctx.close()
+
+
+# ----------------------------------------------------------- early stopping
+def _conv_cases(rng, pop, top, tol):
+    """Energies of runs whose `top` lowest lie just inside, just outside and
+    far from the tolerance, with ties, shuffles and non-finite values."""
+    runs = []
+    for scale in (0.5, 0.999, 1.001, 2.0, 0.0):
+        e = rng.normal(-20.0, 2.0, pop)
+        base = rng.normal(0.0, 1.0, top)
+        base = (base - base.mean()) / base.std() if scale else np.zeros(top)
+        e[:top] = -40.0 + base * tol * scale
+        runs.append(rng.permutation(e))
+    e = rng.normal(-20.0, 2.0, pop)
+    e[:top + 3] = -30.0                      # ties across the cut
+    runs.append(e)
+    e = rng.normal(-20.0, 0.01, pop)
+    e[5] = np.nan                            # a NaN among the lowest
+    runs.append(e)
+    e = rng.normal(-20.0, 0.01, pop)
+    e[7] = np.inf                            # an unevaluated individual above the top
+    runs.append(e)
+    runs += [rng.normal(-20.0, s, pop) for s in (1e-3, 1e-2, 0.05, 0.1, 0.3)]
+    return np.array(runs, np.float32)
+
+
+@pytest.mark.parametrize("pop, top, tol", [(150, 15, 0.15), (64, 2, 0.05), (1024, 300, 1.0)])
+def test_converged_flags_match_oracle(pkg, torch, pop, top, tol):
+    ctx = pkg.Context(0)
+    rng = np.random.default_rng(pop + top)
+    e = _conv_cases(rng, pop, top, tol)
+    runs = e.shape[0]
+    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, conv_top=top, conv_tol=tol)
+    flags = torch.empty(runs, dtype=torch.int32, device="cuda")
+    ctx.ga_converged_dev(gp, torch.from_numpy(e.reshape(-1)).cuda(), flags)
+    got = flags.cpu().numpy()
+    ref = np.array([oracle.converged(e[r].astype(np.float64), top, f32(tol)) for r in range(runs)])
+    assert np.array_equal(got, ref.astype(np.int32)), (got, ref)
+    assert got[0] == 1 and got[3] == 0 and got[4] == 1 and got[6] == 0
+    ctx.close()
+
+
+def test_dock_early_stopping(pkg, torch, w):
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    runs, pop, gens, it = 4, 24, 12, 20
+    base = dict(n_runs=runs, pop=pop, max_gens=gens, ls_iters=it, ls_rate=1.0, seed=9)
+    full = pop + gens * pop * it
+    # always converged: every run stops at the first test (generation 3)
+    _, _, ev = ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=3, conv_top=6, conv_tol=1e6, **base))
+    assert np.all(ev == pop + 3 * pop * it)
+    # never converged: the full schedule, identical to early stopping off
+    off = ctx.dock(rid, lid, pkg.adgb.dock_params(**base))
+    never = ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=3, conv_top=6, conv_tol=1e-12, **base))
+    assert np.all(never[2] == full)
+    for a, b in zip(off, never):
+        assert np.array_equal(a, b)
+    # a tolerance in between: runs stop at test generations, deterministically,
+    # and keep the best they found before stopping
+    gp = pkg.adgb.dock_params(conv_every=2, conv_top=6, conv_tol=0.5, **base)
+    bg, be, ev = ctx.dock(rid, lid, gp)
+    stop_gen = (ev - pop) // (pop * it)
+    assert np.all((ev - pop) % (pop * it) == 0)
+    assert np.all((stop_gen % 2 == 0) | (stop_gen == gens)) and np.all(stop_gen >= 2)
+    bg2, be2, ev2 = ctx.dock(rid, lid, gp)
+    assert np.array_equal(bg, bg2) and np.array_equal(be, be2) and np.array_equal(ev, ev2)
+    R, L = oracle.Receptor(w["receptor"]), oracle.Ligand(w["ligand"])
+    for r in range(runs):
+        assert abs(be[r] - oracle.score(R, L, bg[r])[0]) <= 1e-9 * max(abs(be[r]), 1.0)
+    # bad parameters are refused
+    with pytest.raises(pkg.AdgbError):
+        ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=2, conv_top=1, **base))
+    with pytest.raises(pkg.AdgbError):
+        ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=2, conv_top=6, conv_tol=0.0, **base))
     ctx.close()

@@ -66,16 +66,24 @@ def test_job_same_alone_and_in_mix(pkg, torch, world):
     ctx.close()
 
 
-def test_job_equals_dock_call(pkg, torch, world):
+@pytest.mark.parametrize("conv", [None, (1, 5, 1e6), (2, 5, 0.5)])
+def test_job_equals_dock_call(pkg, torch, world, conv):
+    """A served job gives what dock() gives, also with early stopping (runs
+    that stop early stop at the same generation)."""
     recs, ligs = world
     ctx = pkg.Context(0)
     rid = ctx.upload_receptor_grids(recs[0])
     lid = ctx.upload_ligand_torsion_tree(ligs[0])
-    prm = params(pkg, 7, runs=3, pop=20, gens=3, iters=25)
+    prm = params(pkg, 7, runs=3, pop=20, gens=6 if conv else 3, iters=25)
+    if conv:
+        prm.conv_every, prm.conv_top, prm.conv_tol = conv
     gd, ed, vd = ctx.dock(rid, lid, prm)
     srv = pkg.Server(ctx)
     j = srv.submit(rid, ligs[0], prm)
-    assert srv.wait(j, 60000)["status"] == 0
+    info = srv.wait(j, 60000)
+    assert info["status"] == 0
+    if conv and conv[2] > 1e5:
+        assert info["generations"] == 1      # every run converged at the first test
     gs, es, vs = srv.result(j)
     assert np.array_equal(vd, vs)
     assert np.allclose(gs, gd[:, :gs.shape[1]], atol=1e-5, rtol=0)

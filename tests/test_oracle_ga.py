@@ -109,3 +109,39 @@ def test_dock_accounting_and_best(oracle_mod, w):
     prm2 = oracle_mod.dock_params(n_runs=1, pop=12, max_gens=10, max_evals=100, ls_iters=15, ls_rate=1.0, seed=5)
     _, _, ev2 = oracle_mod.dock(w["receptor"], w["ligand"], prm2)
     assert ev2[0] == 12 + 12 * 15
+
+
+# ----------------------------------------------------------- early stopping
+def test_converged_is_the_std_of_the_lowest(oracle_mod):
+    """The early-stopping test reduces to numpy's population standard
+    deviation of the sorted lowest energies."""
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        pop = int(rng.integers(2, 300))
+        top = int(rng.integers(2, pop + 1))
+        e = rng.normal(-10.0, 10.0 ** rng.uniform(-3, 1), pop)
+        tol = float(10.0 ** rng.uniform(-3, 1))
+        ref = np.std(np.sort(e)[:top]) < tol
+        assert oracle_mod.converged(e, top, tol) == ref
+        assert oracle_mod.converged(rng.permutation(e), top, tol) == ref
+    # worked case: lowest three are -10.1, -10.0, -9.9 -> std = sqrt(0.02 / 3) = 0.08165
+    e = np.array([5.0, -10.0, 7.0, -9.9, -10.1, 3.0])
+    assert oracle_mod.converged(e, 3, 0.082) and not oracle_mod.converged(e, 3, 0.0816)
+    # non-finite among the lowest: not converged; above them: irrelevant
+    assert not oracle_mod.converged(np.array([-1.0, np.nan, -1.0, 4.0]), 2, 1.0)
+    assert oracle_mod.converged(np.array([-1.0, np.inf, -1.0, 4.0]), 2, 1.0)
+
+
+def test_dock_early_stopping_accounting(oracle_mod, w):
+    rec, lig = w["receptor"], w["ligand"]
+    base = dict(n_runs=3, pop=12, max_gens=6, ls_iters=5, ls_rate=1.0, seed=3)
+    full = 12 + 6 * 12 * 5
+    _, _, ev = oracle_mod.dock(rec, lig, oracle_mod.dock_params(**base))
+    assert np.all(ev == full)
+    _, _, ev = oracle_mod.dock(rec, lig, oracle_mod.dock_params(conv_every=2, conv_top=4,
+                                                                  conv_tol=1e6, **base))
+    assert np.all(ev == 12 + 2 * 12 * 5)
+    b0, e0, ev0 = oracle_mod.dock(rec, lig, oracle_mod.dock_params(**base))
+    b1, e1, ev1 = oracle_mod.dock(rec, lig, oracle_mod.dock_params(conv_every=2, conv_top=4,
+                                                                     conv_tol=1e-12, **base))
+    assert np.array_equal(ev0, ev1) and np.array_equal(e0, e1) and np.array_equal(b0, b1)
