@@ -205,6 +205,43 @@ int local_search_dev(adgb_ctx *ctx, int receptor_id, int ligand_id,
 int local_search(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes,
                  int n, const adgb_ls_params *p, float *best_energy, float *state);
 
+/*
+ * local_search_sw - Solis-Wets local search of n genotypes (Solis and Wets,
+ * 1981; the derivative-free alternative to the gradient search among the
+ * local searches Sec. 2.1 names).  Energy only: each evaluation is the
+ * scoring function without its gradient, with one reduction of E.
+ * Every step draws d_j = bias_j + rho * s_j * z_j (z_j standard normal from
+ * Philox4x32-10 keyed by seed, counter (genotype, step, 0x5357 << 16 | call,
+ * j / 4), Box-Muller on two 24-bit uniforms; s_j = 1 A for the translation
+ * genes, angle_scale rad for the angle genes; torsions wrapped), tries x + d
+ * and, if that is not lower, x - d.  A lower energy moves x (bias <- 0.2 bias
+ * + 0.4 d forward, bias - 0.4 d backward), otherwise bias <- bias / 2;
+ * max_succ successes in a row double rho, max_fail failures halve it.  A
+ * search stops after max_evals evaluations (the start point counts one) or
+ * once rho < rho_min.  genes [n][6+T] in: start, out: final genotype (the
+ * lowest energy seen, since x only moves downhill); energy [n] out; evals [n]
+ * out or NULL; state [n][2(6+T)+5] out or NULL: (x, bias, rho, successes,
+ * failures, E(x), steps); with ADGB_LS_RESUME also in (genes in ignored; the
+ * call then spends up to max_evals further evaluations).
+ * Errors: EINVAL, ENOTFOUND, EDEVICE.
+ */
+typedef struct {
+    int max_evals;           /* evaluations a search may spend, >= 1 */
+    float rho0, rho_min;     /* initial step scale, and the scale below which a search stops */
+    int max_succ, max_fail;  /* successes / failures in a row before rho doubles / halves */
+    float angle_scale;       /* deviation of the angle genes per unit rho (rad) */
+    unsigned long long seed;
+    int call;                /* random-stream selector, 0..65535 */
+    int reduce_variant;      /* ADGB_REDUCE_* or -1 for the context default */
+    int flags;               /* ADGB_LS_RESUME */
+} adgb_sw_params;
+
+int local_search_sw_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes_dev, int n,
+                        const adgb_sw_params *p, float *energy_dev, int *evals_dev,
+                        float *state_dev, adgb_stream stream);
+int local_search_sw(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes, int n,
+                    const adgb_sw_params *p, float *energy, int *evals, float *state);
+
 /* Lamarckian GA docking parameters (Sec. 2.1: a GA proposes genotypes and
  * each is refined by the local search).  The paper prints no GA rules; the
  * library's rules: individual 0 of a generation is the previous best; every

@@ -252,6 +252,43 @@ def ga_generation(genes, energies, params: DockParams, run, gen):
     return out, fl
 
 
+class SwParams(C.Structure):
+    _fields_ = [("max_evals", C.c_int), ("max_succ", C.c_int), ("max_fail", C.c_int),
+                ("rho0", C.c_double), ("rho_min", C.c_double), ("angle_scale", C.c_double),
+                ("seed", C.c_ulonglong), ("call", C.c_int)]
+
+
+SW_DEFAULTS = dict(max_evals=300, max_succ=4, max_fail=4, rho0=1.0, rho_min=0.01,
+                   angle_scale=1.0, seed=2410, call=0)
+
+
+def sw_params(**kw) -> SwParams:
+    d = dict(SW_DEFAULTS)
+    d.update(kw)
+    return SwParams(*[d[f] for f, _ in SwParams._fields_])
+
+
+def sw_normal(seed, genotype, step, call, j) -> float:
+    f = lib().orc_sw_normal
+    f.restype = C.c_double
+    return f(C.c_ulonglong(seed), C.c_uint(genotype), C.c_uint(step), C.c_uint(call), C.c_int(j))
+
+
+def sw_search(rec, lig, genes, params: SwParams, genotype=0, state=None):
+    """Solis-Wets search of one genotype: (energy, genes, evals, state
+    [2G+5]); resumes from `state` when given."""
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes).copy()
+    st = np.zeros(2 * L.G + 5) if state is None else _d(state).copy()
+    e = C.c_double()
+    ev = C.c_int()
+    rc = lib().orc_sw_search(C.byref(R.c), C.byref(L.c), _pd(g), C.byref(params), C.c_int(genotype),
+                             C.c_int(0 if state is None else 1), _pd(st), C.byref(e), C.byref(ev))
+    if rc:
+        raise ValueError("orc_sw_search failed")
+    return e.value, g, ev.value, st
+
+
 def converged(energies, top, tol) -> bool:
     """Early-stopping test: population standard deviation of the `top`
     lowest energies below tol (this project's reading)."""

@@ -593,6 +593,113 @@ int orc_ga_generation(int G, int pop, const double *go, const double *eo,
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * Solis-Wets local search (Solis and Wets, "Minimization by random search
+ * techniques", Math. Oper. Res. 6, 1981; AutoDock's derivative-free local
+ * search).  This project's reading, step by step:
+ *   x: genotype, E(x) its energy, bias b (zero at the start), scale rho.
+ *   One step: d_j = b_j + rho * s_j * z_j with z_j standard normal and
+ *   s_j = 1 (translation genes, A) or angle_scale (angles, rad).
+ *   If E(x + d) < E(x): x <- x + d, b <- 0.2 b + 0.4 d (success).
+ *   Else if E(x - d) < E(x): x <- x - d, b <- b - 0.4 d (success).
+ *   Else b <- 0.5 b (failure).
+ *   max_succ successes in a row: rho <- 2 rho; max_fail failures in a row:
+ *   rho <- rho / 2.  Stop after max_evals evaluations or when rho < rho_min.
+ * Torsions are wrapped to [-pi, pi) after every move.  The normal numbers
+ * come from Philox4x32-10 (key = seed, counter = (genotype, step,
+ * 0x5357 << 16 | call, j / 4)) by the Box-Muller transform of two 24-bit
+ * uniforms u1 = ((w >> 8) + 1) 2^-24, u2 = (w' >> 8) 2^-24.
+ * ------------------------------------------------------------------------ */
+double orc_sw_normal(unsigned long long seed, unsigned int genotype, unsigned int step,
+                     unsigned int call, int j) {
+    const unsigned int ctr[4] = {genotype, step, 0x53570000u | (call & 0xFFFFu), (unsigned int)j >> 2};
+    const unsigned int key[2] = {(unsigned int)seed, (unsigned int)(seed >> 32)};
+    unsigned int o[4];
+    orc_philox4x32_10(ctr, key, o);
+    const int second = (j >> 1) & 1;
+    const unsigned int a = second ? o[2] : o[0], b = second ? o[3] : o[1];
+    const double u1 = (double)((a >> 8) + 1u) / 16777216.0;
+    const double u2 = (double)(b >> 8) / 16777216.0;
+    const double r = sqrt(-2.0 * log(u1));
+    return (j & 1) ? r * sin(2.0 * PI * u2) : r * cos(2.0 * PI * u2);
+}
+
+int orc_sw_search(const orc_receptor *R, const orc_ligand *L, double *genes,
+                  const orc_sw_params *p, int genotype, int resume, double *state,
+                  double *energy, int *evals_out) {
+    const int G = 6 + L->n_tors;
+    double *x = (double *)malloc(sizeof(double) * 4 * (size_t)G);
+    double *b = x + G, *d = x + 2 * G, *y = x + 3 * G;
+    double rho, ex;
+    int ns, nf, step, evals = 0, bad = 0;
+    if (resume) {
+        for (int j = 0; j < G; j++) { x[j] = state[j]; b[j] = state[G + j]; }
+        rho = state[2 * G];
+        ns = (int)state[2 * G + 1];
+        nf = (int)state[2 * G + 2];
+        ex = state[2 * G + 3];
+        step = (int)state[2 * G + 4];
+    } else {
+        for (int j = 0; j < G; j++) { x[j] = genes[j]; b[j] = 0.0; }
+        rho = p->rho0;
+        ns = nf = step = 0;
+        ex = INFINITY;
+        if (p->max_evals > 0) {
+            bad |= orc_score(R, L, x, &ex, NULL, NULL, NULL) != 0;
+            evals = 1;
+        }
+    }
+    while (evals < p->max_evals && rho >= p->rho_min) {
+        for (int j = 0; j < G; j++) {
+            const double z = orc_sw_normal(p->seed, (unsigned int)genotype, (unsigned int)step,
+                                           (unsigned int)p->call, j);
+            d[j] = b[j] + rho * (j < 3 ? 1.0 : p->angle_scale) * z;
+            y[j] = x[j] + d[j];
+            if (j >= 6) y[j] = wrap_angle(y[j]);
+        }
+        double e1;
+        bad |= orc_score(R, L, y, &e1, NULL, NULL, NULL) != 0;
+        evals++;
+        int ok = e1 < ex;
+        if (ok) {
+            ex = e1;
+            for (int j = 0; j < G; j++) { x[j] = y[j]; b[j] = 0.2 * b[j] + 0.4 * d[j]; }
+        } else if (evals < p->max_evals) {
+            for (int j = 0; j < G; j++) {
+                y[j] = x[j] - d[j];
+                if (j >= 6) y[j] = wrap_angle(y[j]);
+            }
+            double e2;
+            bad |= orc_score(R, L, y, &e2, NULL, NULL, NULL) != 0;
+            evals++;
+            ok = e2 < ex;
+            if (ok) {
+                ex = e2;
+                for (int j = 0; j < G; j++) { x[j] = y[j]; b[j] = b[j] - 0.4 * d[j]; }
+            }
+        }
+        if (!ok)
+            for (int j = 0; j < G; j++) b[j] *= 0.5;
+        if (ok) { ns++; nf = 0; } else { nf++; ns = 0; }
+        if (ns >= p->max_succ) { rho *= 2.0; ns = 0; }
+        if (nf >= p->max_fail) { rho *= 0.5; nf = 0; }
+        step++;
+    }
+    for (int j = 0; j < G; j++) genes[j] = x[j];
+    if (state) {
+        for (int j = 0; j < G; j++) { state[j] = x[j]; state[G + j] = b[j]; }
+        state[2 * G] = rho;
+        state[2 * G + 1] = ns;
+        state[2 * G + 2] = nf;
+        state[2 * G + 3] = ex;
+        state[2 * G + 4] = step;
+    }
+    *energy = ex;
+    if (evals_out) *evals_out = evals;
+    free(x);
+    return bad ? -1 : 0;
+}
+
 /* Early stopping, this project's reading (Sec. 5.3 speaks of runs that do
  * or do not converge without defining the test): the population standard
  * deviation of the `top` lowest energies is below tol.  Written as the

@@ -90,6 +90,18 @@ int orc_ga_generation(int G, int pop, const double *genes_old, const double *ene
 int orc_converged(int pop, const double *energy, int top, double tol);
 int orc_dock(const orc_receptor *R, const orc_ligand *L, const orc_dock_params *p,
              double *best_genes, double *best_energy, long long *evals, int nthreads);
+/* Solis-Wets local search (Solis and Wets, 1981), energy only */
+typedef struct {
+    int max_evals, max_succ, max_fail;
+    double rho0, rho_min, angle_scale;
+    unsigned long long seed;
+    int call;
+} orc_sw_params;
+double orc_sw_normal(unsigned long long seed, unsigned int genotype, unsigned int step,
+                     unsigned int call, int j);
+int orc_sw_search(const orc_receptor *R, const orc_ligand *L, double *genes,
+                  const orc_sw_params *p, int genotype, int resume, double *state,
+                  double *energy, int *evals);
 double orc_sum_naive(const double *x, long n, long stride);
 double orc_sum_neumaier(const double *x, long n, long stride);
 

@@ -35,6 +35,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
            "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev", "ga_converged_dev",
+           "local_search_sw_dev", "local_search_sw",
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget"]
@@ -115,6 +116,23 @@ class _LSParams(C.Structure):
                 ("reduce_variant", C.c_int), ("flags", C.c_int)]
 
 
+class _SwParams(C.Structure):
+    _fields_ = [("max_evals", C.c_int), ("rho0", C.c_float), ("rho_min", C.c_float),
+                ("max_succ", C.c_int), ("max_fail", C.c_int), ("angle_scale", C.c_float),
+                ("seed", C.c_ulonglong), ("call", C.c_int), ("reduce_variant", C.c_int),
+                ("flags", C.c_int)]
+
+
+SW_DEFAULTS = dict(max_evals=300, rho0=1.0, rho_min=0.01, max_succ=4, max_fail=4,
+                   angle_scale=1.0, seed=2410, call=0, reduce_variant=-1, flags=0)
+
+
+def sw_params(**kw) -> _SwParams:
+    d = dict(SW_DEFAULTS)
+    d.update(kw)
+    return _SwParams(*[d[f] for f, _ in _SwParams._fields_])
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -146,6 +164,10 @@ def load(build: bool = False):
     L.local_search_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_LSParams),
                                    vp, vp, vp]
     L.local_search.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_LSParams), vp, vp]
+    L.local_search_sw_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_SwParams), vp,
+                                      vp, vp, vp]
+    L.local_search_sw.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.POINTER(_SwParams), vp, vp,
+                                  vp]
     L.reduce4_bench_dev.argtypes = [vp, C.c_int, vp, C.c_int, C.c_int, C.c_int, vp, vp]
     L.dock_dev.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp, vp]
     L.dock.argtypes = [vp, C.c_int, C.c_int, C.POINTER(_DockParams), vp, vp, vp]
@@ -416,6 +438,30 @@ class Context:
         self._chk(self.lib.local_search(self.h, rid, lid, g.ctypes.data, n, C.byref(p), e.ctypes.data,
                                         _ptr(st)))
         return e, g, st
+
+    def local_search_sw_dev(self, rid, lid, genes, energy, params, evals=None, state=None):
+        """Solis-Wets search of device genotypes in place (energy-only)."""
+        _check_dev(genes, "genes")
+        _check_dev(energy, "energy")
+        self._chk(self.lib.local_search_sw_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
+                                               C.byref(params), _ptr(energy), _ptr(evals),
+                                               _ptr(state), _stream()))
+
+    def local_search_sw(self, rid, lid, genes, params, state=None, want_state=False):
+        """Host-buffer Solis-Wets search: (energy [n], genes [n][G], evals [n],
+        state [n][2G+5] or None); resumes from `state` when params.flags has
+        LS_RESUME."""
+        g = _f32(genes).copy()
+        n, G = g.shape
+        e = np.zeros(n, np.float32)
+        ev = np.zeros(n, np.int32)
+        st = None
+        if (params.flags & LS_RESUME) or want_state:
+            st = (np.array(state, dtype=np.float32, order="C", copy=True) if state is not None
+                  else np.zeros((n, 2 * G + 5), np.float32))
+        self._chk(self.lib.local_search_sw(self.h, rid, lid, g.ctypes.data, n, C.byref(params),
+                                           e.ctypes.data, ev.ctypes.data, _ptr(st)))
+        return e, g, ev, st
 
     def local_search_host_ptr(self, rid, lid, genes_ptr, n, iters, best_ptr, rho=0.8, eps=1e-2,
                               variant=-1):

@@ -60,6 +60,15 @@ struct LigDev {
     float hb_R, hb_eps;
 };
 
+// Solis-Wets local search parameters as the kernels see them.
+struct SwCfg {
+    int max_evals, max_succ, max_fail, resume;
+    float rho0, rho_min, angle_scale;
+    uint64_t seed;
+    uint32_t call;     // random-stream selector
+    int pose_base;     // random-stream index of the first genotype
+};
+
 // Lamarckian GA parameters as the kernels see them.
 struct DockCfg {
     int n_runs, pop, max_gens, ls_iters;
@@ -179,6 +188,8 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                         int iters, float rho, float eps, int resume, float *energy,
                         float *grad, float *state, cudaStream_t s,
                         const int *iters_per_pose = nullptr);
+cudaError_t launch_sw(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const SwCfg &c,
+                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s);
 cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const DockCfg &d,
                         float *best_genes, double *best_energy, long long *evals_out,
                         DockScratch &w, cudaStream_t s);

@@ -942,6 +942,80 @@ int local_search(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int 
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search");
 }
 
+static int check_sw(adgb_ctx *c, const adgb_sw_params *p, int &variant, SwCfg &w) {
+    if (!p) return fail(c, ADGB_EINVAL, "local_search_sw: null parameters");
+    if (p->max_evals < 1 || !(p->rho0 > 0.f) || !finite(p->rho0) || !(p->rho_min >= 0.f) ||
+        !finite(p->rho_min) || p->max_succ < 1 || p->max_fail < 1 || !(p->angle_scale > 0.f) ||
+        !finite(p->angle_scale) || p->call < 0 || p->call > 0xFFFF)
+        return fail(c, ADGB_EINVAL, "local_search_sw: bad parameters");
+    variant = p->reduce_variant;
+    int rc = check_variant(c, variant);
+    if (rc) return rc;
+    w.max_evals = p->max_evals;
+    w.max_succ = p->max_succ;
+    w.max_fail = p->max_fail;
+    w.resume = (p->flags & ADGB_LS_RESUME) ? 1 : 0;
+    w.rho0 = p->rho0;
+    w.rho_min = p->rho_min;
+    w.angle_scale = p->angle_scale;
+    w.seed = p->seed;
+    w.call = (uint32_t)p->call;
+    w.pose_base = 0;
+    return ADGB_OK;
+}
+
+int local_search_sw_dev(adgb_ctx *c, int receptor_id, int ligand_id, float *genes_dev, int n,
+                        const adgb_sw_params *p, float *energy_dev, int *evals_dev,
+                        float *state_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    SwCfg w;
+    int rc = check_sw(c, p, variant, w);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!genes_dev || !energy_dev || (w.resume && !state_dev))))
+        return fail(c, ADGB_EINVAL, "local_search_sw: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L))) return rc;
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_sw(R->dev, L->dev, pick_cfg(c, *L, variant), w, genes_dev, n, energy_dev,
+                              evals_dev, state_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search_sw");
+}
+
+int local_search_sw(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int n,
+                    const adgb_sw_params *p, float *energy, int *evals, float *state) {
+    if (!c) return ADGB_EINVAL;
+    int variant;
+    SwCfg w;
+    int rc = check_sw(c, p, variant, w);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!genes || !energy || (w.resume && !state))))
+        return fail(c, ADGB_EINVAL, "local_search_sw: bad arguments");
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    if ((rc = lookup(c, receptor_id, ligand_id, &R, &L)) || n == 0) return rc;
+    DeviceGuard g(c->device);
+    const size_t G = 6 + L->n_tors, SW = 2 * G + 5;
+    const size_t bg = al256(4 * G * n), be = al256(4 * (size_t)n), bv = al256(4 * (size_t)n);
+    const size_t bs = state ? al256(4 * SW * n) : 0;
+    if ((rc = stage_reserve(c, bg + be + bv + bs))) return rc;
+    char *base = (char *)c->stage;
+    float *dg = (float *)base, *de = (float *)(base + bg);
+    int *dv = (int *)(base + bg + be);
+    float *ds = state ? (float *)(base + bg + be + bv) : nullptr;
+    cudaError_t e = cudaMemcpyAsync(dg, genes, 4 * G * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && w.resume) e = cudaMemcpyAsync(ds, state, 4 * SW * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_sw(R->dev, L->dev, pick_cfg(c, *L, variant), w, dg, n, de, dv, ds, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(genes, dg, 4 * G * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && evals) e = cudaMemcpyAsync(evals, dv, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && state) e = cudaMemcpyAsync(state, ds, 4 * SW * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search_sw");
+}
+
 static int check_dock(adgb_ctx *c, const adgb_dock_params *p, int &variant, DockCfg &d) {
     return dock_cfg_from_params(p, c->opts.reduce_variant, d, variant, &c->err);
 }

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "adgb_internal.cuh"
+#include "philox.cuh"
 #include "reduce.cuh"
 
 namespace adgb {
@@ -682,6 +683,258 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
     if (gt == 0) io.energy[0] = best_e;
 }
 
+// ---------------------------------------------------------------------------
+// Solis-Wets local search (Solis and Wets, Math. Oper. Res. 6, 1981, as
+// AutoDock's alternative to the gradient search; Sec. 2.1 names both local
+// searches).  Energy only: no forces, gather, torsion scans or gene gradient,
+// one reduction of E per evaluation.  Each step draws a deviate
+// d = bias + rho * sigma_j * z (z standard normal, sigma_j = 1 A for the
+// translation genes, angle_scale rad for the angles), tries x + d, then x - d;
+// a success moves x and updates the bias (0.2 b + 0.4 d forward, b - 0.4 d
+// backward), a failure halves the bias; max_succ successes in a row double
+// rho, max_fail failures halve it.  A search ends after max_evals
+// evaluations or when rho < rho_min.  x only ever moves to a lower energy,
+// so the final x is the best seen.
+// ---------------------------------------------------------------------------
+struct SwArgs {
+    RecDev rec;
+    LigDev lig;
+    SmemLayout L;
+    float *genes;         // [n][G] in (start) / out (final = best)
+    float *energy;        // [n] out
+    int *evals;           // [n] out or null
+    float *state;         // [n][2G + 5] (x, bias, rho, successes, failures, E, step) or null
+    int n, max_evals, max_succ, max_fail, resume;
+    float rho0, rho_min, angle_scale;
+    uint64_t seed;
+    uint32_t call;        // random-stream selector (with the genotype index and the step)
+    int pose_base;        // genotype index of genes[0] in the random stream
+};
+
+constexpr uint32_t SW_TAG = 0x53570000u;
+
+// Standard normal number j of step `it` of genotype `pose`: Box-Muller on
+// two 24-bit uniforms of one Philox4x32-10 output (u1 in (0, 1], u2 in [0, 1)).
+__device__ __forceinline__ float sw_normal(uint64_t seed, uint32_t pose, uint32_t it,
+                                           uint32_t call, int j) {
+    const Philox4 o = philox4x32_10(pose, it, SW_TAG | (call & 0xFFFFu), (uint32_t)j >> 2,
+                                    (uint32_t)seed, (uint32_t)(seed >> 32));
+    const bool second = (j >> 1) & 1;
+    const uint32_t a = second ? o.z : o.x, b = second ? o.w : o.y;
+    const float u1 = (float)((a >> 8) + 1u) * (1.0f / 16777216.0f);
+    const float u2 = (float)(b >> 8) * (1.0f / 16777216.0f);
+    const float r = sqrtf(-2.f * logf(u1));
+    float sn, cs;
+    sincospif(2.f * u2, &sn, &cs);
+    return (j & 1) ? r * sn : r * cs;
+}
+
+template <int TPP, int VAR>
+__device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayout &L,
+                                               const LigDev &lig, const RecDev &rec,
+                                               const StagedLig &sl, const int group, const int gt,
+                                               const SwArgs &a, const int pose, Tc05Warp &tw) {
+    const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T, NP = lig.n_pairs;
+    float4 *s_ref = reinterpret_cast<float4 *>(sm + L.ref);
+    int *s_type = reinterpret_cast<int *>(sm + L.type);
+    int *s_frag = reinterpret_cast<int *>(sm + L.frag);
+    int *s_tpar = reinterpret_cast<int *>(sm + L.tparent);
+    float4 *s_tax = reinterpret_cast<float4 *>(sm + L.taxis);
+    float4 *s_tb = reinterpret_cast<float4 *>(sm + L.tbref);
+    const float4 *pconst = lig.pconst;
+    const uint32_t *prs = sl.prs;
+    unsigned char *P = sm + L.pose0 + group * L.pose_stride;
+    float4 *xyz = reinterpret_cast<float4 *>(P + L.p_xyz);
+    float *genes_s = reinterpret_cast<float *>(P + L.p_genes);
+    float2 *sc = reinterpret_cast<float2 *>(P + L.p_sc);
+    float *red = reinterpret_cast<float *>(P + L.p_red);
+    float *stage = reinterpret_cast<float *>(P + L.p_stage) + (gt >> 5) * 32 * 12;
+    constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
+
+    // energy of the genotype held lane-wise in g[] (whole group)
+    auto energy = [&](const float *g) -> float {
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int j = gt + r * TPP;
+            if (r * TPP < G) {
+                const bool full = j == 3 || j == 4;
+                float sh, ch;
+                sincosf(full ? g[r] : 0.5f * g[r], &sh, &ch);
+                if (j < G) {
+                    genes_s[j] = g[r];
+                    const float2 v = full ? make_float2(sh, ch)
+                                          : make_float2(2.f * sh * ch, 2.f * sh * sh);
+                    if (j >= 6) sc[j - 6] = v;
+                    else if (j >= 3) sc[SC_ROT + j - 3] = v;
+                }
+            }
+        }
+        group_sync<TPP>(group);
+        const float3 tr = make_float3(genes_s[0], genes_s[1], genes_s[2]);
+        const float2 sphi = sc[SC_ROT], sth = sc[SC_ROT + 1], sal = sc[SC_ROT + 2];
+        const float3 u = make_float3(sth.x * sphi.y, sth.x * sphi.x, sth.y);
+        const float s = sal.x, o = sal.y;
+        const float m00 = o * (u.x * u.x - 1.f), m11 = o * (u.y * u.y - 1.f),
+                    m22 = o * (u.z * u.z - 1.f);
+        const float m01 = o * u.x * u.y - s * u.z, m10 = o * u.x * u.y + s * u.z;
+        const float m02 = o * u.x * u.z + s * u.y, m20 = o * u.x * u.z - s * u.y;
+        const float m12 = o * u.y * u.z - s * u.x, m21 = o * u.y * u.z + s * u.x;
+        float e_part = 0.f;
+        for (int i = gt; i < N; i += TPP) {
+            const float4 r4 = s_ref[i];
+            float3 p = make_float3(r4.x, r4.y, r4.z);
+            for (int k = s_frag[i]; k >= 0; k = s_tpar[k]) rotate_about(p, s_tax[k], s_tb[k], sc[k]);
+            float3 x;
+            x.x = p.x + (m00 * p.x + m01 * p.y + m02 * p.z) + tr.x;
+            x.y = p.y + (m10 * p.x + m11 * p.y + m12 * p.z) + tr.y;
+            x.z = p.z + (m20 * p.x + m21 * p.y + m22 * p.z) + tr.z;
+            xyz[i] = make_float4(x.x, x.y, x.z, r4.w);
+            float3 gi;
+            e_part += inter_atom(rec, s_type[i], r4.w, x, gi);
+        }
+        group_sync<TPP>(group);
+#pragma unroll 2
+        for (int p = gt; p < NP; p += TPP) {
+            const uint32_t pr = prs[p];
+            float3 f;
+            e_part += pair_term(xyz[pr & 255], xyz[(pr >> 8) & 255], __ldg(pconst + p),
+                                (pr >> 24) & 1, f);
+        }
+        float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        group_sum8<TPP, VAR>(v, red, stage, group, gt, tw);
+        group_sync<TPP>(group);   // every lane is done with genes_s, sc and xyz
+        return v[0];
+    };
+
+    float *gio = a.genes + (size_t)pose * G;
+    float *st = a.state ? a.state + (size_t)pose * (2 * G + 5) : nullptr;
+    float x[NG], bias[NG], y[NG], d[NG];
+    float rho, Ex;
+    int ns, nf, step, evals = 0;
+#pragma unroll
+    for (int r = 0; r < NG; r++) {
+        const int j = gt + r * TPP;
+        x[r] = bias[r] = 0.f;
+        if (j < G) {
+            x[r] = a.resume ? st[j] : gio[j];
+            bias[r] = a.resume ? st[G + j] : 0.f;
+        }
+    }
+    if (a.resume) {
+        rho = st[2 * G];
+        ns = (int)st[2 * G + 1];
+        nf = (int)st[2 * G + 2];
+        Ex = st[2 * G + 3];
+        step = (int)st[2 * G + 4];
+    } else {
+        rho = a.rho0;
+        ns = nf = step = 0;
+        Ex = a.max_evals > 0 ? energy(x) : INFINITY;
+        evals = a.max_evals > 0 ? 1 : 0;
+    }
+    const uint32_t id = (uint32_t)(a.pose_base + pose);
+    while (evals < a.max_evals && rho >= a.rho_min) {
+#pragma unroll
+        for (int r = 0; r < NG; r++) {
+            const int j = gt + r * TPP;
+            d[r] = y[r] = 0.f;
+            if (j < G) {
+                const float z = sw_normal(a.seed, id, (uint32_t)step, a.call, j);
+                d[r] = bias[r] + rho * (j < 3 ? 1.f : a.angle_scale) * z;
+                float w = x[r] + d[r];
+                if (j >= 6) w -= 2.f * PI_F * floorf((w + PI_F) * (0.5f / PI_F));
+                y[r] = w;
+            }
+        }
+        const float E1 = energy(y);
+        evals++;
+        bool ok = E1 < Ex;
+        if (ok) {
+            Ex = E1;
+#pragma unroll
+            for (int r = 0; r < NG; r++) {
+                x[r] = y[r];
+                bias[r] = 0.2f * bias[r] + 0.4f * d[r];
+            }
+        } else if (evals < a.max_evals) {
+#pragma unroll
+            for (int r = 0; r < NG; r++) {
+                const int j = gt + r * TPP;
+                float w = x[r] - d[r];
+                if (j >= 6) w -= 2.f * PI_F * floorf((w + PI_F) * (0.5f / PI_F));
+                y[r] = j < G ? w : 0.f;
+            }
+            const float E2 = energy(y);
+            evals++;
+            ok = E2 < Ex;
+            if (ok) {
+                Ex = E2;
+#pragma unroll
+                for (int r = 0; r < NG; r++) {
+                    x[r] = y[r];
+                    bias[r] = bias[r] - 0.4f * d[r];
+                }
+            }
+        }
+        if (!ok) {
+#pragma unroll
+            for (int r = 0; r < NG; r++) bias[r] *= 0.5f;
+        }
+        if (ok) {
+            ns++;
+            nf = 0;
+        } else {
+            nf++;
+            ns = 0;
+        }
+        if (ns >= a.max_succ) {
+            rho *= 2.f;
+            ns = 0;
+        }
+        if (nf >= a.max_fail) {
+            rho *= 0.5f;
+            nf = 0;
+        }
+        step++;
+    }
+#pragma unroll
+    for (int r = 0; r < NG; r++) {
+        const int j = gt + r * TPP;
+        if (j < G) {
+            gio[j] = x[r];
+            if (st) {
+                st[j] = x[r];
+                st[G + j] = bias[r];
+            }
+        }
+    }
+    if (gt == 0) {
+        a.energy[pose] = Ex;
+        if (a.evals) a.evals[pose] = evals;
+        if (st) {
+            st[2 * G] = rho;
+            st[2 * G + 1] = (float)ns;
+            st[2 * G + 2] = (float)nf;
+            st[2 * G + 3] = Ex;
+            st[2 * G + 4] = (float)step;
+        }
+    }
+}
+
+template <int TPP, int VAR>
+__global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) sw_kernel(const SwArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + tc_front<VAR>();
+    const StagedLig sl = stage_ligand(sm, a.L, a.lig);
+    Tc05Warp tw;
+    tc_begin<VAR>(smem_raw, tw);
+    __syncthreads();
+    const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
+    const int pose = blockIdx.x * (blockDim.x / TPP) + group;
+    if (pose < a.n) search_pose_sw<TPP, VAR>(sm, a.L, a.lig, a.rec, sl, group, gt, a, pose, tw);
+    tc_end<VAR>(tw);
+}
+
 template <int TPP, int VAR>
 __device__ __forceinline__ void eval_one(const EvalArgs &a, const StagedLig &sl, unsigned char *sm,
                                          int group, int gt, int pose, Tc05Warp &tw) {
@@ -923,6 +1176,62 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
         case 32: return launch_v<32>(a, cfg.ppb, cfg.variant, smem, s);
         case 64: return launch_v<64>(a, cfg.ppb, cfg.variant, smem, s);
         case 128: return launch_v<128>(a, cfg.ppb, cfg.variant, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int TPP, int VAR>
+static cudaError_t launch_sw_t(const SwArgs &a, int ppb, int smem, cudaStream_t s) {
+    auto k = sw_kernel<TPP, VAR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<(a.n + ppb - 1) / ppb, TPP * ppb, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int TPP>
+static cudaError_t launch_sw_v(const SwArgs &a, int ppb, int variant, int smem, cudaStream_t s) {
+    switch (variant) {
+        case ADGB_REDUCE_SHFL: return launch_sw_t<TPP, ADGB_REDUCE_SHFL>(a, ppb, smem, s);
+        case ADGB_REDUCE_MMA_TF32X2: return launch_sw_t<TPP, ADGB_REDUCE_MMA_TF32X2>(a, ppb, smem, s);
+        case ADGB_REDUCE_MMA_BF16X3: return launch_sw_t<TPP, ADGB_REDUCE_MMA_BF16X3>(a, ppb, smem, s);
+        case ADGB_REDUCE_TCGEN05: return launch_sw_t<TPP, ADGB_REDUCE_TCGEN05>(a, ppb, smem, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_sw(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const SwCfg &c,
+                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    SwArgs a;
+    a.rec = rec;
+    a.lig = lig;
+    a.L.make(lig.n_atoms, lig.n_tors, cfg.ppb, cfg.tpp / 32, cfg.chunk, lig.n_pairs,
+             cfg.stage_pairs != 0, uses_mma_stage(cfg.variant));
+    a.genes = genes;
+    a.energy = energy;
+    a.evals = evals;
+    a.state = state;
+    a.n = n;
+    a.max_evals = c.max_evals;
+    a.max_succ = c.max_succ;
+    a.max_fail = c.max_fail;
+    a.resume = c.resume;
+    a.rho0 = c.rho0;
+    a.rho_min = c.rho_min;
+    a.angle_scale = c.angle_scale;
+    a.seed = c.seed;
+    a.call = c.call;
+    a.pose_base = c.pose_base;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int smem = eval_smem_bytes(a.L.total, cfg, dev, false);
+    if (smem < 0) return cudaErrorInvalidValue;
+    switch (cfg.tpp) {
+        case 32: return launch_sw_v<32>(a, cfg.ppb, cfg.variant, smem, s);
+        case 64: return launch_sw_v<64>(a, cfg.ppb, cfg.variant, smem, s);
+        case 128: return launch_sw_v<128>(a, cfg.ppb, cfg.variant, smem, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -1,12 +1,14 @@
 """Times local-search launches on a named synthetic workload.
 
     python -m paper_2410_10447_gb300.run_ls [--workload lga_n32] [--iters 300]
-        [--n 0] [--cfgs 32:4,64:2] [--variants 0,1,2] [--reps 3]
+        [--n 0] [--cfgs 32:4,64:2] [--variants 0,1,2] [--reps 3] [--method adadelta|sw]
 
 For every launch shape "threads_per_pose:poses_per_block" and reduction
 variant it runs one warm-up launch and `reps` timed launches (CUDA events)
 and prints the best time and evaluations/s.  Used for launch-shape sweeps
-and as the target of ncu captures (one launch per repetition).
+and as the target of ncu captures (one launch per repetition).  With
+--method sw the launches are Solis-Wets searches of at most `iters`
+evaluations (energy only) and the rate counts the evaluations spent.
 """
 from __future__ import annotations
 
@@ -33,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--cfgs", default="32:4")
     ap.add_argument("--variants", default="0")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--method", default="adadelta", choices=["adadelta", "sw"])
     a = ap.parse_args(argv)
     P.load(build=True)
     w = synth.workload(a.workload, n_poses=a.n or None)
@@ -48,21 +51,27 @@ def main(argv=None):
             best = torch.empty(n, device="cuda")
             g = torch.empty_like(g0)
             ms = []
+            evc = torch.empty(n, dtype=torch.int32, device="cuda")
+            swp = P.adgb.sw_params(max_evals=a.iters, reduce_variant=v)
             for _ in range(a.reps + 1):
                 g.copy_(g0)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record()
-                ctx.local_search_dev(rid, lid, g, best, a.iters, variant=v)
+                if a.method == "sw":
+                    ctx.local_search_sw_dev(rid, lid, g, best, swp, evals=evc)
+                else:
+                    ctx.local_search_dev(rid, lid, g, best, a.iters, variant=v)
                 e1.record()
                 torch.cuda.synchronize()
                 ms.append(e0.elapsed_time(e1))
             t = min(ms[1:]) if a.reps else ms[0]
-            key = "%d:%d:v%d" % (tpp, ppb, v)
-            res[key] = dict(ms=t, evals_per_s=n * a.iters / t * 1e3,
+            evals = int(evc.sum()) if a.method == "sw" else n * a.iters
+            key = "%s:%d:%d:v%d" % (a.method, tpp, ppb, v)
+            res[key] = dict(ms=t, evals=evals, evals_per_s=evals / t * 1e3,
                             median_best=float(best.median()))
-            print("%s tpp=%d ppb=%d variant=%d: %.3f ms  %.1f M evals/s  median best %.3f"
-                  % (a.workload, tpp, ppb, v, t, n * a.iters / t / 1e3, float(best.median())),
+            print("%s %s tpp=%d ppb=%d variant=%d: %.3f ms  %.1f M evals/s  median best %.3f"
+                  % (a.workload, a.method, tpp, ppb, v, t, evals / t / 1e3, float(best.median())),
                   flush=True)
         ctx.close()
     print(json.dumps(res))
