@@ -161,6 +161,20 @@ def oracle_dock_sample(w, n_runs, gens, nthreads, seed):
     return int(ev.sum()), time.perf_counter() - t
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu), or the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def reference_arm(args, rank, world):
     """FP64 CPU oracle on the host cores, bounded sample per step."""
     if rank != 0:
@@ -327,6 +341,9 @@ def main():
                 torch.cuda.synchronize()
                 ms.append(a.elapsed_time(b))
             extra[name] = n * ITERS / (min(ms) / 1e3)
+    # measured FP32 FMA and special-function throughput (after the timed region)
+    from paper_2410_10447_gb300.reduce_bench import alu_peaks
+    probe = alu_peaks(ctx, torch)
 
     if rank != 0:
         if dist:
@@ -344,9 +361,13 @@ def main():
         oracle.build()
         cores = os.cpu_count() or 1
         ev_c, t_c = oracle_dock_sample(w, args.cpu_runs, 1, cores, 77)
+        ev_1, t_1 = oracle_dock_sample(w, 1, 1, 1, 78)
         cpu = {"value": ev_c / t_c, "unit": "evals/s", "cores": cores, "kind": "oracle",
                "sample": "FP64 oracle dock of %d runs x %d genotypes x 1 generation (%d "
-                         "evaluations), OpenMP over runs" % (args.cpu_runs, POP, ev_c)}
+                         "evaluations), OpenMP over runs" % (args.cpu_runs, POP, ev_c),
+               "single_thread": {"value": ev_1 / t_1, "sample": "1 run x %d genotypes x 1 "
+                                 "generation (%d evaluations), one thread" % (POP, ev_1)},
+               "cpu_model": cpu_model()}
     q = lambda v, p: float(np.percentile(v, p))
     line = {
         "metric": "energy+gradient evals/s", "value": value, "unit": "evals/s",
@@ -370,7 +391,8 @@ def main():
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "eval_kernel (local search, 3000 genotypes x 300 evaluations)",
                      "flops_per_eval": fl,
-                     "peak_basis": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 x 2070 MHz"},
+                     "peak_basis": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 x 2070 MHz",
+                     "peak_probe": dict(probe, frac_of_ffma_probe=achieved / probe["ffma_tflops"])},
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -35,7 +35,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
            "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev", "ga_converged_dev",
-           "local_search_sw_dev", "local_search_sw",
+           "local_search_sw_dev", "local_search_sw", "alu_bench_dev",
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget"]
@@ -194,6 +194,7 @@ def load(build: bool = False):
     L.ga_generation_dev.argtypes = [vp, C.c_int, C.POINTER(_DockParams), C.c_int, vp, vp, vp, vp,
                                     vp]
     L.ga_converged_dev.argtypes = [vp, C.POINTER(_DockParams), vp, vp, vp]
+    L.alu_bench_dev.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     _lib = L
     return L
 
@@ -389,6 +390,10 @@ class Context:
         self._chk(self.lib.ga_generation_dev(self.h, lid, C.byref(params), gen, _ptr(genes),
                                              _ptr(energy), _ptr(genes_out), _ptr(iters_out),
                                              _stream()))
+
+    def alu_bench_dev(self, kind, n_blocks, threads, reps, out):
+        """ALU throughput probe (kind 0 FFMA, 1 ex2.approx, 2 rsqrt.approx)."""
+        self._chk(self.lib.alu_bench_dev(self.h, kind, n_blocks, threads, reps, _ptr(out), _stream()))
 
     def ga_converged_dev(self, params, energy, converged):
         """Early-stopping test of params (conv_top, conv_tol) on energy

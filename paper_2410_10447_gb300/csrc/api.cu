@@ -1174,6 +1174,17 @@ int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "reduce4_bench");
 }
 
+int alu_bench_dev(adgb_ctx *c, int kind, int n_blocks, int threads, int reps, float *out_dev,
+                  adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (kind < 0 || kind > 2 || n_blocks < 1 || threads < 32 || threads > 256 || threads % 32 ||
+        reps < 1 || !out_dev)
+        return fail(c, ADGB_EINVAL, "alu_bench: bad arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_alu_bench(kind, n_blocks, threads, reps, out_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "alu_bench");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

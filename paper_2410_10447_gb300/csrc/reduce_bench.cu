@@ -339,6 +339,50 @@ static int tc_groups(int threads) {
     return W % 8 == 0 ? 8 : (W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 0));
 }
 
+// ---------------------------------------------------------------------------
+// ALU throughput probes for the roofline of the scoring kernels: chains of
+// dependent FP32 fused multiply-adds (8 independent chains a thread) or of
+// special-function-unit operations (ex2.approx or rsqrt.approx), long enough
+// that issue throughput, not latency, bounds them.  out[thread] keeps the
+// results alive.
+// ---------------------------------------------------------------------------
+template <int KIND>
+__global__ void __launch_bounds__(256) alu_kernel(float *out, int reps, float b, float c) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) a[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int r = 0; r < reps; r++) {
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if constexpr (KIND == 0) {
+                    a[k] = fmaf(a[k], b, c);
+                } else if constexpr (KIND == 1) {
+                    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(-a[k]));
+                } else {
+                    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k] + c));
+                }
+            }
+        }
+    }
+    float t = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) t += a[k];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = t;
+}
+
+cudaError_t launch_alu_bench(int kind, int n_blocks, int threads, int reps, float *out,
+                             cudaStream_t s) {
+    switch (kind) {
+        case 0: alu_kernel<0><<<n_blocks, threads, 0, s>>>(out, reps, 0.999f, 1e-3f); break;
+        case 1: alu_kernel<1><<<n_blocks, threads, 0, s>>>(out, reps, 0.f, 0.f); break;
+        case 2: alu_kernel<2><<<n_blocks, threads, 0, s>>>(out, reps, 0.f, 1.f); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int n_blocks,
                                  int reps, float *out, cudaStream_t s) {
     switch (variant) {
