@@ -130,9 +130,10 @@ def profile_traffic(kernel_sha):
         return None
     vals = {}
     for line in txt.splitlines():
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_sha1")):
-            k, v = line.split(":", 1)
-            vals[k.strip().strip("-* ")] = v.strip().strip("`")
+        item = line.strip().lstrip("-* ")
+        if ":" in item and item.startswith(("traffic_bytes_per_launch", "kernel_source_sha1")):
+            k, v = item.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha1") != kernel_sha:
         return None
     try:
