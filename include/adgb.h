@@ -275,6 +275,15 @@ typedef struct {
     int conv_every;
     int conv_top;
     float conv_tol;
+    /* Local search of the LGA: 0 = ADADELTA (rho, eps), 1 = Solis-Wets with the
+     * sw_* parameters below (see local_search_sw; each individual's search is
+     * keyed by genotype index run * pop + k and call = generation mod 65536,
+     * and spends at most ls_iters evaluations; a run counts the evaluations
+     * actually spent).  The serving loop runs ADADELTA only. */
+    int ls_method;
+    float sw_rho0, sw_rho_min;
+    int sw_max_succ, sw_max_fail;
+    float sw_angle_scale;
 } adgb_dock_params;
 
 /*

@@ -209,12 +209,16 @@ class DockParams(C.Structure):
                 ("rho", C.c_double), ("eps", C.c_double), ("p_cross", C.c_double),
                 ("p_mut", C.c_double), ("mut_trans", C.c_double), ("mut_angle", C.c_double),
                 ("seed", C.c_ulonglong), ("conv_every", C.c_int), ("conv_top", C.c_int),
-                ("conv_tol", C.c_double)]
+                ("conv_tol", C.c_double), ("ls_method", C.c_int), ("sw_rho0", C.c_double),
+                ("sw_rho_min", C.c_double), ("sw_max_succ", C.c_int), ("sw_max_fail", C.c_int),
+                ("sw_angle_scale", C.c_double)]
 
 
 DOCK_DEFAULTS = dict(n_runs=1, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
                      ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
-                     mut_angle=np.pi / 2, seed=2410, conv_every=0, conv_top=15, conv_tol=0.15)
+                     mut_angle=np.pi / 2, seed=2410, conv_every=0, conv_top=15, conv_tol=0.15,
+                     ls_method=0, sw_rho0=1.0, sw_rho_min=0.01, sw_max_succ=4, sw_max_fail=4,
+                     sw_angle_scale=1.0)
 
 
 def dock_params(**kw) -> DockParams:

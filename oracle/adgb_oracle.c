@@ -758,7 +758,14 @@ int orc_dock(const orc_receptor *R, const orc_ligand *L, const orc_dock_params *
             for (int k = 0; k < P; k++) {
                 double *gk = gb + (size_t)k * G;
                 int it = fl[k] ? p->ls_iters : 1;
-                bad |= orc_local_search(R, L, gk, it, p->rho, p->eps, 0, NULL, e + k) != 0;
+                if (p->ls_method == 1) {
+                    /* Solis-Wets: genotype r * P + k, call = generation mod 2^16 */
+                    orc_sw_params sw = {it, p->sw_max_succ, p->sw_max_fail, p->sw_rho0,
+                                        p->sw_rho_min, p->sw_angle_scale, p->seed, gen & 0xFFFF};
+                    bad |= orc_sw_search(R, L, gk, &sw, r * P + k, 0, NULL, e + k, &it) != 0;
+                } else {
+                    bad |= orc_local_search(R, L, gk, it, p->rho, p->eps, 0, NULL, e + k) != 0;
+                }
                 ev += it;
                 if (e[k] < be) { be = e[k]; memcpy(bg, gk, sizeof(double) * G); }
             }

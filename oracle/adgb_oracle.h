@@ -79,6 +79,10 @@ typedef struct {
     unsigned long long seed;
     int conv_every, conv_top;  /* early stopping: test every conv_every generations (0: off) */
     double conv_tol;
+    int ls_method;             /* 0 ADADELTA, 1 Solis-Wets (sw_* below) */
+    double sw_rho0, sw_rho_min;
+    int sw_max_succ, sw_max_fail;
+    double sw_angle_scale;
 } orc_dock_params;
 
 void orc_philox4x32_10(const unsigned int ctr[4], const unsigned int key[2], unsigned int out[4]);

@@ -77,13 +77,16 @@ class _DockParams(C.Structure):
                 ("rho", C.c_float), ("eps", C.c_float), ("p_cross", C.c_float),
                 ("p_mut", C.c_float), ("mut_trans", C.c_float), ("mut_angle", C.c_float),
                 ("seed", C.c_ulonglong), ("reduce_variant", C.c_int),
-                ("conv_every", C.c_int), ("conv_top", C.c_int), ("conv_tol", C.c_float)]
+                ("conv_every", C.c_int), ("conv_top", C.c_int), ("conv_tol", C.c_float),
+                ("ls_method", C.c_int), ("sw_rho0", C.c_float), ("sw_rho_min", C.c_float),
+                ("sw_max_succ", C.c_int), ("sw_max_fail", C.c_int), ("sw_angle_scale", C.c_float)]
 
 
 DOCK_DEFAULTS = dict(n_runs=20, pop=150, max_gens=27, max_evals=2500000, ls_iters=300,
                      ls_rate=1.0, rho=0.8, eps=1e-2, p_cross=0.8, p_mut=0.02, mut_trans=2.0,
                      mut_angle=float(np.pi / 2), seed=2410, reduce_variant=-1,
-                     conv_every=0, conv_top=15, conv_tol=0.15)
+                     conv_every=0, conv_top=15, conv_tol=0.15, ls_method=0, sw_rho0=1.0,
+                     sw_rho_min=0.01, sw_max_succ=4, sw_max_fail=4, sw_angle_scale=1.0)
 
 
 def dock_params(**kw) -> _DockParams:

@@ -77,6 +77,9 @@ struct DockCfg {
     uint64_t seed;
     int conv_every, conv_top;   // early stopping (conv_every = 0: off)
     float conv_tol;
+    int ls_method;              // 0 ADADELTA, 1 Solis-Wets
+    float sw_rho0, sw_rho_min, sw_angle_scale;
+    int sw_max_succ, sw_max_fail;
 };
 
 // Device working set of one dock call.
@@ -188,8 +191,12 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                         int iters, float rho, float eps, int resume, float *energy,
                         float *grad, float *state, cudaStream_t s,
                         const int *iters_per_pose = nullptr);
+// Solis-Wets searches; budget [n] (evaluations each genotype may spend) or
+// null for c.max_evals; evals [n] receives the evaluations spent (it may be
+// the budget array itself).
 cudaError_t launch_sw(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const SwCfg &c,
-                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s);
+                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s,
+                      const int *budget = nullptr);
 cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const DockCfg &d,
                         float *best_genes, double *best_energy, long long *evals_out,
                         DockScratch &w, cudaStream_t s);

@@ -619,6 +619,12 @@ int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg
         (p->conv_every > 0 && (p->conv_top < 2 || p->conv_top > p->pop || !(p->conv_tol > 0.f) ||
                                !finite(p->conv_tol))))
         return ferr(err, ADGB_EINVAL, "dock: bad early-stopping parameters");
+    if (p->ls_method < 0 || p->ls_method > 1 ||
+        (p->ls_method == 1 &&
+         (!(p->sw_rho0 > 0.f) || !finite(p->sw_rho0) || !(p->sw_rho_min >= 0.f) ||
+          !finite(p->sw_rho_min) || p->sw_max_succ < 1 || p->sw_max_fail < 1 ||
+          !(p->sw_angle_scale > 0.f) || !finite(p->sw_angle_scale))))
+        return ferr(err, ADGB_EINVAL, "dock: bad local-search method parameters");
     variant = p->reduce_variant < 0 ? default_variant : p->reduce_variant;
     if (variant < 0 || variant >= ADGB_REDUCE_N) return ferr(err, ADGB_EINVAL, "unknown reduce variant %d", variant);
     d.n_runs = p->n_runs;
@@ -637,6 +643,12 @@ int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg
     d.conv_every = p->conv_every;
     d.conv_top = p->conv_top;
     d.conv_tol = p->conv_tol;
+    d.ls_method = p->ls_method;
+    d.sw_rho0 = p->sw_rho0;
+    d.sw_rho_min = p->sw_rho_min;
+    d.sw_max_succ = p->sw_max_succ;
+    d.sw_max_fail = p->sw_max_fail;
+    d.sw_angle_scale = p->sw_angle_scale;
     return ADGB_OK;
 }
 

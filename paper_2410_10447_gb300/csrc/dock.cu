@@ -11,8 +11,9 @@
 //    the lower index), two-point crossover with probability p_cross, per-gene
 //    mutation with probability p_mut by a uniform offset in [-1, 1) times
 //    mut_trans (translation genes) or mut_angle; torsions wrapped;
-//  - each individual gets a local search of ls_iters evaluations with
-//    probability ls_rate, otherwise one scoring evaluation;
+//  - each individual gets a local search of ls_iters evaluations (ADADELTA,
+//    or a Solis-Wets search spending at most that many) with probability
+//    ls_rate, otherwise one scoring evaluation;
 //  - a run stops after max_gens generations or once its evaluation count
 //    reaches max_evals;
 //  - early stopping (optional): after every conv_every-th generation a run
@@ -463,9 +464,27 @@ cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     init_pop_kernel<<<(n + 127) / 128, 128, 0, s>>>(rec, lig.n_tors, d.seed, d.n_runs, d.pop,
                                                      w.genes[0], w.iters);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = launch_eval(rec, lig, cfg, MODE_LS, w.genes[0], w.genes[0], n, 1, d.rho, d.eps, 0,
-                         w.energy, nullptr, nullptr, s, w.iters)) != cudaSuccess)
-        return e;
+    // one local-search launch over every run's individuals (budgets in w.iters;
+    // the Solis-Wets search writes back the evaluations it spent)
+    auto local_search = [&](float *genes, int gen) -> cudaError_t {
+        if (d.ls_method == 1) {
+            SwCfg c;
+            c.max_evals = 0;
+            c.max_succ = d.sw_max_succ;
+            c.max_fail = d.sw_max_fail;
+            c.resume = 0;
+            c.rho0 = d.sw_rho0;
+            c.rho_min = d.sw_rho_min;
+            c.angle_scale = d.sw_angle_scale;
+            c.seed = d.seed;
+            c.call = (uint32_t)gen & 0xFFFFu;
+            c.pose_base = 0;
+            return launch_sw(rec, lig, cfg, c, genes, n, w.energy, w.iters, nullptr, s, w.iters);
+        }
+        return launch_eval(rec, lig, cfg, MODE_LS, genes, genes, n, 0, d.rho, d.eps, 0, w.energy,
+                           nullptr, nullptr, s, w.iters);
+    };
+    if ((e = local_search(w.genes[0], 0)) != cudaSuccess) return e;
     const int bt = 128;
     best_kernel<<<d.n_runs, bt, 0, s>>>(d.pop, G, w.genes[0], w.energy, w.iters, best_genes,
                                        w.best_e, w.evals, w.done, d.max_evals, 0, d.conv_every,
@@ -477,9 +496,7 @@ cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
         ga_kernel<<<d.n_runs, gt, gsm, s>>>(d.pop, G, w.genes[cur], w.energy, d, (uint32_t)gen,
                                            w.genes[cur ^ 1], w.iters, w.done);
         cur ^= 1;
-        if ((e = launch_eval(rec, lig, cfg, MODE_LS, w.genes[cur], w.genes[cur], n, 0, d.rho,
-                             d.eps, 0, w.energy, nullptr, nullptr, s, w.iters)) != cudaSuccess)
-            return e;
+        if ((e = local_search(w.genes[cur], gen)) != cudaSuccess) return e;
         best_kernel<<<d.n_runs, bt, 0, s>>>(d.pop, G, w.genes[cur], w.energy, w.iters,
                                            best_genes, w.best_e, w.evals, w.done, d.max_evals,
                                            gen, d.conv_every, d.conv_top, d.conv_tol);

@@ -704,6 +704,7 @@ struct SwArgs {
     float *energy;        // [n] out
     int *evals;           // [n] out or null
     float *state;         // [n][2G + 5] (x, bias, rho, successes, failures, E, step) or null
+    const int *budget;    // [n] evaluations each genotype may spend, or null (max_evals)
     int n, max_evals, max_succ, max_fail, resume;
     float rho0, rho_min, angle_scale;
     uint64_t seed;
@@ -808,6 +809,7 @@ __device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayo
 
     float *gio = a.genes + (size_t)pose * G;
     float *st = a.state ? a.state + (size_t)pose * (2 * G + 5) : nullptr;
+    const int max_evals = a.budget ? a.budget[pose] : a.max_evals;
     float x[NG], bias[NG], y[NG], d[NG];
     float rho, Ex;
     int ns, nf, step, evals = 0;
@@ -829,11 +831,11 @@ __device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayo
     } else {
         rho = a.rho0;
         ns = nf = step = 0;
-        Ex = a.max_evals > 0 ? energy(x) : INFINITY;
-        evals = a.max_evals > 0 ? 1 : 0;
+        Ex = max_evals > 0 ? energy(x) : INFINITY;
+        evals = max_evals > 0 ? 1 : 0;
     }
     const uint32_t id = (uint32_t)(a.pose_base + pose);
-    while (evals < a.max_evals && rho >= a.rho_min) {
+    while (evals < max_evals && rho >= a.rho_min) {
 #pragma unroll
         for (int r = 0; r < NG; r++) {
             const int j = gt + r * TPP;
@@ -856,7 +858,7 @@ __device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayo
                 x[r] = y[r];
                 bias[r] = 0.2f * bias[r] + 0.4f * d[r];
             }
-        } else if (evals < a.max_evals) {
+        } else if (evals < max_evals) {
 #pragma unroll
             for (int r = 0; r < NG; r++) {
                 const int j = gt + r * TPP;
@@ -908,6 +910,7 @@ __device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayo
             }
         }
     }
+    group_sync<TPP>(group);   // every lane has read the budget before it is overwritten
     if (gt == 0) {
         a.energy[pose] = Ex;
         if (a.evals) a.evals[pose] = evals;
@@ -1201,7 +1204,8 @@ static cudaError_t launch_sw_v(const SwArgs &a, int ppb, int variant, int smem, 
 }
 
 cudaError_t launch_sw(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const SwCfg &c,
-                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s) {
+                      float *genes, int n, float *energy, int *evals, float *state, cudaStream_t s,
+                      const int *budget) {
     if (n == 0) return cudaSuccess;
     SwArgs a;
     a.rec = rec;
@@ -1212,6 +1216,7 @@ cudaError_t launch_sw(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, 
     a.energy = energy;
     a.evals = evals;
     a.state = state;
+    a.budget = budget;
     a.n = n;
     a.max_evals = c.max_evals;
     a.max_succ = c.max_succ;

@@ -469,6 +469,10 @@ int dock_submit(adgb_server *s, int receptor_id, const adgb_ligand_desc *lig,
     std::string err;
     int variant = 0;
     int rc = dock_cfg_from_params(p, s->cfg.variant, j->d, variant, &err);
+    if (rc == ADGB_OK && j->d.ls_method != 0) {
+        rc = ADGB_EINVAL;
+        err = "dock_submit: the serving loop runs the ADADELTA local search only";
+    }
     if (rc == ADGB_OK) rc = make_ligand_blob(&err, lig, j->blob);
     int n_type_maps = 0;
     if (rc == ADGB_OK && ctx_receptor(s->ctx, receptor_id, &j->rec, &n_type_maps) != ADGB_OK) {

@@ -47,7 +47,10 @@ def oracle_params(gp):
                               p_cross=f32(gp.p_cross), p_mut=f32(gp.p_mut),
                               mut_trans=f32(gp.mut_trans), mut_angle=f32(gp.mut_angle),
                               seed=gp.seed, conv_every=gp.conv_every, conv_top=gp.conv_top,
-                              conv_tol=f32(gp.conv_tol))
+                              conv_tol=f32(gp.conv_tol), ls_method=gp.ls_method,
+                              sw_rho0=f32(gp.sw_rho0), sw_rho_min=f32(gp.sw_rho_min),
+                              sw_max_succ=gp.sw_max_succ, sw_max_fail=gp.sw_max_fail,
+                              sw_angle_scale=f32(gp.sw_angle_scale))
 
 
 def ang(a, b):
@@ -237,4 +240,40 @@ def test_dock_early_stopping(pkg, torch, w):
         ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=2, conv_top=1, **base))
     with pytest.raises(pkg.AdgbError):
         ctx.dock(rid, lid, pkg.adgb.dock_params(conv_every=2, conv_top=6, conv_tol=0.0, **base))
+    ctx.close()
+
+
+# ------------------------------------------------- Solis-Wets inside the LGA
+def test_dock_with_solis_wets(pkg, torch, w):
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    runs, pop, gens, it = 4, 20, 4, 40
+    gp = pkg.adgb.dock_params(n_runs=runs, pop=pop, max_gens=gens, ls_iters=it, ls_rate=1.0, seed=13,
+                              ls_method=1, sw_angle_scale=0.5, sw_rho_min=0.3)
+    bg, be, ev = ctx.dock(rid, lid, gp)
+    # evaluations actually spent: a search stops before its budget once rho < rho_min
+    assert np.all(ev >= pop + gens * pop) and np.all(ev <= pop + gens * pop * it)
+    assert np.any(ev < pop + gens * pop * it)
+    bg2, be2, ev2 = ctx.dock(rid, lid, gp)
+    assert np.array_equal(bg, bg2) and np.array_equal(be, be2) and np.array_equal(ev, ev2)
+    R, L = oracle.Receptor(w["receptor"]), oracle.Ligand(w["ligand"])
+    T = w["ligand"]["n_tors"]
+    for r in range(runs):
+        assert abs(be[r] - oracle.score(R, L, bg[r])[0]) <= 1e-9 * max(abs(be[r]), 1.0)
+        init = min(oracle.score(R, L, oracle.init_individual(w["receptor"], T, 13, r, k))[0]
+                   for k in range(pop))
+        assert be[r] <= init + 1e-3 * max(abs(init), 1.0)
+    # the oracle's LGA with the same Solis-Wets searches: same distribution of results
+    gp8 = pkg.adgb.dock_params(n_runs=8, pop=16, max_gens=3, ls_iters=40, ls_rate=1.0, seed=21,
+                               ls_method=1, sw_angle_scale=0.5, sw_rho_min=0.3)
+    _, be_g, ev_g = ctx.dock(rid, lid, gp8)
+    _, be_o, ev_o = oracle.dock(w["receptor"], w["ligand"], oracle_params(gp8))
+    assert abs(np.median(be_g) - np.median(be_o)) <= 0.15 * abs(np.median(be_o)) + 1.0, (be_g, be_o)
+    assert abs(np.mean(ev_g) - np.mean(ev_o)) <= 0.25 * np.mean(ev_o)
+    # the serving loop runs ADADELTA only
+    srv = pkg.Server(ctx)
+    with pytest.raises(pkg.AdgbError):
+        srv.submit(rid, w["ligand"], gp)
+    srv.stop()
     ctx.close()

@@ -145,3 +145,18 @@ def test_dock_early_stopping_accounting(oracle_mod, w):
     b1, e1, ev1 = oracle_mod.dock(rec, lig, oracle_mod.dock_params(conv_every=2, conv_top=4,
                                                                      conv_tol=1e-12, **base))
     assert np.array_equal(ev0, ev1) and np.array_equal(e0, e1) and np.array_equal(b0, b1)
+
+
+def test_dock_with_solis_wets_accounting(oracle_mod, w):
+    """The oracle's LGA with Solis-Wets searches counts the evaluations they
+    spend (at most ls_iters each) and keeps the best energy it saw."""
+    rec, lig = w["receptor"], w["ligand"]
+    prm = oracle_mod.dock_params(n_runs=3, pop=10, max_gens=3, ls_iters=30, ls_rate=1.0, seed=8,
+                                 ls_method=1)
+    bg, be, ev = oracle_mod.dock(rec, lig, prm)
+    assert np.all(ev >= 10 + 3 * 10) and np.all(ev <= 10 + 3 * 10 * 30)
+    R, L = oracle_mod.Receptor(rec), oracle_mod.Ligand(lig)
+    for r in range(3):
+        assert oracle_mod.score(R, L, bg[r])[0] == pytest.approx(be[r], rel=1e-12, abs=1e-12)
+    bg2, be2, ev2 = oracle_mod.dock(rec, lig, prm)
+    assert np.array_equal(be, be2) and np.array_equal(ev, ev2)
