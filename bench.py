@@ -68,6 +68,22 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(dist, t, device):
+    """The slowest rank's time, on every rank (t itself without a process group)."""
+    if not dist:
+        return t
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(world, units_per_rank, t_max):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, timed by the slowest rank."""
+    return world * units_per_rank / t_max
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled during the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -284,12 +300,9 @@ def main():
     t_dev = sum(dev_ms) / 1e3
     assert int(evals.sum()) == EVALS_PER_DOCK, int(evals.sum())
     assert torch.isfinite(best_e).all()
-    if dist:
-        tt = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(dist, t_dev, "cuda")
     evals_rank = args.steps * EVALS_PER_DOCK
-    value = world * evals_rank / t_dev
+    value = job_rate(world, evals_rank, t_dev)
 
     # end to end through the host C calls of one docking job per step
     lig_bytes = sum(np.asarray(lig[k]).nbytes for k in ("type", "charge", "xyz", "tors_bond",
@@ -308,11 +321,8 @@ def main():
         ctx.release_ligand(l2)
         e2e_ms.append(1e3 * (time.perf_counter() - t1))
     t_e2e = sum(e2e_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e = world * evals_rank / t_e2e
+    t_e2e = max_over_ranks(dist, t_e2e, "cuda")
+    e2e = job_rate(world, evals_rank, t_e2e)
 
     # the local-search kernel alone, same launch shape as inside dock()
     g0 = torch.from_numpy(synth.make_poses(7, n, w["receptor"], lig["n_tors"])).cuda()
