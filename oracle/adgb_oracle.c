@@ -26,7 +26,16 @@
  *    max(r, 0.5 A), below which their gradient is zero;
  *  - ADADELTA (Zeiler 2012) moves against the gradient; the best (lowest)
  *    energy seen and its genotype are kept, ties keep the earlier one;
- *    torsion genes are wrapped to [-pi, pi) after each update.
+ *    torsion genes are wrapped to [-pi, pi) after each update;
+ *  - the Lamarckian GA rules, the Solis-Wets search and the early-stopping
+ *    test are this project's readings, written out where they are defined
+ *    below.
+ *
+ * Parity unpinned: the Philox4x32-10 stream (no published known-answer
+ * vectors are available here; pinned by statistics only) and therefore the
+ * exact GA decisions and Solis-Wets deviates built on it; the GA rules and
+ * the Solis-Wets constants have no printed values in the paper to compare
+ * with.
  */
 #include "adgb_oracle.h"
 
