@@ -277,3 +277,30 @@ def test_dock_with_solis_wets(pkg, torch, w):
         srv.submit(rid, w["ligand"], gp)
     srv.stop()
     ctx.close()
+
+
+def test_dock_edge_sizes(pkg, torch, w):
+    """Largest population (1024), no generations, one-individual-budget runs."""
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(w["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+    R, L = oracle.Receptor(w["receptor"]), oracle.Ligand(w["ligand"])
+    T = w["ligand"]["n_tors"]
+    # pop 1024, one generation of 2-evaluation searches
+    bg, be, ev = ctx.dock(rid, lid, pkg.adgb.dock_params(n_runs=2, pop=1024, max_gens=1, ls_iters=2,
+                                                         ls_rate=1.0, seed=3))
+    assert np.all(ev == 1024 + 1024 * 2)
+    for r in range(2):
+        assert abs(be[r] - oracle.score(R, L, bg[r])[0]) <= 1e-9 * max(abs(be[r]), 1.0)
+    # no generation: the best of the initial population, each scored once
+    bg, be, ev = ctx.dock(rid, lid, pkg.adgb.dock_params(n_runs=3, pop=8, max_gens=0, seed=4))
+    assert np.all(ev == 8)
+    for r in range(3):
+        init = [oracle.score(R, L, oracle.init_individual(w["receptor"], T, 4, r, k))[0]
+                for k in range(8)]
+        assert abs(be[r] - min(init)) <= max(1e-4 * abs(min(init)), 1e-3)
+    # bad population sizes are refused
+    for pop in (1, 1025):
+        with pytest.raises(pkg.AdgbError):
+            ctx.dock(rid, lid, pkg.adgb.dock_params(n_runs=1, pop=pop, max_gens=1, seed=1))
+    ctx.close()
