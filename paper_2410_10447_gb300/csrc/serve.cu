@@ -107,6 +107,10 @@ struct adgb_server {
     bool stop = false;
     long long next_id = 1;
     cudaStream_t stream = nullptr;
+    // the size classes' local-search launches run concurrently, one stream
+    // each, between two events of the main stream (tables ready / all done)
+    cudaStream_t cls_stream[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_tables = nullptr, ev_cls[3] = {nullptr, nullptr, nullptr};
     std::chrono::steady_clock::time_point t0;
     std::string err;
     // per-tick tables (pinned staging, device copies)
@@ -114,7 +118,7 @@ struct adgb_server {
     LigDev *h_ligs = nullptr, *d_ligs = nullptr;
     RecDev *h_recs = nullptr, *d_recs = nullptr;
     int cap_items = 0, cap_jobs = 0;
-    int *d_counter = nullptr;
+    int *d_counter = nullptr;        // 2 ints per size class (work counter, finished blocks)
     long long ticks = 0, items_run = 0;
     double busy_s = 0;
 };
@@ -248,12 +252,20 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->d_recs, s->h_recs, sizeof(RecDev) * act.size(), cudaMemcpyHostToDevice, s->stream);
     if (e != cudaSuccess) return e;
+    // one persistent launch per size class, concurrently: a class with few
+    // items no longer leaves the GPU idle while it drains
+    e = cudaEventRecord(s->ev_tables, s->stream);
+    if (e != cudaSuccess) return e;
     for (int c = 0; c < 3; c++) {
         if (!count[c]) continue;
         const int grid = items_grid(ccfg[c], budget[c], s->device);
         if (grid < 1) return cudaErrorInvalidConfiguration;
-        e = launch_eval_items(s->d_items + first[c], count[c], s->d_ligs, s->d_recs, s->d_counter,
-                              ccfg[c], budget[c], grid, s->stream);
+        e = cudaStreamWaitEvent(s->cls_stream[c], s->ev_tables, 0);
+        if (e == cudaSuccess)
+            e = launch_eval_items(s->d_items + first[c], count[c], s->d_ligs, s->d_recs,
+                                  s->d_counter + 2 * c, ccfg[c], budget[c], grid, s->cls_stream[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev_cls[c], s->cls_stream[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_cls[c], 0);
         if (e != cudaSuccess) return e;
     }
     s->items_run += n_items;
@@ -388,6 +400,21 @@ void fill_info(const adgb_server *s, const Job *j, adgb_job_info *info) {
 
 extern "C" {
 
+static void release_streams(adgb_server *s) {
+    for (int c = 0; c < 3; c++) {
+        if (s->cls_stream[c]) cudaStreamDestroy(s->cls_stream[c]);
+        if (s->ev_cls[c]) cudaEventDestroy(s->ev_cls[c]);
+        s->cls_stream[c] = nullptr;
+        s->ev_cls[c] = nullptr;
+    }
+    if (s->ev_tables) cudaEventDestroy(s->ev_tables);
+    if (s->d_counter) cudaFree(s->d_counter);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    s->ev_tables = nullptr;
+    s->d_counter = nullptr;
+    s->stream = nullptr;
+}
+
 int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out) {
     if (!ctx || !out) return ADGB_EINVAL;
     *out = nullptr;
@@ -416,14 +443,20 @@ int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->d_counter, 0, 2 * sizeof(int));
-    if (prev >= 0) cudaSetDevice(prev);
+    for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+        e = cudaStreamCreateWithFlags(&s->cls_stream[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_cls[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_tables, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 6 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_counter, 0, 6 * sizeof(int));
     if (e != cudaSuccess) {
-        if (s->stream) cudaStreamDestroy(s->stream);
+        release_streams(s);
+        if (prev >= 0) cudaSetDevice(prev);
         delete s;
         return ADGB_EDEVICE;
     }
+    if (prev >= 0) cudaSetDevice(prev);
     s->budget = s->opts.mem_budget_bytes > 0 ? (size_t)s->opts.mem_budget_bytes : free_b / 4;
     s->t0 = std::chrono::steady_clock::now();
     s->th = std::thread(server_loop, s);
@@ -451,8 +484,7 @@ int serve_stop(adgb_server *s) {
     cudaFree(s->d_items);
     cudaFree(s->d_ligs);
     cudaFree(s->d_recs);
-    cudaFree(s->d_counter);
-    cudaStreamDestroy(s->stream);
+    release_streams(s);
     if (prev >= 0) cudaSetDevice(prev);
     s->cv_done.notify_all();
     delete s;
