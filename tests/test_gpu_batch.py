@@ -101,3 +101,41 @@ def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune, varian
         r += n_poses[i]
     ctx.batch_release(bid)
     ctx.close()
+
+
+def test_uneven_512_full_size_sampled(pkg, torch):
+    """The uneven workload at its full size in the launch configuration
+    run_batch times (512 ligands of 10-128 atoms x 64 genotypes x 300
+    evaluations, one autotuned, graph-replayed persistent launch): sampled
+    genotypes' returned energies equal the FP64 oracle's energy of the
+    returned genotypes, and are no higher than their start energies."""
+    w = synth.WORKLOADS["uneven_512"]
+    rec = synth.make_receptor(synth.generate.BASE_SEED + w["index"], w["grid"], w["n_type_maps"])
+    ligs = synth.make_uneven_batch(synth.generate.BASE_SEED + w["index"], 512, w["atoms"], w["tors"],
+                                   w["n_types"])
+    poses = 64
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(rec)
+    lids = [ctx.upload_ligand_torsion_tree(L) for L in ligs]
+    genes = [synth.make_poses(7000 + i, poses, rec, L["n_tors"]) for i, L in enumerate(ligs)]
+    g0 = torch.from_numpy(pack(genes)).cuda()
+    bid = ctx.batch_create([rid] * len(ligs), lids, [poses] * len(ligs))
+    ctx.batch_autotune(bid, g0, iters=15)
+    g = g0.clone()
+    e = torch.empty(g0.shape[0], device="cuda")
+    ctx.batch_local_search_dev(bid, g, e, 300)
+    be, gb = e.cpu().numpy(), g.cpu().numpy()
+    assert np.all(np.isfinite(be))
+    rng = np.random.default_rng(0)
+    R = oracle.Receptor(rec)
+    for i in sorted(rng.choice(len(ligs), 12, replace=False)):
+        L = oracle.Ligand(ligs[i])
+        G = 6 + ligs[i]["n_tors"]
+        for k in rng.choice(poses, 2, replace=False):
+            row = i * poses + k
+            e_ref = oracle.score(R, L, gb[row, :G])[0]
+            assert abs(be[row] - e_ref) <= max(1e-4 * abs(e_ref), 1e-3), (i, k, be[row], e_ref)
+            e0 = oracle.score(R, L, genes[i][k])[0]
+            assert be[row] <= e0 + max(1e-4 * abs(e0), 1e-3)
+    ctx.batch_release(bid)
+    ctx.close()
