@@ -36,6 +36,7 @@ using namespace adgb;
 namespace {
 
 enum { JOB_QUEUED = 1, JOB_RUNNING = 2, JOB_DONE = 0 };
+constexpr int NCLS = 2;   // ligand-size classes of the local-search launches
 
 struct Job {
     long long id = 0;
@@ -109,8 +110,8 @@ struct adgb_server {
     cudaStream_t stream = nullptr;
     // the size classes' local-search launches run concurrently, one stream
     // each, between two events of the main stream (tables ready / all done)
-    cudaStream_t cls_stream[3] = {nullptr, nullptr, nullptr};
-    cudaEvent_t ev_tables = nullptr, ev_cls[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t cls_stream[NCLS] = {nullptr, nullptr};
+    cudaEvent_t ev_tables = nullptr, ev_cls[NCLS] = {nullptr, nullptr};
     std::chrono::steady_clock::time_point t0;
     std::string err;
     // per-tick tables (pinned staging, device copies)
@@ -188,22 +189,22 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
         }
     }
     // multi-ligand local-search launches over every active individual: one
-    // per size class (one warp a genotype up to 32 atoms, 64 threads up to
-    // 96, 128 above), each a persistent launch over that class's work items
-    // (a job's class depends on its ligand alone)
+    // per size class (one warp a genotype up to 32 atoms, 128 threads above),
+    // each a persistent launch over that class's work items (a job's class
+    // depends on its ligand alone)
     std::vector<int> cls(act.size());
-    EvalCfg ccfg[3];
-    for (int c = 0; c < 3; c++) {
+    EvalCfg ccfg[NCLS];
+    for (int c = 0; c < NCLS; c++) {
         ccfg[c] = s->cfg;
         if (!s->forced_shape) {
-            ccfg[c].tpp = c == 0 ? 32 : (c == 1 ? 64 : 128);
+            ccfg[c].tpp = c == 0 ? 32 : 128;
             ccfg[c].ppb = 128 / ccfg[c].tpp;
         }
     }
     int n_items = 0;
     for (size_t u = 0; u < act.size(); u++) {
         const int N = act[u]->lig.n_atoms;
-        cls[u] = s->forced_shape ? 0 : (N <= 32 ? 0 : (N <= 96 ? 1 : 2));
+        cls[u] = s->forced_shape ? 0 : (N <= 32 ? 0 : 1);
         n_items += (act[u]->d.n_runs * act[u]->d.pop + ccfg[cls[u]].ppb - 1) / ccfg[cls[u]].ppb;
     }
     e = grow_tables(s, n_items, (int)act.size());
@@ -212,8 +213,8 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
         s->h_ligs[u] = act[u]->lig;
         s->h_recs[u] = act[u]->rec;
     }
-    int k = 0, first[3], count[3], budget[3];
-    for (int c = 0; c < 3; c++) {
+    int k = 0, first[NCLS], count[NCLS], budget[NCLS];
+    for (int c = 0; c < NCLS; c++) {
         first[c] = k;
         budget[c] = 1024;
         const EvalCfg &cf = ccfg[c];
@@ -256,7 +257,7 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     // items no longer leaves the GPU idle while it drains
     e = cudaEventRecord(s->ev_tables, s->stream);
     if (e != cudaSuccess) return e;
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < NCLS; c++) {
         if (!count[c]) continue;
         const int grid = items_grid(ccfg[c], budget[c], s->device);
         if (grid < 1) return cudaErrorInvalidConfiguration;
@@ -401,7 +402,7 @@ void fill_info(const adgb_server *s, const Job *j, adgb_job_info *info) {
 extern "C" {
 
 static void release_streams(adgb_server *s) {
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < NCLS; c++) {
         if (s->cls_stream[c]) cudaStreamDestroy(s->cls_stream[c]);
         if (s->ev_cls[c]) cudaEventDestroy(s->ev_cls[c]);
         s->cls_stream[c] = nullptr;
@@ -443,13 +444,13 @@ int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out
     size_t free_b = 0, total_b = 0;
     cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    for (int c = 0; c < 3 && e == cudaSuccess; c++) {
+    for (int c = 0; c < NCLS && e == cudaSuccess; c++) {
         e = cudaStreamCreateWithFlags(&s->cls_stream[c], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_cls[c], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_tables, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 6 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->d_counter, 0, 6 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * NCLS * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_counter, 0, 2 * NCLS * sizeof(int));
     if (e != cudaSuccess) {
         release_streams(s);
         if (prev >= 0) cudaSetDevice(prev);
