@@ -383,3 +383,17 @@ def test_reduce4_tcgen05_rejects_odd_warp_counts(pkg, torch):
     with pytest.raises(pkg.AdgbError):
         ctx.reduce4_bench_dev(pkg.REDUCE4_TCGEN05_TF32X2, x, 96, reps=1)
     ctx.close()
+
+
+def test_alu_probe(pkg, torch):
+    """The ALU throughput probe runs its chains to finite values and refuses
+    bad shapes (it measures the roofline's denominator)."""
+    ctx = make_ctx(pkg)
+    out = torch.empty(4 * 64, device="cuda")
+    for kind in (0, 1, 2):
+        ctx.alu_bench_dev(kind, 4, 64, 3, out)
+        assert torch.isfinite(out).all()
+    for bad in ((3, 4, 64, 3), (0, 4, 48, 3), (0, 0, 64, 3), (0, 4, 512, 3)):
+        with pytest.raises(pkg.AdgbError):
+            ctx.alu_bench_dev(*bad, out)
+    ctx.close()
