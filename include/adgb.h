@@ -482,13 +482,18 @@ int dock_forget(adgb_server *server, long long job_id);
  *   ADGB_REDUCE4_TCGEN05_TF32X2 - one block-wide tcgen05.mma chain on the
  *     fifth-generation tensor cores (split TF32 operands, FP32 accumulation
  *     in tensor memory); needs threads to be a multiple of 64.  Should the
- *     wait for the tensor core ever give up, the block's outputs are NaN.
+ *     wait for the tensor core ever give up, the block's outputs are NaN;
+ *   ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST - the same kernel with nothing issued
+ *     to the tensor core, so that every completion wait gives up after a
+ *     short bounded wait: the outputs are NaN, the tensor memory is released
+ *     and the context stays usable (a test of the failure path).
  * threads: 32..1024, a multiple of 32; reps >= 1.
  * Errors: EINVAL, EDEVICE.
  */
 #define ADGB_REDUCE4_PAPER_FS 100
 #define ADGB_REDUCE4_PAPER_HALF 101
 #define ADGB_REDUCE4_TCGEN05_TF32X2 102
+#define ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST 103
 int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
                       int threads, int n_blocks, int reps, float *out_dev,
                       adgb_stream stream);

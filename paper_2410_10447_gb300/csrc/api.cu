@@ -1176,11 +1176,13 @@ int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads
     if (!c) return ADGB_EINVAL;
     const bool known = variant == ADGB_REDUCE_SHFL || variant == ADGB_REDUCE_MMA_TF32X2 ||
                        variant == ADGB_REDUCE_MMA_BF16X3 || variant == ADGB_REDUCE4_PAPER_FS ||
-                       variant == ADGB_REDUCE4_PAPER_HALF || variant == ADGB_REDUCE4_TCGEN05_TF32X2;
+                       variant == ADGB_REDUCE4_PAPER_HALF || variant == ADGB_REDUCE4_TCGEN05_TF32X2 ||
+                       variant == ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST;
     if (!known) return fail(c, ADGB_EINVAL, "reduce4_bench: unknown variant %d", variant);
     if (threads < 32 || threads > 1024 || threads % 32 || n_blocks < 1 || reps < 1 || !in_dev || !out_dev)
         return fail(c, ADGB_EINVAL, "reduce4_bench: bad arguments");
-    if (variant == ADGB_REDUCE4_TCGEN05_TF32X2 && threads % 64)
+    if ((variant == ADGB_REDUCE4_TCGEN05_TF32X2 || variant == ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST) &&
+        threads % 64)
         return fail(c, ADGB_EINVAL, "reduce4_bench: the tcgen05 form needs a multiple of 64 threads");
     DeviceGuard g(c->device);
     cudaError_t e = launch_reduce4_bench(variant, in_dev, threads, n_blocks, reps, out_dev,

@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(1024) reduce4_half_kernel(const float4 *in, fl
 // NaN; the TMEM is still released.
 // ---------------------------------------------------------------------------
 constexpr int TC_WAIT_LIMIT = 1 << 16;   // probes, each suspending up to a time limit
+constexpr int TC_SELFTEST_LIMIT = 64;     // the wait self-test gives up after 64 probes
 
 template <int NG>
 struct TcShape {
@@ -195,9 +196,12 @@ struct TcShape {
 
 __host__ __device__ constexpr int tc_smem_bytes(int threads) { return 16 + 1024 + 32 * threads; }
 
+// wait_limit: mbarrier probes before a wait gives up; no_mma (the wait
+// self-test): nothing is issued or committed, so every wait gives up.
 template <int NG>
 __global__ void __launch_bounds__(1024) reduce4_tc05_kernel(const float4 *in, float4 *out,
-                                                            int reps, float tiny) {
+                                                            int reps, float tiny, int wait_limit,
+                                                            int no_mma) {
     constexpr int N = TcShape<NG>::N, NCOLS = TcShape<NG>::NCOLS;
     extern __shared__ __align__(16) unsigned char tsm[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(tsm);
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(1024) reduce4_tc05_kernel(const float4 *in, fl
         tc05::fence_proxy_async_smem();
         tc05::fence_before();
         if (__syncthreads_or(bad)) break;
-        if (tid == 0) {
+        if (tid == 0 && !no_mma) {
             tc05::fence_after();
             for (int s = 0; s < n_mma; s++) {
                 const uint32_t bs = b_s + (uint32_t)((s >> 2) * NG * 1024 + (s & 3) * 32);
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(1024) reduce4_tc05_kernel(const float4 *in, fl
             }
             tc05::commit(mbar);
         }
-        if (!__all_sync(0xffffffffu, tc05::mbar_wait(mbar, r & 1, TC_WAIT_LIMIT))) {
+        if (!__all_sync(0xffffffffu, tc05::mbar_wait(mbar, r & 1, wait_limit))) {
             bad = true;
             continue;
         }
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(1024) reduce4_tc05_kernel(const float4 *in, fl
         x.w = x0.w + tot.w * tiny;
     }
     if (bad) {   // let the MMAs in flight finish (bounded) before TMEM is released
-        (void)tc05::mbar_wait(mbar, (r - 1) & 1, TC_WAIT_LIMIT);   // phase r - 1 gave up
+        (void)tc05::mbar_wait(mbar, (r - 1) & 1, wait_limit);   // phase r - 1 gave up
         tot = make_float4(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000),
                           __int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
     }
@@ -312,7 +316,7 @@ static cudaError_t launch_half(const float *in, int threads, int n_blocks, int r
 // wait for a resident CTA to finish).
 template <int NG>
 static cudaError_t launch_tc(const float *in, int threads, int n_blocks, int reps, float *out,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool self_test) {
     int dev = 0, sm_smem = 0, reserved = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
@@ -328,7 +332,9 @@ static cudaError_t launch_tc(const float *in, int threads, int n_blocks, int rep
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     k<<<n_blocks, threads, smem, s>>>(reinterpret_cast<const float4 *>(in),
-                                      reinterpret_cast<float4 *>(out), reps, 0.f);
+                                      reinterpret_cast<float4 *>(out), reps, 0.f,
+                                      self_test ? TC_SELFTEST_LIMIT : TC_WAIT_LIMIT,
+                                      self_test ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -397,12 +403,15 @@ cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int 
         case ADGB_REDUCE4_PAPER_HALF:
             return launch_half(in, threads, n_blocks, reps, out, s);
         case ADGB_REDUCE4_TCGEN05_TF32X2:
+        case ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST: {
+            const bool st = variant == ADGB_REDUCE4_TCGEN05_WAIT_SELFTEST;
             switch (tc_groups(threads)) {
-                case 8: return launch_tc<8>(in, threads, n_blocks, reps, out, s);
-                case 4: return launch_tc<4>(in, threads, n_blocks, reps, out, s);
-                case 2: return launch_tc<2>(in, threads, n_blocks, reps, out, s);
+                case 8: return launch_tc<8>(in, threads, n_blocks, reps, out, s, st);
+                case 4: return launch_tc<4>(in, threads, n_blocks, reps, out, s, st);
+                case 2: return launch_tc<2>(in, threads, n_blocks, reps, out, s, st);
             }
             return cudaErrorInvalidValue;
+        }
     }
     return cudaErrorInvalidValue;
 }

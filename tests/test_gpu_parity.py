@@ -397,3 +397,17 @@ def test_alu_probe(pkg, torch):
         with pytest.raises(pkg.AdgbError):
             ctx.alu_bench_dev(*bad, out)
     ctx.close()
+
+
+def test_tcgen05_wait_gives_up_cleanly(pkg, torch):
+    """Failure path of the bounded tensor-core completion wait: with nothing
+    committed every wait gives up (after a short bounded wait), the outputs
+    are NaN, the tensor memory is released and the context keeps working."""
+    ctx = make_ctx(pkg)
+    x = torch.ones(8 * 256 * 4, device="cuda")
+    out = ctx.reduce4_bench_dev(103, x, 256, reps=2)
+    torch.cuda.synchronize()
+    assert torch.isnan(out).all()
+    ok = ctx.reduce4_bench_dev(pkg.REDUCE4_TCGEN05_TF32X2, x, 256, reps=2)
+    assert torch.all(ok == 256.0)
+    ctx.close()
