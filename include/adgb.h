@@ -17,7 +17,8 @@
  *    referenced by integer ids, released explicitly or by adgb_destroy.
  *  - A context is bound to one device.  Calls on one context must not run
  *    concurrently from several host threads (thread-compatible); the
- *    library keeps no global state.
+ *    library's only global state is the fixed device array of
+ *    dock_noalloc_dev and its per-device address cache (mutex-guarded).
  *  - adgb_stream is the CUDA runtime's cudaStream_t (NULL = legacy default
  *    stream); it is declared here without the CUDA headers.
  *
