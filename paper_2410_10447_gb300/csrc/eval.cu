@@ -348,7 +348,9 @@ __device__ __forceinline__ StagedLig stage_ligand(unsigned char *sm, const SmemL
 }
 
 // Whole evaluation loop of one genotype by one pose group (TPP threads).
-template <int TPP, int VAR>
+// NGS: genes each lane holds (ceil(G / TPP) at most); the default covers
+// the largest genotype.
+template <int TPP, int VAR, int NGS = (MAX_GENES + TPP - 1) / TPP>
 __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout &L,
                                             const LigDev &lig, const RecDev &rec,
                                             const StagedLig &sl, const int group, const int gt,
@@ -375,7 +377,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
     float4 *fbuf = reinterpret_cast<float4 *>(P + L.p_force);
     constexpr int MAXA = ADGB_MAX_ATOMS / TPP;  // atoms owned per thread, at most
 
-    constexpr int NG = (MAX_GENES + TPP - 1) / TPP;
+    constexpr int NG = NGS;
     float om[NG], eg2[NG], ed2[NG], best[NG];
 #pragma unroll
     for (int r = 0; r < NG; r++) {
@@ -938,7 +940,7 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) sw_kernel(const SwArgs a
     tc_end<VAR>(tw);
 }
 
-template <int TPP, int VAR>
+template <int TPP, int VAR, int NGS>
 __device__ __forceinline__ void eval_one(const EvalArgs &a, const StagedLig &sl, unsigned char *sm,
                                          int group, int gt, int pose, Tc05Warp &tw) {
     const int G = 6 + a.lig.n_tors;
@@ -953,10 +955,10 @@ __device__ __forceinline__ void eval_one(const EvalArgs &a, const StagedLig &sl,
     io.resume = a.resume;
     io.rho = a.rho;
     io.eps = a.eps;
-    search_pose<TPP, VAR>(sm, a.L, a.lig, a.rec, sl, group, gt, io, tw);
+    search_pose<TPP, VAR, NGS>(sm, a.L, a.lig, a.rec, sl, group, gt, io, tw);
 }
 
-template <int TPP, int VAR>
+template <int TPP, int VAR, int NGS>
 __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + tc_front<VAR>();
@@ -966,7 +968,7 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_kernel(const EvalAr
     __syncthreads();
     const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
     const int pose = blockIdx.x * (blockDim.x / TPP) + group;
-    if (pose < a.n) eval_one<TPP, VAR>(a, sl, sm, group, gt, pose, tw);
+    if (pose < a.n) eval_one<TPP, VAR, NGS>(a, sl, sm, group, gt, pose, tw);
     tc_end<VAR>(tw);
 }
 
@@ -987,6 +989,7 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + items_front<VAR>();
     int &s_item = *reinterpret_cast<int *>(sm - 16);
+    constexpr int NG_MAX = (MAX_GENES + TPP - 1) / TPP;
     const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
     int cur_lig = -1;
     SmemLayout L;
@@ -1019,7 +1022,13 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
             io.resume = 0;
             io.rho = w.rho;
             io.eps = w.eps;
-            search_pose<TPP, VAR>(sm, L, a.ligs[w.lig], a.recs[w.rec], sl, group, gt, io, tw);
+            // same specialisation as the single-ligand launch, so that both
+            // give bit-identical searches
+            const LigDev &lg = a.ligs[w.lig];
+            if (NG_MAX > 1 && 6 + lg.n_tors <= TPP)
+                search_pose<TPP, VAR, 1>(sm, L, lg, a.recs[w.rec], sl, group, gt, io, tw);
+            else
+                search_pose<TPP, VAR, NG_MAX>(sm, L, lg, a.recs[w.rec], sl, group, gt, io, tw);
         }
         __syncthreads();  // the item is done before smem or s_item change
     }
@@ -1125,9 +1134,13 @@ int items_grid(const EvalCfg &cfg, int budget, int device) {
     return per_sm * prop.multiProcessorCount;
 }
 
+// A genotype that fits one gene a lane runs the kernel built for that
+// (fewer live registers); larger ones the general kernel.
 template <int TPP, int VAR>
 static cudaError_t launch_t(const EvalArgs &a, int ppb, int smem, cudaStream_t s) {
-    auto k = eval_kernel<TPP, VAR>;
+    constexpr int NG_MAX = (MAX_GENES + TPP - 1) / TPP;
+    auto k = (NG_MAX > 1 && 6 + a.lig.n_tors <= TPP) ? eval_kernel<TPP, VAR, 1>
+                                                      : eval_kernel<TPP, VAR, NG_MAX>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int blocks = (a.n + ppb - 1) / ppb;
