@@ -81,6 +81,10 @@ typedef struct {
     int threads_per_pose;  /* 0 = pick per ligand; else 32, 64 or 128 */
     int poses_per_block;   /* 0 = pick per ligand; else 1..8 (at most 128 threads a block) */
     int reduce_variant;    /* default ADGB_REDUCE_* for calls that do not say */
+    int pair_rounds;       /* intramolecular pairs of ligands of at most 32 atoms scored one
+                              warp a genotype: 0 = matching rounds (ligand_pair_rounds;
+                              measured 1.05-1.16x faster for 8-32 atoms), 1 = per-pair
+                              force buffer and incidence lists, as for larger ligands */
 } adgb_options;
 
 /* Receptor grid (Sec. 2.1: the receptor is fixed; its interaction with a
@@ -162,6 +166,26 @@ int release_ligand(adgb_ctx *ctx, int ligand_id);
  * is not NULL.
  */
 int validate_ligand_torsion_tree(const adgb_ligand_desc *lig, char *msg, int msg_len);
+
+/*
+ * ligand_pair_rounds - the host-side schedule of the intramolecular pairs
+ * (Sec. 2.1, Eq. 1's pair sum) that upload_ligand_torsion_tree builds for
+ * a ligand of at most 32 atoms, without a context or a device.  Lane a of
+ * the warp that scores a genotype owns internal atom a; in round r lane a
+ * computes at most one pair with atom a first and receives the reaction
+ * force of at most one pair with atom a second.  The paper has no
+ * counterpart (its block-wide kernel sums forces through shared memory).
+ * n_rounds: rounds (0 above 32 atoms or without pairs); max_degree: the
+ * largest number of pairs an atom is in (n_rounds = ceil(max_degree / 2)).
+ * words [words_cap]: if words_cap >= 32 * n_rounds, word of lane a in round r
+ * at [32 r + a]: partner lane (bits 0-4; a itself without a pair), lane whose
+ * pair's reaction force lane a receives (bits 8-12; a lane without a pair
+ * when there is none), H-bond flag (bit 24).  perm [n_atoms] (may be NULL):
+ * caller's index of internal atom a.  Errors: EINVAL as
+ * validate_ligand_torsion_tree, or words_cap too small for a non-NULL words.
+ */
+int ligand_pair_rounds(const adgb_ligand_desc *lig, int *n_rounds, int *max_degree,
+                       unsigned int *words, int words_cap, int *perm);
 
 /*
  * pose_coords - atom coordinates of n genotypes (Sec. 2.1).

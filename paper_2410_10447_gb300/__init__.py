@@ -7,5 +7,6 @@ from .adgb import (  # noqa: F401
     EXPORTS, LS_RESUME, REDUCE4_PAPER_FS, REDUCE4_PAPER_HALF, REDUCE4_TCGEN05_TF32X2, REDUCE_MMA_BF16X3, REDUCE_MMA_TF32X2, REDUCE_SHFL,
     REDUCE_TCGEN05,
     VARIANTS, AdgbError, Context, Server, library_path, load, validate_ligand_torsion_tree,
+    ligand_pair_rounds,
 )
 from .build import build  # noqa: F401

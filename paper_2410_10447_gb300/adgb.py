@@ -31,7 +31,7 @@ LS_RESUME = 1
 # the C ABI's exported entry points (checked against include/adgb.h by the tests)
 EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_grids",
            "release_receptor", "upload_ligand_torsion_tree", "release_ligand",
-           "validate_ligand_torsion_tree",
+           "validate_ligand_torsion_tree", "ligand_pair_rounds",
            "pose_coords_dev", "pose_coords", "score_poses_dev", "score_poses",
            "local_search_dev", "local_search", "reduce4_bench_dev", "dock_dev", "dock",
            "rescore_fp64_dev", "ga_init_population_dev", "ga_generation_dev", "ga_converged_dev",
@@ -50,7 +50,7 @@ class AdgbError(RuntimeError):
 
 class _Options(C.Structure):
     _fields_ = [("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
-                ("reduce_variant", C.c_int)]
+                ("reduce_variant", C.c_int), ("pair_rounds", C.c_int)]
 
 
 class _Grid(C.Structure):
@@ -98,7 +98,7 @@ def dock_params(**kw) -> _DockParams:
 class _ServeOptions(C.Structure):
     _fields_ = [("max_active_jobs", C.c_int), ("mem_budget_bytes", C.c_longlong),
                 ("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
-                ("reduce_variant", C.c_int)]
+                ("reduce_variant", C.c_int), ("pair_rounds", C.c_int)]
 
 
 class _JobInfo(C.Structure):
@@ -160,6 +160,8 @@ def load(build: bool = False):
     L.upload_ligand_torsion_tree.argtypes = [vp, C.POINTER(_Ligand), C.POINTER(C.c_int)]
     L.release_ligand.argtypes = [vp, C.c_int]
     L.validate_ligand_torsion_tree.argtypes = [C.POINTER(_Ligand), C.c_char_p, C.c_int]
+    L.ligand_pair_rounds.argtypes = [C.POINTER(_Ligand), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     vp, C.c_int, vp]
     L.pose_coords_dev.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
     L.pose_coords.argtypes = [vp, C.c_int, vp, C.c_int, vp]
     L.score_poses_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp, C.c_int, vp]
@@ -257,14 +259,33 @@ def validate_ligand_torsion_tree(lig: dict):
     return rc, buf.value.decode()
 
 
+def ligand_pair_rounds(lig: dict):
+    """(n_rounds, max_degree, words [n_rounds][32] uint32, perm [n_atoms]) of
+    the pair schedule the library builds for ligands of at most 32 atoms;
+    needs no GPU."""
+    d, _keep = _ligand_desc(lig)
+    nr, md = C.c_int(0), C.c_int(0)
+    L = load()
+    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(md), None, 0, None)
+    if rc != ADGB_OK:
+        raise AdgbError(rc, "ligand_pair_rounds")
+    words = np.zeros((max(nr.value, 1), 32), np.uint32)
+    perm = np.zeros(int(lig["n_atoms"]), np.int32)
+    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(md), words.ctypes.data,
+                              words.size, perm.ctypes.data)
+    if rc != ADGB_OK:
+        raise AdgbError(rc, "ligand_pair_rounds")
+    return nr.value, md.value, words[:nr.value], perm
+
+
 class Context:
     """One adgb context on one CUDA device."""
 
     def __init__(self, device: int = 0, threads_per_pose: int = 0, poses_per_block: int = 0,
-                 reduce_variant: int = REDUCE_SHFL):
+                 reduce_variant: int = REDUCE_SHFL, pair_rounds: int = 0):
         self.lib = load()
         self.h = C.c_void_p()
-        opts = _Options(threads_per_pose, poses_per_block, reduce_variant)
+        opts = _Options(threads_per_pose, poses_per_block, reduce_variant, pair_rounds)
         rc = self.lib.adgb_create(C.byref(self.h), device, C.byref(opts))
         if rc != ADGB_OK:
             raise AdgbError(rc, "adgb_create(device=%d)" % device)

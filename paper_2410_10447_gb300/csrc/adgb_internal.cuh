@@ -54,6 +54,11 @@ struct LigDev {
     const uint16_t *inc;      // [2 Np] (pair index - q*PAIR_CHUNK) << 1 | (atom is the pair's
                               // second atom), ordered by chunk and atom (within an atom's
                               // list, in the order that spreads reads over the banks)
+    int n_rounds;             // matching rounds of the pair list (0 above 32 atoms): in a
+                              // round lane a computes at most one pair with atom a first
+                              // and receives the force of at most one pair with atom a second
+    const uint32_t *rword;    // [n_rounds][32] partner lane | force-source lane << 8 | hb << 24
+    const float4 *rconst;     // [n_rounds][32] the pair's constants as in pconst (zeros: no pair)
     // the caller's per-type parameters, kept for the FP64 rescoring
     const float *t_R, *t_eps, *t_vol, *t_sol;
     const int *t_hb;
@@ -244,12 +249,13 @@ struct LigandBlob {
     LigDev rel;
     int max_type = 0;
 };
-int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &out);
+int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_rounds, LigandBlob &out);
 LigDev bind_ligand(const LigandBlob &b, const unsigned char *mem);
 int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg &d, int &variant,
                          std::string *err);
 int ctx_device(const adgb_ctx *c);
 int ctx_default_variant(const adgb_ctx *c);
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps);
+int ctx_pair_rounds(const adgb_ctx *c);
 
 }  // namespace adgb

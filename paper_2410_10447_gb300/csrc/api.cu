@@ -159,10 +159,145 @@ struct HostLigand {
     std::vector<float4> pconst;
     std::vector<int> inc_off;
     std::vector<uint16_t> inc;
+    int R = 0;                       // matching rounds (ligands of at most 32 atoms)
+    std::vector<uint32_t> rword;     // [R][32]
+    std::vector<float4> rconst;      // [R][32]
     std::vector<float> tR, teps, tvol, tsol;
     std::vector<int> thb;
     int max_type = 0;
 };
+
+// Matching rounds of the pair list for ligands of at most 32 atoms, where lane
+// a of a warp owns atom a.  A round gives every lane at most one pair to
+// compute (its atom first) and at most one pair whose force it receives (its
+// atom second), so that a pair's partner position and its reaction force
+// travel by warp shuffles and no force buffer is needed.
+//   1. Orient the pairs so that every atom's in- and out-degrees differ by at
+//      most one: join the odd-degree atoms to an extra vertex, walk closed
+//      trails until every edge is used (each trail enters and leaves a vertex
+//      equally often), orient along the walk, drop the extra edges.
+//   2. Colour the edges of the bipartite graph (tail side, head side) with
+//      D = max over atoms of max(in, out) = ceil(max degree / 2) colours
+//      (Konig's theorem): a colour a free at the tail and b free at the head;
+//      if a is taken at the head, swap a and b along the alternating path
+//      that starts there.  Colour = round.
+// Word of lane l in round r: partner lane (bits 0-4; l itself without a
+// pair), source lane of the received force (bits 8-12; a lane without a pair
+// in that round when l receives nothing, so that the force read is an exact
+// zero), hb flag (bit 24).  A lane without a pair has all-zero constants,
+// which make the pair term exactly zero.
+void build_rounds(HostLigand &h) {
+    const int N = h.N, NP = h.NP, X = N;  // X: the extra vertex
+    std::vector<int> ea(NP), eb(NP);
+    std::vector<std::vector<int>> adj(N + 1);  // edge ids
+    std::vector<int> ex_a, ex_b;
+    for (int p = 0; p < NP; p++) {
+        ea[p] = h.pairs[p] & 255;
+        eb[p] = (h.pairs[p] >> 8) & 255;
+        adj[ea[p]].push_back(p);
+        adj[eb[p]].push_back(p);
+    }
+    for (int v = 0; v < N; v++)
+        if (adj[v].size() & 1) {
+            const int id = NP + (int)ex_a.size();
+            ex_a.push_back(v);
+            ex_b.push_back(X);
+            adj[v].push_back(id);
+            adj[X].push_back(id);
+        }
+    const int NE = NP + (int)ex_a.size();
+    auto end_a = [&](int e) { return e < NP ? ea[e] : ex_a[e - NP]; };
+    auto end_b = [&](int e) { return e < NP ? eb[e] : ex_b[e - NP]; };
+    std::vector<char> used(NE, 0);
+    std::vector<int> tail(NE, -1), head(NE, -1);
+    std::vector<size_t> next(N + 1, 0);
+    for (int s0 = 0; s0 <= N; s0++) {
+        for (;;) {
+            while (next[s0] < adj[s0].size() && used[adj[s0][next[s0]]]) next[s0]++;
+            if (next[s0] == adj[s0].size()) break;
+            int v = s0;
+            for (;;) {  // a closed trail from s0 (every degree is even)
+                while (next[v] < adj[v].size() && used[adj[v][next[v]]]) next[v]++;
+                if (next[v] == adj[v].size()) break;
+                const int e = adj[v][next[v]];
+                used[e] = 1;
+                const int w = end_a(e) == v ? end_b(e) : end_a(e);
+                tail[e] = v;
+                head[e] = w;
+                v = w;
+            }
+        }
+    }
+    std::vector<int> outd(N, 0), ind(N, 0);
+    for (int p = 0; p < NP; p++) {
+        outd[tail[p]]++;
+        ind[head[p]]++;
+    }
+    int D = 0;
+    for (int v = 0; v < N; v++) D = std::max(D, std::max(outd[v], ind[v]));
+    // at_t[v][c] / at_h[v][c]: the edge of colour c leaving / entering v, or -1
+    std::vector<int> at_t((size_t)N * D, -1), at_h((size_t)N * D, -1), col(NP, -1);
+    for (int p = 0; p < NP; p++) {
+        const int u = tail[p], w = head[p];
+        int a = 0, b = 0;
+        while (at_t[(size_t)u * D + a] >= 0) a++;
+        while (at_h[(size_t)w * D + b] >= 0) b++;
+        if (at_h[(size_t)w * D + a] >= 0) {
+            // path from w: w -a- t1 -b- h2 -a- t3 ... ; swap a and b along it
+            std::vector<int> path;
+            int v = w, c = a;
+            bool on_head = true;
+            for (;;) {
+                const int e = on_head ? at_h[(size_t)v * D + c] : at_t[(size_t)v * D + c];
+                if (e < 0) break;
+                path.push_back(e);
+                v = on_head ? tail[e] : head[e];
+                on_head = !on_head;
+                c = c == a ? b : a;
+            }
+            for (int e : path) {
+                at_t[(size_t)tail[e] * D + col[e]] = -1;
+                at_h[(size_t)head[e] * D + col[e]] = -1;
+            }
+            for (int e : path) {
+                col[e] = col[e] == a ? b : a;
+                at_t[(size_t)tail[e] * D + col[e]] = e;
+                at_h[(size_t)head[e] * D + col[e]] = e;
+            }
+        }
+        col[p] = a;
+        at_t[(size_t)u * D + a] = p;
+        at_h[(size_t)w * D + a] = p;
+    }
+    h.R = D;
+    h.rword.assign((size_t)D * 32, 0);
+    h.rconst.assign((size_t)D * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int r = 0; r < D; r++) {
+        uint32_t *wd = &h.rword[(size_t)r * 32];
+        int idle = -1;  // a lane without a pair this round
+        for (int l = 0; l < 32; l++) {
+            const int e = l < N ? at_t[(size_t)l * D + r] : -1;
+            if (e < 0) {
+                wd[l] = (uint32_t)l;
+                if (idle < 0) idle = l;
+            } else {
+                // lane l computes the pair with its own atom first: the pair
+                // term is symmetric (swapping the atoms negates dx, dy, dz
+                // exactly and hence the force)
+                wd[l] = (uint32_t)head[e] | ((h.pairs[e] >> 24) & 1u) << 24;
+                h.rconst[(size_t)r * 32 + l] = h.pconst[e];
+            }
+        }
+        for (int l = 0; l < 32; l++) {
+            const int e = l < N ? at_h[(size_t)l * D + r] : -1;
+            wd[l] |= (uint32_t)(e >= 0 ? tail[e] : idle) << 8;
+        }
+    }
+}
+
+// Whether the kernels use the matching rounds of a ligand (mode as
+// adgb_options.pair_rounds).
+bool use_pair_rounds(const HostLigand &h, int mode) { return h.R > 0 && mode == 0; }
 
 int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
     if (!d) return ferr(err, ADGB_EINVAL, "ligand: null descriptor");
@@ -455,6 +590,7 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         const double ds = (double)h.sv[i].x * h.sv[j].y + (double)h.sv[j].x * h.sv[i].y;
         h.pconst[p] = make_float4(ab.x, ab.y, (float)qq, (float)ds);
     }
+    if (N <= 32 && NP > 0) build_rounds(h);
     return ADGB_OK;
 }
 
@@ -507,10 +643,11 @@ int lookup(adgb_ctx *c, int rid, int lid, Receptor **R, Ligand **L) {
 
 namespace adgb {
 
-int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &out) {
+int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_rounds, LigandBlob &out) {
     HostLigand h;
     int rc = build_ligand(err, d, h);
     if (rc) return rc;
+    if (!use_pair_rounds(h, pair_rounds)) h.R = 0;
     const int N = h.N, T = h.T, NP = h.NP, NT = d->n_types;
     const int Tz = T > 0 ? T : 1, NPz = NP > 0 ? NP : 1;
     size_t off = 0;
@@ -521,6 +658,8 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     const size_t o_pconst = take(16 * NPz);
     const int NCH = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
     const size_t o_incoff = take(4 * (size_t)(NCH > 0 ? NCH : 1) * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
+    const int Rz = h.R > 0 ? h.R : 1;
+    const size_t o_rword = take(4 * 32 * (size_t)Rz), o_rconst = take(16 * 32 * (size_t)Rz);
     const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
                  o_tsol = take(4 * NT), o_thb = take(4 * NT);
     std::vector<unsigned char> &buf = out.bytes;
@@ -541,6 +680,10 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     memcpy(&buf[o_perm], h.perm.data(), 4 * N);
     if (NCH) memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (size_t)NCH * (N + 1));
     if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
+    if (h.R) {
+        memcpy(&buf[o_rword], h.rword.data(), 4 * 32 * (size_t)h.R);
+        memcpy(&buf[o_rconst], h.rconst.data(), 16 * 32 * (size_t)h.R);
+    }
     memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
     memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
     memcpy(&buf[o_tvol], h.tvol.data(), 4 * NT);
@@ -552,6 +695,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     v.n_pairs = NP;
     v.n_types = NT;
     v.n_chunks = NCH;
+    v.n_rounds = h.R;
     // offsets travel in the pointer fields until bind_ligand relocates them
     auto at = [](size_t o) { return reinterpret_cast<const unsigned char *>((uintptr_t)o); };
     v.ref = reinterpret_cast<const float4 *>(at(o_ref));
@@ -568,6 +712,8 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, LigandBlob &ou
     v.perm = reinterpret_cast<const int *>(at(o_perm));
     v.inc_off = reinterpret_cast<const int *>(at(o_incoff));
     v.inc = reinterpret_cast<const uint16_t *>(at(o_inc));
+    v.rword = reinterpret_cast<const uint32_t *>(at(o_rword));
+    v.rconst = reinterpret_cast<const float4 *>(at(o_rconst));
     v.t_R = reinterpret_cast<const float *>(at(o_tR));
     v.t_eps = reinterpret_cast<const float *>(at(o_teps));
     v.t_vol = reinterpret_cast<const float *>(at(o_tvol));
@@ -596,6 +742,8 @@ LigDev bind_ligand(const LigandBlob &b, const unsigned char *mem) {
     v.perm = mv(v.perm);
     v.inc_off = mv(v.inc_off);
     v.inc = mv(v.inc);
+    v.rword = mv(v.rword);
+    v.rconst = mv(v.rconst);
     v.t_R = mv(v.t_R);
     v.t_eps = mv(v.t_eps);
     v.t_vol = mv(v.t_vol);
@@ -657,6 +805,8 @@ int dock_cfg_from_params(const adgb_dock_params *p, int default_variant, DockCfg
 int ctx_device(const adgb_ctx *c) { return c->device; }
 int ctx_default_variant(const adgb_ctx *c) { return c->opts.reduce_variant; }
 
+int ctx_pair_rounds(const adgb_ctx *c) { return c->opts.pair_rounds; }
+
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps) {
     auto it = c->recs.find(rid);
     if (it == c->recs.end()) return ADGB_ENOTFOUND;
@@ -684,7 +834,8 @@ int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts) {
         return ADGB_EINVAL;
     }
     if (c->opts.poses_per_block < 0 || c->opts.poses_per_block > 8 ||
-        c->opts.reduce_variant < 0 || c->opts.reduce_variant >= ADGB_REDUCE_N) {
+        c->opts.reduce_variant < 0 || c->opts.reduce_variant >= ADGB_REDUCE_N ||
+        c->opts.pair_rounds < 0 || c->opts.pair_rounds > 1) {
         delete c;
         return ADGB_EINVAL;
     }
@@ -783,7 +934,7 @@ int upload_ligand_torsion_tree(adgb_ctx *c, const adgb_ligand_desc *d, int *liga
     if (!c) return ADGB_EINVAL;
     if (!ligand_id) return fail(c, ADGB_EINVAL, "ligand: null id pointer");
     LigandBlob blob;
-    int rc = make_ligand_blob(&c->err, d, blob);
+    int rc = make_ligand_blob(&c->err, d, c->opts.pair_rounds, blob);
     if (rc) return rc;
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
@@ -818,6 +969,27 @@ int validate_ligand_torsion_tree(const adgb_ligand_desc *d, char *msg, int msg_l
         msg[msg_len - 1] = 0;
     }
     return rc;
+}
+
+int ligand_pair_rounds(const adgb_ligand_desc *d, int *n_rounds, int *max_degree,
+                       unsigned int *words, int words_cap, int *perm) {
+    std::string err;
+    HostLigand h;
+    const int rc = build_ligand(&err, d, h);
+    if (rc) return rc;
+    std::vector<int> deg(h.N, 0);
+    for (uint32_t c : h.pairs) {
+        deg[c & 255]++;
+        deg[(c >> 8) & 255]++;
+    }
+    if (n_rounds) *n_rounds = h.R;
+    if (max_degree) *max_degree = h.N ? *std::max_element(deg.begin(), deg.end()) : 0;
+    if (words) {
+        if (words_cap < 32 * h.R) return ADGB_EINVAL;
+        std::copy(h.rword.begin(), h.rword.end(), words);
+    }
+    if (perm) std::copy(h.perm.begin(), h.perm.end(), perm);
+    return ADGB_OK;
 }
 
 int release_ligand(adgb_ctx *c, int id) {
@@ -1546,6 +1718,7 @@ extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev,
         chosen->threads_per_pose = best.tpp;
         chosen->poses_per_block = best.ppb;
         chosen->reduce_variant = best.variant;
+        chosen->pair_rounds = c->opts.pair_rounds;
     }
     return ADGB_OK;
 }

@@ -431,7 +431,11 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         const float m02 = o * u.x * u.z + s * u.y, m20 = o * u.x * u.z - s * u.y;
         const float m12 = o * u.y * u.z - s * u.x, m21 = o * u.y * u.z + s * u.x;
 
-        // 2. coordinates and intermolecular terms
+        // 2. coordinates and intermolecular terms.  With matching rounds
+        //    (one warp, at most 32 atoms: lane a owns atom a) the lane keeps
+        //    its atom's position and gradient in registers.
+        const bool rounds = TPP == 32 && lig.n_rounds > 0;
+        float3 xo = make_float3(0.f, 0.f, 0.f), go = xo;
         float e_part = 0.f;
         for (int i = gt; i < N; i += TPP) {
             const float4 r4 = s_ref[i];
@@ -444,16 +448,48 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
             xyz[i] = make_float4(x.x, x.y, x.z, r4.w);
             float3 g;
             e_part += inter_atom(rec, s_type[i], r4.w, x, g);
-            grd[i] = make_float4(g.x, g.y, g.z, 0.f);
+            if (rounds) {
+                xo = x;
+                go = g;
+            } else {
+                grd[i] = make_float4(g.x, g.y, g.z, 0.f);
+            }
         }
         group_sync<TPP>(group);
 
-        // 3. intramolecular pairs, chunk by chunk (PAIR_CHUNK pairs): every
+        // 3a. intramolecular pairs in matching rounds: the partner's position
+        //     and the reaction force of the pair whose second atom is the
+        //     lane's come by shuffles; lanes without a pair compute an exact
+        //     zero (zero constants, partner = itself).
+        if (rounds) {
+            const uint32_t *rw = lig.rword + gt;
+            const float4 *rc = lig.rconst + gt;
+            const float4 xi = make_float4(xo.x, xo.y, xo.z, 0.f);
+#pragma unroll 2
+            for (int r = 0; r < lig.n_rounds; r++) {
+                const uint32_t w = __ldg(rw + 32 * r);
+                const float4 pc = __ldg(rc + 32 * r);
+                const int pj = w & 31, src = (w >> 8) & 31;
+                const float4 xj = make_float4(__shfl_sync(0xffffffffu, xo.x, pj),
+                                              __shfl_sync(0xffffffffu, xo.y, pj),
+                                              __shfl_sync(0xffffffffu, xo.z, pj), 0.f);
+                float3 f;
+                e_part += pair_term(xi, xj, pc, (w >> 24) & 1, f);
+                go.x += f.x;
+                go.y += f.y;
+                go.z += f.z;
+                go.x -= __shfl_sync(0xffffffffu, f.x, src);
+                go.y -= __shfl_sync(0xffffffffu, f.y, src);
+                go.z -= __shfl_sync(0xffffffffu, f.z, src);
+            }
+        }
+
+        // 3b. otherwise, chunk by chunk (PAIR_CHUNK pairs): every
         //    pair's force goes to its own slot of the force buffer, then each
         //    atom's owner adds the forces of its pairs in the chunk (per-chunk
         //    incidence lists with known bounds).  No two threads ever write
         //    the same word.
-        for (int q = 0; q < lig.n_chunks; q++) {
+        for (int q = 0; q < (rounds ? 0 : lig.n_chunks); q++) {
             const int c0 = q * PAIR_CHUNK, c1 = min(NP, c0 + PAIR_CHUNK);
 #pragma unroll 2
             for (int p = c0 + gt; p < c1; p += TPP) {
@@ -491,7 +527,8 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float4 *tq = reinterpret_cast<float4 *>(P + L.p_tq);
         for (int i = gt; i < N; i += TPP) {
-            const float4 g = grd[i], x = xyz[i];
+            const float4 g = rounds ? make_float4(go.x, go.y, go.z, 0.f) : grd[i];
+            const float4 x = rounds ? make_float4(xo.x, xo.y, xo.z, 0.f) : xyz[i];
             const float3 d = make_float3(x.x - tr.x, x.y - tr.y, x.z - tr.z);
             const float3 c = make_float3(d.y * g.z - d.z * g.y, d.z * g.x - d.x * g.z,
                                          d.x * g.y - d.y * g.x);

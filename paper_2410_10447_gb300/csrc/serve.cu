@@ -506,7 +506,7 @@ int dock_submit(adgb_server *s, int receptor_id, const adgb_ligand_desc *lig,
         rc = ADGB_EINVAL;
         err = "dock_submit: the serving loop runs the ADADELTA local search only";
     }
-    if (rc == ADGB_OK) rc = make_ligand_blob(&err, lig, j->blob);
+    if (rc == ADGB_OK) rc = make_ligand_blob(&err, lig, ctx_pair_rounds(s->ctx), j->blob);
     int n_type_maps = 0;
     if (rc == ADGB_OK && ctx_receptor(s->ctx, receptor_id, &j->rec, &n_type_maps) != ADGB_OK) {
         rc = ADGB_ENOTFOUND;

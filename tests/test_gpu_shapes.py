@@ -1,7 +1,8 @@
 """Ligand shapes across the kernels' internal boundaries, each against the
 FP64 oracle: atom counts just below and above one warp (32), two warps (64),
 four warps (128) and the maximum (256); torsion counts 0 and the maximum
-(40); pair lists below and above one force-buffer chunk (1024 pairs).  For
+(40); pair lists below and above one force-buffer chunk (1024 pairs); up to
+32 atoms, both pair paths (matching rounds and force buffer).  For
 every shape: scores with each reduction variant, a short ADADELTA search
 that must return its best, and the Solis-Wets start energy.
 Tolerances: energy max(1e-4 |E|, 1e-3 kcal/mol); gene gradient 1e-3 (FP32
@@ -44,13 +45,16 @@ def near_face(r, x, tol=1e-4):
     return bool(np.any(np.abs(u - np.round(u)) * r["spacing"] < tol))
 
 
+@pytest.mark.parametrize("pair_rounds", [0, 1])
 @pytest.mark.parametrize("n_atoms, n_tors", SHAPES)
-def test_shape_parity(pkg, torch, rec, n_atoms, n_tors):
+def test_shape_parity(pkg, torch, rec, n_atoms, n_tors, pair_rounds):
+    if pair_rounds and n_atoms > 32:
+        pytest.skip("one pair path above 32 atoms")
     lig = synth.make_ligand(31_000 + n_atoms, n_atoms, 8, n_tors)
     genes = synth.make_poses(32_000 + n_atoms, 6, rec, n_tors)
     R, L = oracle.Receptor(rec), oracle.Ligand(lig)
     refs = [oracle.score(R, L, g) for g in genes]
-    ctx = pkg.Context(0)
+    ctx = pkg.Context(0, pair_rounds=pair_rounds)
     rid = ctx.upload_receptor_grids(rec)
     lid = ctx.upload_ligand_torsion_tree(lig)
     for v in (0, 1, 2, 3):
