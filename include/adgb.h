@@ -173,15 +173,16 @@ int validate_ligand_torsion_tree(const adgb_ligand_desc *lig, char *msg, int msg
  * a ligand of at most 32 atoms, without a context or a device.  Lane a of
  * the warp that scores a genotype owns internal atom a; in round r lane a
  * computes at most one pair with atom a first and receives the reaction
- * force of at most one pair with atom a second.  The paper has no
+ * forces of at most two pairs with atom a second.  The paper has no
  * counterpart (its block-wide kernel sums forces through shared memory).
- * n_rounds: rounds (0 above 32 atoms or without pairs); max_degree: the
- * largest number of pairs an atom is in (n_rounds = ceil(max_degree / 2)).
- * words [words_cap]: if words_cap >= 32 * n_rounds, word of lane a in round r
- * at [32 r + a]: partner lane (bits 0-4; a itself without a pair), lane whose
- * pair's reaction force lane a receives (bits 8-12; a lane without a pair
- * when there is none), H-bond flag (bit 24).  perm [n_atoms] (may be NULL):
- * caller's index of internal atom a.  Errors: EINVAL as
+ * n_rounds: rounds (0 above 32 atoms or without pairs), normally
+ * max(ceil(pairs / atoms), ceil(max_degree / 3)); max_degree: the largest
+ * number of pairs an atom is in.  words [words_cap]: if words_cap >=
+ * 32 * n_rounds, word of lane a in round r at [32 r + a]: partner lane
+ * (bits 0-4; a itself without a pair), lanes whose pairs' reaction forces
+ * lane a receives (bits 8-12 and 16-20), H-bond flag (bit 24), whether each
+ * of the two receive slots is used (bits 25, 26).  perm [n_atoms] (may be
+ * NULL): caller's index of internal atom a.  Errors: EINVAL as
  * validate_ligand_torsion_tree, or words_cap too small for a non-NULL words.
  */
 int ligand_pair_rounds(const adgb_ligand_desc *lig, int *n_rounds, int *max_degree,

@@ -56,8 +56,9 @@ struct LigDev {
                               // list, in the order that spreads reads over the banks)
     int n_rounds;             // matching rounds of the pair list (0 above 32 atoms): in a
                               // round lane a computes at most one pair with atom a first
-                              // and receives the force of at most one pair with atom a second
-    const uint32_t *rword;    // [n_rounds][32] partner lane | force-source lane << 8 | hb << 24
+                              // and receives the forces of at most two pairs with atom a second
+    const uint32_t *rword;    // [n_rounds][32] partner lane | force-source lanes << 8, << 16 |
+                              // hb << 24 | source used << 25, << 26
     const float4 *rconst;     // [n_rounds][32] the pair's constants as in pconst (zeros: no pair)
     // the caller's per-type parameters, kept for the FP64 rescoring
     const float *t_R, *t_eps, *t_vol, *t_sol;

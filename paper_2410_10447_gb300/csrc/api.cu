@@ -169,26 +169,33 @@ struct HostLigand {
 
 // Matching rounds of the pair list for ligands of at most 32 atoms, where lane
 // a of a warp owns atom a.  A round gives every lane at most one pair to
-// compute (its atom first) and at most one pair whose force it receives (its
-// atom second), so that a pair's partner position and its reaction force
-// travel by warp shuffles and no force buffer is needed.
-//   1. Orient the pairs so that every atom's in- and out-degrees differ by at
-//      most one: join the odd-degree atoms to an extra vertex, walk closed
-//      trails until every edge is used (each trail enters and leaves a vertex
-//      equally often), orient along the walk, drop the extra edges.
-//   2. Colour the edges of the bipartite graph (tail side, head side) with
-//      D = max over atoms of max(in, out) = ceil(max degree / 2) colours
-//      (Konig's theorem): a colour a free at the tail and b free at the head;
-//      if a is taken at the head, swap a and b along the alternating path
-//      that starts there.  Colour = round.
+// compute (its atom first) and at most two pairs whose reaction force it
+// receives (its atom second), so that partner positions and reaction forces
+// travel by warp shuffles and no force buffer is needed.  Rounds:
+// R = max(ceil(pairs / atoms), ceil(max degree / 3)), the least for which
+// an atom of the largest degree fits (one out, two in a round) and the
+// atoms' lanes hold every pair; R grows only if no orientation below fits.
+//   1. Orient the pairs with every atom's in- and out-degrees within one of
+//      each other: join the odd-degree atoms to an extra vertex, walk closed
+//      trails until every edge is used (a closed trail enters and leaves a
+//      vertex equally often), orient along the walk, drop the extra edges.
+//   2. While an atom has more than R out-edges, reverse a directed path
+//      from it to an atom with fewer than R (breadth-first search); the
+//      ends change by one, the inner atoms not at all.  In-degrees stay at
+//      most 2R because the degree is at most 3R.
+//   3. Split each atom's in-edges over two receive slots (at most R each)
+//      and colour the edges of the bipartite graph (tails; slots) with R
+//      colours (Konig's theorem): a colour a free at the tail and b free at
+//      the slot; if a is taken at the slot, swap a and b along the
+//      alternating path that starts there.  Colour = round.
 // Word of lane l in round r: partner lane (bits 0-4; l itself without a
-// pair), source lane of the received force (bits 8-12; a lane without a pair
-// in that round when l receives nothing, so that the force read is an exact
-// zero), hb flag (bit 24).  A lane without a pair has all-zero constants,
-// which make the pair term exactly zero.
+// pair), source lanes of the two received forces (bits 8-12 and 16-20), hb
+// flag (bit 24), whether each receive slot is used (bits 25 and 26).  A lane
+// without a pair has all-zero constants, which make the pair term exactly
+// zero.
 void build_rounds(HostLigand &h) {
     const int N = h.N, NP = h.NP, X = N;  // X: the extra vertex
-    std::vector<int> ea(NP), eb(NP);
+    std::vector<int> ea(NP), eb(NP), deg(N, 0);
     std::vector<std::vector<int>> adj(N + 1);  // edge ids
     std::vector<int> ex_a, ex_b;
     for (int p = 0; p < NP; p++) {
@@ -196,6 +203,8 @@ void build_rounds(HostLigand &h) {
         eb[p] = (h.pairs[p] >> 8) & 255;
         adj[ea[p]].push_back(p);
         adj[eb[p]].push_back(p);
+        deg[ea[p]]++;
+        deg[eb[p]]++;
     }
     for (int v = 0; v < N; v++)
         if (adj[v].size() & 1) {
@@ -228,69 +237,112 @@ void build_rounds(HostLigand &h) {
             }
         }
     }
-    std::vector<int> outd(N, 0), ind(N, 0);
-    for (int p = 0; p < NP; p++) {
-        outd[tail[p]]++;
-        ind[head[p]]++;
+    const int maxdeg = *std::max_element(deg.begin(), deg.end());
+    int R = std::max((NP + N - 1) / N, (maxdeg + 2) / 3);
+    std::vector<int> outd(N);
+    auto count_out = [&]() {
+        std::fill(outd.begin(), outd.end(), 0);
+        for (int p = 0; p < NP; p++) outd[tail[p]]++;
+    };
+    count_out();
+    for (int u = 0; u < N; u++) {
+        while (outd[u] > R) {
+            // breadth-first search along out-edges for an atom below R
+            std::vector<int> via(N, -1);
+            std::vector<char> seen(N, 0);
+            std::vector<int> queue(1, u);
+            seen[u] = 1;
+            int found = -1;
+            for (size_t qi = 0; qi < queue.size() && found < 0; qi++) {
+                const int x = queue[qi];
+                for (int p = 0; p < NP && found < 0; p++) {
+                    if (tail[p] != x || seen[head[p]]) continue;
+                    seen[head[p]] = 1;
+                    via[head[p]] = p;
+                    if (outd[head[p]] < R) found = head[p];
+                    else queue.push_back(head[p]);
+                }
+            }
+            if (found < 0) {  // every atom reachable from u is full: widen
+                R++;
+                continue;
+            }
+            for (int x = found; x != u;) {
+                const int p = via[x];
+                const int t = tail[p];
+                std::swap(tail[p], head[p]);
+                x = t;
+            }
+            count_out();
+        }
     }
-    int D = 0;
-    for (int v = 0; v < N; v++) D = std::max(D, std::max(outd[v], ind[v]));
-    // at_t[v][c] / at_h[v][c]: the edge of colour c leaving / entering v, or -1
-    std::vector<int> at_t((size_t)N * D, -1), at_h((size_t)N * D, -1), col(NP, -1);
+    // receive slots: slot 2v + k, k = 0, 1; an atom's in-edges split in halves
+    std::vector<int> slot(NP, -1), ind(N, 0);
+    for (int p = 0; p < NP; p++) ind[head[p]]++;
+    for (int v = 0; v < N; v++) R = std::max(R, (ind[v] + 1) / 2);
+    std::vector<int> filled(N, 0);
     for (int p = 0; p < NP; p++) {
-        const int u = tail[p], w = head[p];
+        const int v = head[p];
+        slot[p] = 2 * v + (filled[v]++ < (ind[v] + 1) / 2 ? 0 : 1);
+    }
+    // at_t[u][c] / at_s[q][c]: the edge of colour c leaving atom u / in slot q
+    std::vector<int> at_t((size_t)N * R, -1), at_s((size_t)2 * N * R, -1), col(NP, -1);
+    for (int p = 0; p < NP; p++) {
+        const int u = tail[p], q = slot[p];
         int a = 0, b = 0;
-        while (at_t[(size_t)u * D + a] >= 0) a++;
-        while (at_h[(size_t)w * D + b] >= 0) b++;
-        if (at_h[(size_t)w * D + a] >= 0) {
-            // path from w: w -a- t1 -b- h2 -a- t3 ... ; swap a and b along it
+        while (at_t[(size_t)u * R + a] >= 0) a++;
+        while (at_s[(size_t)q * R + b] >= 0) b++;
+        if (at_s[(size_t)q * R + a] >= 0) {
+            // path from q: q -a- t1 -b- q2 -a- t3 ... ; swap a and b along it
             std::vector<int> path;
-            int v = w, c = a;
-            bool on_head = true;
+            int v = q, c = a;
+            bool on_slot = true;
             for (;;) {
-                const int e = on_head ? at_h[(size_t)v * D + c] : at_t[(size_t)v * D + c];
+                const int e = on_slot ? at_s[(size_t)v * R + c] : at_t[(size_t)v * R + c];
                 if (e < 0) break;
                 path.push_back(e);
-                v = on_head ? tail[e] : head[e];
-                on_head = !on_head;
+                v = on_slot ? tail[e] : slot[e];
+                on_slot = !on_slot;
                 c = c == a ? b : a;
             }
             for (int e : path) {
-                at_t[(size_t)tail[e] * D + col[e]] = -1;
-                at_h[(size_t)head[e] * D + col[e]] = -1;
+                at_t[(size_t)tail[e] * R + col[e]] = -1;
+                at_s[(size_t)slot[e] * R + col[e]] = -1;
             }
             for (int e : path) {
                 col[e] = col[e] == a ? b : a;
-                at_t[(size_t)tail[e] * D + col[e]] = e;
-                at_h[(size_t)head[e] * D + col[e]] = e;
+                at_t[(size_t)tail[e] * R + col[e]] = e;
+                at_s[(size_t)slot[e] * R + col[e]] = e;
             }
         }
         col[p] = a;
-        at_t[(size_t)u * D + a] = p;
-        at_h[(size_t)w * D + a] = p;
+        at_t[(size_t)u * R + a] = p;
+        at_s[(size_t)q * R + a] = p;
     }
-    h.R = D;
-    h.rword.assign((size_t)D * 32, 0);
-    h.rconst.assign((size_t)D * 32, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int r = 0; r < D; r++) {
+    h.R = R;
+    h.rword.assign((size_t)R * 32, 0);
+    h.rconst.assign((size_t)R * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int r = 0; r < R; r++) {
         uint32_t *wd = &h.rword[(size_t)r * 32];
-        int idle = -1;  // a lane without a pair this round
         for (int l = 0; l < 32; l++) {
-            const int e = l < N ? at_t[(size_t)l * D + r] : -1;
-            if (e < 0) {
-                wd[l] = (uint32_t)l;
-                if (idle < 0) idle = l;
-            } else {
-                // lane l computes the pair with its own atom first: the pair
-                // term is symmetric (swapping the atoms negates dx, dy, dz
-                // exactly and hence the force)
-                wd[l] = (uint32_t)head[e] | ((h.pairs[e] >> 24) & 1u) << 24;
-                h.rconst[(size_t)r * 32 + l] = h.pconst[e];
+            uint32_t w = (uint32_t)l | (uint32_t)l << 8 | (uint32_t)l << 16;
+            if (l < N) {
+                const int e = at_t[(size_t)l * R + r];
+                if (e >= 0) {
+                    // lane l computes the pair with its own atom first: the
+                    // pair term is symmetric (swapping the atoms negates dx,
+                    // dy, dz exactly and hence the force)
+                    w = (w & ~31u) | (uint32_t)head[e] | ((h.pairs[e] >> 24) & 1u) << 24;
+                    h.rconst[(size_t)r * 32 + l] = h.pconst[e];
+                }
+                for (int k = 0; k < 2; k++) {
+                    const int f = at_s[(size_t)(2 * l + k) * R + r];
+                    if (f >= 0)
+                        w = (w & ~(31u << (8 + 8 * k))) | (uint32_t)tail[f] << (8 + 8 * k) |
+                            1u << (25 + k);
+                }
             }
-        }
-        for (int l = 0; l < 32; l++) {
-            const int e = l < N ? at_h[(size_t)l * D + r] : -1;
-            wd[l] |= (uint32_t)(e >= 0 ? tail[e] : idle) << 8;
+            wd[l] = w;
         }
     }
 }

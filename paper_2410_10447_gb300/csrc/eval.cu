@@ -458,9 +458,10 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         group_sync<TPP>(group);
 
         // 3a. intramolecular pairs in matching rounds: the partner's position
-        //     and the reaction force of the pair whose second atom is the
-        //     lane's come by shuffles; lanes without a pair compute an exact
-        //     zero (zero constants, partner = itself).
+        //     and the reaction forces of the (at most two) pairs whose second
+        //     atom is the lane's come by shuffles, an unused receive slot
+        //     weighted by zero; lanes without a pair compute an exact zero
+        //     (zero constants, partner = itself).
         if (rounds) {
             const uint32_t *rw = lig.rword + gt;
             const float4 *rc = lig.rconst + gt;
@@ -469,18 +470,22 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
             for (int r = 0; r < lig.n_rounds; r++) {
                 const uint32_t w = __ldg(rw + 32 * r);
                 const float4 pc = __ldg(rc + 32 * r);
-                const int pj = w & 31, src = (w >> 8) & 31;
+                const int pj = w & 31, s1 = (w >> 8) & 31, s2 = (w >> 16) & 31;
                 const float4 xj = make_float4(__shfl_sync(0xffffffffu, xo.x, pj),
                                               __shfl_sync(0xffffffffu, xo.y, pj),
                                               __shfl_sync(0xffffffffu, xo.z, pj), 0.f);
                 float3 f;
                 e_part += pair_term(xi, xj, pc, (w >> 24) & 1, f);
+                const float m1 = (w >> 25) & 1 ? 1.f : 0.f, m2 = (w >> 26) & 1 ? 1.f : 0.f;
                 go.x += f.x;
                 go.y += f.y;
                 go.z += f.z;
-                go.x -= __shfl_sync(0xffffffffu, f.x, src);
-                go.y -= __shfl_sync(0xffffffffu, f.y, src);
-                go.z -= __shfl_sync(0xffffffffu, f.z, src);
+                go.x -= m1 * __shfl_sync(0xffffffffu, f.x, s1);
+                go.y -= m1 * __shfl_sync(0xffffffffu, f.y, s1);
+                go.z -= m1 * __shfl_sync(0xffffffffu, f.z, s1);
+                go.x -= m2 * __shfl_sync(0xffffffffu, f.x, s2);
+                go.y -= m2 * __shfl_sync(0xffffffffu, f.y, s2);
+                go.z -= m2 * __shfl_sync(0xffffffffu, f.z, s2);
             }
         }
 
