@@ -21,6 +21,8 @@
 //      that own the genes.
 #include <math.h>
 
+#include <algorithm>
+
 #include "adgb_internal.cuh"
 #include "philox.cuh"
 #include "reduce.cuh"
@@ -1153,6 +1155,25 @@ cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *
     return cudaErrorInvalidValue;
 }
 
+// Blocks an SM holds at once, from the kernel's registers and static shared
+// memory and the device's limits (registers allocated per warp in units of
+// 256), and for the tcgen05 variant the 512 TMEM columns.  Used for that
+// variant's persistent launches: for those kernels the runtime's occupancy
+// query was measured to report one block an SM, although the launch holds
+// as many as registers and shared memory allow (ncu: 5 for 96 registers).
+static int resident_blocks(const cudaFuncAttributes &fa, const cudaDeviceProp &prop,
+                           const EvalCfg &cfg, int smem) {
+    const int threads = cfg.tpp * cfg.ppb, warps = (threads + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    int n = regs_warp > 0 ? prop.regsPerMultiprocessor / (regs_warp * warps) : 32;
+    const int smem_block = (int)fa.sharedSizeBytes + smem + (int)prop.reservedSharedMemPerBlock;
+    n = std::min(n, (int)prop.sharedMemPerMultiprocessor / std::max(smem_block, 1));
+    n = std::min(n, prop.maxThreadsPerMultiProcessor / (warps * 32));
+    n = std::min(n, prop.maxBlocksPerMultiProcessor);
+    if (cfg.variant == ADGB_REDUCE_TCGEN05) n = std::min(n, 512 / tc_ncols(warps));
+    return n;
+}
+
 // Resident blocks of the persistent launch: SMs x blocks an SM can hold.
 int items_grid(const EvalCfg &cfg, int budget, int device) {
     cudaDeviceProp prop;
@@ -1163,10 +1184,16 @@ int items_grid(const EvalCfg &cfg, int budget, int device) {
     cudaError_t e = cudaErrorInvalidValue;
 #define ADGB_OCC(TPP, VAR)                                                                   \
     if (cfg.tpp == TPP && cfg.variant == VAR) {                                              \
-        cudaFuncSetAttribute(eval_items_kernel<TPP, VAR>,                                    \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);             \
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, eval_items_kernel<TPP, VAR>, \
-                                                          TPP * cfg.ppb, smem);             \
+        e = cudaFuncSetAttribute(eval_items_kernel<TPP, VAR>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);         \
+        if (e == cudaSuccess && VAR == ADGB_REDUCE_TCGEN05) {                                \
+            cudaFuncAttributes fa;                                                           \
+            e = cudaFuncGetAttributes(&fa, eval_items_kernel<TPP, VAR>);                     \
+            if (e == cudaSuccess) per_sm = resident_blocks(fa, prop, cfg, smem);             \
+        } else if (e == cudaSuccess) {                                                       \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                               \
+                &per_sm, eval_items_kernel<TPP, VAR>, TPP * cfg.ppb, smem);                  \
+        }                                                                                    \
     }
     ADGB_OCC(32, 0) ADGB_OCC(32, 1) ADGB_OCC(32, 2) ADGB_OCC(32, 3)
     ADGB_OCC(64, 0) ADGB_OCC(64, 1) ADGB_OCC(64, 2) ADGB_OCC(64, 3)

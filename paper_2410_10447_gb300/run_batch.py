@@ -3,11 +3,13 @@ genotypes, locally searched by one persistent multi-ligand launch replayed
 from a CUDA graph, against the same work done ligand by ligand.
 
     python -m paper_2410_10447_gb300.run_batch [--ligands 512] [--poses 64]
-        [--iters 300] [--reps 3] [--no-autotune] [--no-serial]
+        [--iters 300] [--reps 3] [--no-autotune] [--no-serial] [--variant V]
 
 Workload uneven_512: ligands with atom counts uniform in [10, 128] and
 torsions uniform in [0, 32] (10 atom types), 64 genotypes each, 300 ADADELTA
-evaluations, one shared 72^3 grid with 10 + 2 maps.  Prints one JSON line.
+evaluations, one shared 72^3 grid with 10 + 2 maps.  --variant forces the
+batch's reduction (REDUCE_*) over the autotuner's pick; the ligand-by-ligand
+comparison always uses the shuffle reduction.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -36,6 +38,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
+    ap.add_argument("--variant", type=int, default=-1)
     a = ap.parse_args(argv)
     P.load(build=True)
     w = synth.WORKLOADS["uneven_512"]
@@ -63,7 +66,7 @@ def main(argv=None):
         g.copy_(g0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record()
-        ctx.batch_local_search_dev(bid, g, e, a.iters)
+        ctx.batch_local_search_dev(bid, g, e, a.iters, variant=a.variant)
         ev1.record()
         torch.cuda.synchronize()
         ms.append(ev0.elapsed_time(ev1))
@@ -73,6 +76,7 @@ def main(argv=None):
                atoms_mean=float(np.mean([L["n_atoms"] for L in ligs])),
                pairs_mean=float(np.mean([len(L["pairs"]) for L in ligs])),
                batch_ms=t_batch, batch_evals_per_s=evals / t_batch * 1e3, autotuned=tuned,
+               variant=a.variant,
                first_call_ms_incl_capture=ms[0], generate_s=t_gen)
     if not a.no_serial:
         # the same work as one single-ligand launch per ligand, back to back
@@ -85,7 +89,7 @@ def main(argv=None):
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record()
             for i in range(a.ligands):
-                ctx.local_search_dev(rid, lids[i], gs[i], es[i], a.iters)
+                ctx.local_search_dev(rid, lids[i], gs[i], es[i], a.iters, variant=P.REDUCE_SHFL)
             ev1.record()
             torch.cuda.synchronize()
             sms.append(ev0.elapsed_time(ev1))

@@ -3,13 +3,18 @@ continuous-batching server.
 
     python -m paper_2410_10447_gb300.serve_bench [--rate 200] [--duration 60]
         [--runs 10] [--pop 150] [--evals-per-run 2.5e6] [--ls-iters 300]
-        [--pool 48] [--max-active 0] [--seed 1]
+        [--pool 48] [--max-active 0] [--seed 1] [--variant -1] [--serial]
 
 Jobs: ligands of 10-256 atoms and 0-40 torsions (a seeded pool, sampled
 uniformly), each against one of four resident receptors (48^3, 64^3, 80^3,
 96^3 grids at 0.375 A, 10 + 2 maps).  Prints one JSON line: offered and
 completed jobs, evaluations/s over the busy period, and the p50/p99 of
 time-to-result (submission to results ready) and of queueing delay.
+--variant: the server's reduction (REDUCE_*; -1 = the context's default,
+the shuffle form).  --serial: afterwards the same jobs are docked one after
+another through the plain dock() call with the shuffle reduction, and the
+line adds their wall time, evaluations/s and the served/serial ratio of
+evaluations/s over wall time.
 """
 from __future__ import annotations
 
@@ -41,6 +46,8 @@ def main(argv=None):
     ap.add_argument("--max-active", type=int, default=0)
     ap.add_argument("--grids", default="48,64,80,96")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--serial", action="store_true")
     a = ap.parse_args(argv)
     P.load(build=True)
     w = synth.WORKLOADS["serving"]
@@ -55,7 +62,7 @@ def main(argv=None):
         pool.append(synth.make_ligand(90000 + k, na, w["n_type_maps"], nt))
     ctx = P.Context(0)
     rids = [ctx.upload_receptor_grids(r) for r in recs]
-    srv = P.Server(ctx, max_active_jobs=a.max_active)
+    srv = P.Server(ctx, max_active_jobs=a.max_active, reduce_variant=a.variant)
     # arrival times and job choices, all seeded
     n_jobs = rng.poisson(a.rate * a.duration)
     arrivals = np.sort(rng.uniform(0.0, a.duration, n_jobs))
@@ -82,7 +89,26 @@ def main(argv=None):
     queue = np.array([i["start_s"] - i["submit_s"] for i in done])
     evals = sum(i["evals"] for i in done)
     q = lambda v, p: float(np.percentile(v, p)) if len(v) else None
+    serial = None
+    if a.serial:
+        # the same jobs, one plain dock() call after another (shuffle reduction)
+        lig_ids, t_serial, ev_serial = {}, 0.0, 0
+        for k in range(n_jobs):
+            c = int(choice[k])
+            if c not in lig_ids:
+                lig_ids[c] = ctx.upload_ligand_torsion_tree(pool[c])
+            prm = P.adgb.dock_params(n_runs=a.runs, pop=a.pop, max_gens=gens,
+                                     max_evals=int(a.evals_per_run), ls_iters=a.ls_iters,
+                                     seed=a.seed * 1_000_000 + k, reduce_variant=P.REDUCE_SHFL)
+            t1 = time.perf_counter()
+            _, _, ev = ctx.dock(rids[recv[k]], lig_ids[c], prm)
+            t_serial += time.perf_counter() - t1
+            ev_serial += int(ev.sum())
+        serial = dict(wall_s=t_serial, evals=ev_serial, evals_per_s=ev_serial / t_serial,
+                      variant="shfl",
+                      served_over_serial=(evals / t_end) / (ev_serial / t_serial))
     print(json.dumps(dict(
+        variant=a.variant, serial=serial,
         rate_hz=a.rate, duration_s=a.duration, offered_jobs=int(n_jobs), completed_jobs=len(done),
         runs=a.runs, pop=a.pop, evals_per_run=a.evals_per_run, ls_iters=a.ls_iters,
         evals_total=int(evals), wall_s=t_end, submit_window_s=t_submitted,
