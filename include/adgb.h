@@ -530,7 +530,8 @@ int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
  * roofline's denominator): n_blocks x threads threads each run reps x 128
  * dependent operations in 8 independent chains.  kind 0: FP32 fused
  * multiply-add (2 flops each); 1: ex2.approx; 2: rsqrt.approx (special-
- * function unit).  out [n_blocks * threads] float32 receives a value per
+ * function unit); 3: packed FP32x2 fused multiply-add (two FMAs, 4 flops,
+ * an instruction).  out [n_blocks * threads] float32 receives a value per
  * thread.  threads: 32..256, a multiple of 32.  Errors: EINVAL, EDEVICE.
  */
 int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, float *out_dev,

@@ -416,7 +416,7 @@ class Context:
                                              _stream()))
 
     def alu_bench_dev(self, kind, n_blocks, threads, reps, out):
-        """ALU throughput probe (kind 0 FFMA, 1 ex2.approx, 2 rsqrt.approx)."""
+        """ALU throughput probe (kind 0 FFMA, 1 ex2.approx, 2 rsqrt.approx, 3 packed FFMA2)."""
         self._chk(self.lib.alu_bench_dev(self.h, kind, n_blocks, threads, reps, _ptr(out), _stream()))
 
     def ga_converged_dev(self, params, energy, converged):

@@ -1417,7 +1417,7 @@ int reduce4_bench_dev(adgb_ctx *c, int variant, const float *in_dev, int threads
 int alu_bench_dev(adgb_ctx *c, int kind, int n_blocks, int threads, int reps, float *out_dev,
                   adgb_stream stream) {
     if (!c) return ADGB_EINVAL;
-    if (kind < 0 || kind > 2 || n_blocks < 1 || threads < 32 || threads > 256 || threads % 32 ||
+    if (kind < 0 || kind > 3 || n_blocks < 1 || threads < 32 || threads > 256 || threads % 32 ||
         reps < 1 || !out_dev)
         return fail(c, ADGB_EINVAL, "alu_bench: bad arguments");
     DeviceGuard g(c->device);

@@ -183,6 +183,58 @@ __device__ __forceinline__ float pair_term(float4 xi, float4 xj, float4 pc, bool
     return evdw + eel + eds;
 }
 
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+
+// Two pair terms that share their first atom (a lane's pairs of two
+// rounds), the same formulas as pair_term with the adds, multiplies and
+// fused multiply-adds of both pairs in packed FP32x2 instructions (one
+// instruction, two IEEE round-to-nearest results); reciprocal square roots,
+// exponentials, the reciprocal, compares and selects per pair.  Returns the
+// two energies' sum; fa, fb = dE/dx_i of each pair.
+__device__ __forceinline__ float pair_term2(float3 xi, float3 xa, float3 xb, float4 pa, float4 pb,
+                                            bool hba, bool hbb, float3 &fa, float3 &fb) {
+    const float2 neg = f2s(-1.f);
+    const float2 dx = __ffma2_rn(f2(xa.x, xb.x), neg, f2s(xi.x));   // x_i - x_j, exact
+    const float2 dy = __ffma2_rn(f2(xa.y, xb.y), neg, f2s(xi.y));
+    const float2 dz = __ffma2_rn(f2(xa.z, xb.z), neg, f2s(xi.z));
+    const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+    const bool la = r2.x >= RMIN2, lb = r2.y >= RMIN2;
+    const float2 r2c = f2(fmaxf(r2.x, RMIN2), fmaxf(r2.y, RMIN2));
+    const float2 rinv = f2(rsqrtf(r2c.x), rsqrtf(r2c.y));
+    const float2 rc = __fmul2_rn(r2c, rinv);
+    const float2 r2i = __fmul2_rn(rinv, rinv);
+    const float2 r4i = __fmul2_rn(r2i, r2i);
+    const float2 r6i = __fmul2_rn(r4i, r2i);
+    const float2 r12i = __fmul2_rn(r6i, r6i);
+    const float2 r10i = __fmul2_rn(r6i, r4i);
+    const float2 rmi = f2(hba ? r10i.x : r6i.x, hbb ? r10i.y : r6i.y);
+    const float2 m = f2(hba ? 10.f : 6.f, hbb ? 10.f : 6.f);
+    const float2 t12 = __fmul2_rn(f2(pa.x, pb.x), r12i), tm = __fmul2_rn(f2(pa.y, pb.y), rmi);
+    const float2 evdw = __ffma2_rn(tm, neg, t12);
+    const float2 dvdw = __fmul2_rn(__ffma2_rn(m, tm, __fmul2_rn(f2s(-12.f), t12)), rinv);
+    const float2 xa_ = __fmul2_rn(f2s(-MS_LAMBDA * MS_B), rc);
+    const float2 ex = f2(__expf(xa_.x), __expf(xa_.y));
+    const float2 den = __ffma2_rn(f2s(MS_K), ex, f2s(1.f));
+    const float2 num = __ffma2_rn(f2s(MS_A), den, f2s(MS_B));
+    const float2 dn = __fmul2_rn(den, num);
+    const float2 rr = f2(__fdividef(1.f, dn.x), __fdividef(1.f, dn.y));
+    const float2 eel =
+        __fmul2_rn(__fmul2_rn(f2(pa.z, pb.z), rinv), __fmul2_rn(__fmul2_rn(den, den), rr));
+    const float2 del = __fmul2_rn(__fmul2_rn(eel, neg),
+                                  __ffma2_rn(f2s(MS_B * MS_K * MS_LAMBDA * MS_B),
+                                             __fmul2_rn(ex, rr), rinv));
+    const float2 xd = __fmul2_rn(r2, f2s(-HALF_INV_SIG2));
+    const float2 eds = __fmul2_rn(f2(pa.w, pb.w), f2(__expf(xd.x), __expf(xd.y)));
+    const float2 frr = __fmul2_rn(__fadd2_rn(dvdw, del), rinv);
+    const float2 ft = __ffma2_rn(eds, f2s(-INV_SIG2), f2(la ? frr.x : 0.f, lb ? frr.y : 0.f));
+    const float2 fx = __fmul2_rn(ft, dx), fy = __fmul2_rn(ft, dy), fz = __fmul2_rn(ft, dz);
+    fa = make_float3(fx.x, fy.x, fz.x);
+    fb = make_float3(fx.y, fy.y, fz.y);
+    const float2 e = __fadd2_rn(__fadd2_rn(evdw, eel), eds);
+    return e.x + e.y;
+}
+
 template <int TPP, int VAR>
 __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage, int group,
                                            int gt, Tc05Warp &tw) {
@@ -467,17 +519,15 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         if (rounds) {
             const uint32_t *rw = lig.rword + gt;
             const float4 *rc = lig.rconst + gt;
-            const float4 xi = make_float4(xo.x, xo.y, xo.z, 0.f);
-#pragma unroll 2
-            for (int r = 0; r < lig.n_rounds; r++) {
-                const uint32_t w = __ldg(rw + 32 * r);
-                const float4 pc = __ldg(rc + 32 * r);
-                const int pj = w & 31, s1 = (w >> 8) & 31, s2 = (w >> 16) & 31;
-                const float4 xj = make_float4(__shfl_sync(0xffffffffu, xo.x, pj),
-                                              __shfl_sync(0xffffffffu, xo.y, pj),
-                                              __shfl_sync(0xffffffffu, xo.z, pj), 0.f);
-                float3 f;
-                e_part += pair_term(xi, xj, pc, (w >> 24) & 1, f);
+            const int R = lig.n_rounds;
+            auto partner = [&](uint32_t w) {
+                const int pj = w & 31;
+                return make_float3(__shfl_sync(0xffffffffu, xo.x, pj),
+                                   __shfl_sync(0xffffffffu, xo.y, pj),
+                                   __shfl_sync(0xffffffffu, xo.z, pj));
+            };
+            auto settle = [&](uint32_t w, float3 f) {  // own force in, received forces out
+                const int s1 = (w >> 8) & 31, s2 = (w >> 16) & 31;
                 const float m1 = (w >> 25) & 1 ? 1.f : 0.f, m2 = (w >> 26) & 1 ? 1.f : 0.f;
                 go.x += f.x;
                 go.y += f.y;
@@ -488,6 +538,26 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                 go.x -= m2 * __shfl_sync(0xffffffffu, f.x, s2);
                 go.y -= m2 * __shfl_sync(0xffffffffu, f.y, s2);
                 go.z -= m2 * __shfl_sync(0xffffffffu, f.z, s2);
+            };
+            int r = 0;
+#pragma unroll 1
+            for (; r + 1 < R; r += 2) {  // two rounds at once, packed arithmetic
+                const uint32_t wa = __ldg(rw + 32 * r), wb = __ldg(rw + 32 * (r + 1));
+                const float4 pa = __ldg(rc + 32 * r), pb = __ldg(rc + 32 * (r + 1));
+                const float3 xa = partner(wa), xb = partner(wb);
+                float3 fa, fb;
+                e_part += pair_term2(xo, xa, xb, pa, pb, (wa >> 24) & 1, (wb >> 24) & 1, fa, fb);
+                settle(wa, fa);
+                settle(wb, fb);
+            }
+            if (r < R) {
+                const uint32_t w = __ldg(rw + 32 * r);
+                const float4 pc = __ldg(rc + 32 * r);
+                const float3 xj = partner(w);
+                float3 f;
+                e_part += pair_term(make_float4(xo.x, xo.y, xo.z, 0.f),
+                                    make_float4(xj.x, xj.y, xj.z, 0.f), pc, (w >> 24) & 1, f);
+                settle(w, f);
             }
         }
 

@@ -357,17 +357,34 @@ __global__ void __launch_bounds__(256) alu_kernel(float *out, int reps, float b,
     float a[8];
 #pragma unroll
     for (int k = 0; k < 8; k++) a[k] = (float)(threadIdx.x + k) * 1e-3f;
-    for (int r = 0; r < reps; r++) {
+    if constexpr (KIND == 3) {
+        // packed FP32 pairs: one instruction, two fused multiply-adds
+        float2 p[8];
 #pragma unroll
-        for (int u = 0; u < 16; u++) {
+        for (int k = 0; k < 8; k++) p[k] = make_float2(a[k], a[k] + 0.5f);
+        const float2 b2 = make_float2(b, b), c2 = make_float2(c, c);
+        for (int r = 0; r < reps; r++) {
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
-                if constexpr (KIND == 0) {
-                    a[k] = fmaf(a[k], b, c);
-                } else if constexpr (KIND == 1) {
-                    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(-a[k]));
-                } else {
-                    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k] + c));
+            for (int u = 0; u < 16; u++) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) p[k] = __ffma2_rn(p[k], b2, c2);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) a[k] = p[k].x + p[k].y;
+    } else {
+        for (int r = 0; r < reps; r++) {
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+#pragma unroll
+                for (int k = 0; k < 8; k++) {
+                    if constexpr (KIND == 0) {
+                        a[k] = fmaf(a[k], b, c);
+                    } else if constexpr (KIND == 1) {
+                        asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(-a[k]));
+                    } else {
+                        asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(a[k]) : "f"(a[k] + c));
+                    }
                 }
             }
         }
@@ -384,6 +401,7 @@ cudaError_t launch_alu_bench(int kind, int n_blocks, int threads, int reps, floa
         case 0: alu_kernel<0><<<n_blocks, threads, 0, s>>>(out, reps, 0.999f, 1e-3f); break;
         case 1: alu_kernel<1><<<n_blocks, threads, 0, s>>>(out, reps, 0.f, 0.f); break;
         case 2: alu_kernel<2><<<n_blocks, threads, 0, s>>>(out, reps, 0.f, 1.f); break;
+        case 3: alu_kernel<3><<<n_blocks, threads, 0, s>>>(out, reps, 0.999f, 1e-3f); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

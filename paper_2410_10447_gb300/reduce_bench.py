@@ -29,7 +29,7 @@ def alu_peaks(ctx, torch, waves=8, threads=256, reps=2000):
     nb = props.multi_processor_count * waves
     out = torch.empty(nb * threads, device="cuda")
     res = {"sms": props.multi_processor_count}
-    for kind, name in ((0, "ffma"), (1, "ex2"), (2, "rsqrt")):
+    for kind, name in ((0, "ffma"), (1, "ex2"), (2, "rsqrt"), (3, "ffma2")):
         ctx.alu_bench_dev(kind, nb, threads, 10, out)
         ms = []
         for _ in range(3):
@@ -43,6 +43,8 @@ def alu_peaks(ctx, torch, waves=8, threads=256, reps=2000):
         rate = ops / (min(ms) / 1e3)
         if kind == 0:
             res["ffma_tflops"] = 2 * rate / 1e12
+        elif kind == 3:
+            res["ffma2_tflops"] = 4 * rate / 1e12
         else:
             res[name + "_gops"] = rate / 1e9
     return res

@@ -390,10 +390,10 @@ def test_alu_probe(pkg, torch):
     bad shapes (it measures the roofline's denominator)."""
     ctx = make_ctx(pkg)
     out = torch.empty(4 * 64, device="cuda")
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3):
         ctx.alu_bench_dev(kind, 4, 64, 3, out)
         assert torch.isfinite(out).all()
-    for bad in ((3, 4, 64, 3), (0, 4, 48, 3), (0, 0, 64, 3), (0, 4, 512, 3)):
+    for bad in ((4, 4, 64, 3), (0, 4, 48, 3), (0, 0, 64, 3), (0, 4, 512, 3)):
         with pytest.raises(pkg.AdgbError):
             ctx.alu_bench_dev(*bad, out)
     ctx.close()
