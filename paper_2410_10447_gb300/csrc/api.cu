@@ -649,10 +649,11 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
 EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     EvalCfg cfg;
     cfg.variant = variant;
-    // one warp a genotype up to 32 atoms (one atom a lane), else 128 threads a
-    // genotype: measured on 3000 genotypes, 128 x 1 beats 64 x 2 and 32 x 4 for
-    // every size from 40 to 192 atoms (by 7-39% over 64 x 2)
-    const int by_size = L.n_atoms <= 32 ? 32 : 128;
+    // one warp a genotype up to 32 atoms (one atom a lane, matching rounds),
+    // two warps up to 48, else 128 threads a genotype: measured on 3000
+    // genotypes, 64 x 2 beats 128 x 1 by 13-16% at 40 and 48 atoms, 128 x 1
+    // beats 64 x 2 by 6-40% from 64 to 192 atoms
+    const int by_size = L.n_atoms <= 32 ? 32 : (L.n_atoms <= 48 ? 64 : 128);
     cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : by_size;
     int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
     while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;

@@ -184,20 +184,21 @@ __device__ __forceinline__ float pair_term(float4 xi, float4 xj, float4 pc, bool
 }
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float3 xyz3(float4 a) { return make_float3(a.x, a.y, a.z); }
 __device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
 
-// Two pair terms that share their first atom (a lane's pairs of two
-// rounds), the same formulas as pair_term with the adds, multiplies and
-// fused multiply-adds of both pairs in packed FP32x2 instructions (one
-// instruction, two IEEE round-to-nearest results); reciprocal square roots,
-// exponentials, the reciprocal, compares and selects per pair.  Returns the
-// two energies' sum; fa, fb = dE/dx_i of each pair.
-__device__ __forceinline__ float pair_term2(float3 xi, float3 xa, float3 xb, float4 pa, float4 pb,
-                                            bool hba, bool hbb, float3 &fa, float3 &fb) {
+// Two pair terms (a, b), the same formulas as pair_term with the adds,
+// multiplies and fused multiply-adds of both pairs in packed FP32x2
+// instructions (one instruction, two IEEE round-to-nearest results);
+// reciprocal square roots, exponentials, the reciprocal, compares and
+// selects per pair.  Returns the two energies' sum; fa, fb = dE/dx_i of each
+// pair (its first atom; the second gets the negative).
+__device__ __forceinline__ float pair_term2(float3 ia, float3 ib, float3 xa, float3 xb, float4 pa,
+                                            float4 pb, bool hba, bool hbb, float3 &fa, float3 &fb) {
     const float2 neg = f2s(-1.f);
-    const float2 dx = __ffma2_rn(f2(xa.x, xb.x), neg, f2s(xi.x));   // x_i - x_j, exact
-    const float2 dy = __ffma2_rn(f2(xa.y, xb.y), neg, f2s(xi.y));
-    const float2 dz = __ffma2_rn(f2(xa.z, xb.z), neg, f2s(xi.z));
+    const float2 dx = __ffma2_rn(f2(xa.x, xb.x), neg, f2(ia.x, ib.x));   // x_i - x_j, exact
+    const float2 dy = __ffma2_rn(f2(xa.y, xb.y), neg, f2(ia.y, ib.y));
+    const float2 dz = __ffma2_rn(f2(xa.z, xb.z), neg, f2(ia.z, ib.z));
     const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
     const bool la = r2.x >= RMIN2, lb = r2.y >= RMIN2;
     const float2 r2c = f2(fmaxf(r2.x, RMIN2), fmaxf(r2.y, RMIN2));
@@ -540,13 +541,14 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
                 go.z -= m2 * __shfl_sync(0xffffffffu, f.z, s2);
             };
             int r = 0;
-#pragma unroll 1
+#pragma unroll 2
             for (; r + 1 < R; r += 2) {  // two rounds at once, packed arithmetic
                 const uint32_t wa = __ldg(rw + 32 * r), wb = __ldg(rw + 32 * (r + 1));
                 const float4 pa = __ldg(rc + 32 * r), pb = __ldg(rc + 32 * (r + 1));
                 const float3 xa = partner(wa), xb = partner(wb);
                 float3 fa, fb;
-                e_part += pair_term2(xo, xa, xb, pa, pb, (wa >> 24) & 1, (wb >> 24) & 1, fa, fb);
+                e_part += pair_term2(xo, xo, xa, xb, pa, pb, (wa >> 24) & 1, (wb >> 24) & 1, fa,
+                                     fb);
                 settle(wa, fa);
                 settle(wb, fb);
             }
@@ -568,8 +570,18 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         //    the same word.
         for (int q = 0; q < (rounds ? 0 : lig.n_chunks); q++) {
             const int c0 = q * PAIR_CHUNK, c1 = min(NP, c0 + PAIR_CHUNK);
-#pragma unroll 2
-            for (int p = c0 + gt; p < c1; p += TPP) {
+            int p = c0 + gt;
+            for (; p + TPP < c1; p += 2 * TPP) {  // pairs p and p + TPP, packed arithmetic
+                const uint32_t pa = prs[p], pb = prs[p + TPP];
+                float3 fa, fb;
+                e_part += pair_term2(xyz3(xyz[pa & 255]), xyz3(xyz[pb & 255]),
+                                     xyz3(xyz[(pa >> 8) & 255]), xyz3(xyz[(pb >> 8) & 255]),
+                                     __ldg(pconst + p), __ldg(pconst + p + TPP), (pa >> 24) & 1,
+                                     (pb >> 24) & 1, fa, fb);
+                fbuf[p - c0] = make_float4(fa.x, fa.y, fa.z, 0.f);
+                fbuf[p + TPP - c0] = make_float4(fb.x, fb.y, fb.z, 0.f);
+            }
+            if (p < c1) {
                 const uint32_t pr = prs[p];
                 const int i = pr & 255, j = (pr >> 8) & 255;
                 float3 f;
@@ -910,8 +922,16 @@ __device__ __forceinline__ void search_pose_sw(unsigned char *sm, const SmemLayo
             e_part += inter_atom(rec, s_type[i], r4.w, x, gi);
         }
         group_sync<TPP>(group);
-#pragma unroll 2
-        for (int p = gt; p < NP; p += TPP) {
+        int p = gt;
+        for (; p + TPP < NP; p += 2 * TPP) {  // pairs p and p + TPP, packed arithmetic
+            const uint32_t pa = prs[p], pb = prs[p + TPP];
+            float3 fa, fb;
+            e_part += pair_term2(xyz3(xyz[pa & 255]), xyz3(xyz[pb & 255]),
+                                 xyz3(xyz[(pa >> 8) & 255]), xyz3(xyz[(pb >> 8) & 255]),
+                                 __ldg(pconst + p), __ldg(pconst + p + TPP), (pa >> 24) & 1,
+                                 (pb >> 24) & 1, fa, fb);
+        }
+        if (p < NP) {
             const uint32_t pr = prs[p];
             float3 f;
             e_part += pair_term(xyz[pr & 255], xyz[(pr >> 8) & 255], __ldg(pconst + p),
