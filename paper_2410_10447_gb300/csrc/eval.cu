@@ -236,13 +236,19 @@ __device__ __forceinline__ float pair_term2(float3 ia, float3 ib, float3 xa, flo
     return e.x + e.y;
 }
 
-template <int TPP, int VAR>
+// ISSUED: the tcgen05 variant's MMAs were already issued (tc05_issue) and
+// only the wait and the TMEM load remain.
+template <int TPP, int VAR, bool ISSUED = false>
 __device__ __forceinline__ void group_sum8(float v[8], float *red, float *stage, int group,
                                            int gt, Tc05Warp &tw) {
-    if constexpr (VAR == ADGB_REDUCE_TCGEN05)
-        warp_sum8_tc05(v, tw);
-    else
+    if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
+        if constexpr (ISSUED)
+            tc05_finish(v, tw);
+        else
+            warp_sum8_tc05(v, tw);
+    } else {
         warp_sum8<VAR>(v, stage);
+    }
     if constexpr (TPP > 32) {
         const int w = gt >> 5;
         if ((gt & 31) == 0) {
@@ -629,6 +635,9 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
             v[6] += c.z;
             if (N > 32) tq[i] = make_float4(c.x, c.y, c.z, 0.f);
         }
+        // the tensor-core reduction of the partials runs while the torsion
+        // scans below are computed
+        if constexpr (VAR == ADGB_REDUCE_TCGEN05) tc05_issue(v, tw);
         if (N <= 32) {
             // one atom per lane of the group's first warp; atoms are in
             // depth-first order, so a torsion's moving set [s, e) sums to
@@ -737,7 +746,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         }
 
         // 5. one reduce-and-broadcast of the 8-vector
-        group_sum8<TPP, VAR>(v, red, stage, group, gt, tw);
+        group_sum8<TPP, VAR, true>(v, red, stage, group, gt, tw);
         group_sync<TPP>(group);  // torsion gradients visible
 
         // 6. gene gradient, best tracking, ADADELTA

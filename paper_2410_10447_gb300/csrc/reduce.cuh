@@ -209,13 +209,14 @@ struct Tc05Warp {
 
 constexpr int TC05_WAIT_LIMIT = 1 << 16;   // mbarrier probes, each suspending up to a time limit
 
-__device__ __forceinline__ void warp_sum8_tc05(float v[8], Tc05Warp &t) {
+// The tcgen05 reduction in two halves, so that independent work can run
+// while the MMAs are in flight: tc05_issue stages the warp's partials (TF32
+// hi and lo terms) and has one lane issue the MMAs and commit them to the
+// warp's mbarrier; tc05_finish waits (bounded) and loads the totals from
+// TMEM.  v is not changed by tc05_issue.
+__device__ __forceinline__ void tc05_issue(const float v[8], Tc05Warp &t) {
     const int lane = threadIdx.x & 31, cq = lane >> 2;
-    if (!t.ok) {
-#pragma unroll
-        for (int c = 0; c < 8; c++) v[c] = __int_as_float(0x7fc00000);
-        return;
-    }
+    if (!t.ok) return;
     unsigned char *mine = t.b + (lane & 3) * 4;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
@@ -236,6 +237,14 @@ __device__ __forceinline__ void warp_sum8_tc05(float v[8], Tc05Warp &t) {
                               s > 0);
         tc05::commit(t.mbar);
     }
+}
+
+__device__ __forceinline__ void tc05_finish(float v[8], Tc05Warp &t) {
+    if (!t.ok) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) v[c] = __int_as_float(0x7fc00000);
+        return;
+    }
     const bool done = __all_sync(0xffffffffu, tc05::mbar_wait(t.mbar, t.phase & 1, TC05_WAIT_LIMIT));
     t.phase++;
     if (!done) {
@@ -250,6 +259,11 @@ __device__ __forceinline__ void warp_sum8_tc05(float v[8], Tc05Warp &t) {
 #pragma unroll
     for (int c = 0; c < 8; c++) v[c] = d[c] + d[8 + c];
     tc05::fence_before();   // these TMEM reads precede the warp's next MMA
+}
+
+__device__ __forceinline__ void warp_sum8_tc05(float v[8], Tc05Warp &t) {
+    tc05_issue(v, t);
+    tc05_finish(v, t);
 }
 
 }  // namespace adgb
