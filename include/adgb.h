@@ -81,10 +81,9 @@ typedef struct {
     int threads_per_pose;  /* 0 = pick per ligand; else 32, 64 or 128 */
     int poses_per_block;   /* 0 = pick per ligand; else 1..8 (at most 128 threads a block) */
     int reduce_variant;    /* default ADGB_REDUCE_* for calls that do not say */
-    int pair_rounds;       /* intramolecular pairs of ligands of at most 32 atoms scored one
-                              warp a genotype: 0 = matching rounds (ligand_pair_rounds;
-                              measured 1.05-1.16x faster for 8-32 atoms), 1 = per-pair
-                              force buffer and incidence lists, as for larger ligands */
+    int pair_rounds;       /* intramolecular pairs: 0 = matching rounds (ligand_pair_rounds;
+                              the default, faster at every size measured), 1 = per-pair
+                              force buffer and incidence lists */
 } adgb_options;
 
 /* Receptor grid (Sec. 2.1: the receptor is fixed; its interaction with a
@@ -169,23 +168,27 @@ int validate_ligand_torsion_tree(const adgb_ligand_desc *lig, char *msg, int msg
 
 /*
  * ligand_pair_rounds - the host-side schedule of the intramolecular pairs
- * (Sec. 2.1, Eq. 1's pair sum) that upload_ligand_torsion_tree builds for
- * a ligand of at most 32 atoms, without a context or a device.  Lane a of
- * the warp that scores a genotype owns internal atom a; in round r lane a
- * computes at most one pair with atom a first and receives the reaction
- * forces of at most two pairs with atom a second.  The paper has no
- * counterpart (its block-wide kernel sums forces through shared memory).
- * n_rounds: rounds (0 above 32 atoms or without pairs), normally
- * max(ceil(pairs / atoms), ceil(max_degree / 3)); max_degree: the largest
- * number of pairs an atom is in.  words [words_cap]: if words_cap >=
- * 32 * n_rounds, word of lane a in round r at [32 r + a]: partner lane
- * (bits 0-4; a itself without a pair), lanes whose pairs' reaction forces
- * lane a receives (bits 8-12 and 16-20), H-bond flag (bit 24), whether each
- * of the two receive slots is used (bits 25, 26).  perm [n_atoms] (may be
- * NULL): caller's index of internal atom a.  Errors: EINVAL as
- * validate_ligand_torsion_tree, or words_cap too small for a non-NULL words.
+ * (Sec. 2.1, Eq. 1's pair sum) that upload_ligand_torsion_tree builds,
+ * without a context or a device: for ligands of at most 32 atoms and of more
+ * than 112 (between, the per-pair force buffer is faster and no rounds are
+ * built).  Lane a owns internal atom a: lanes = 32 up to 32 atoms (one warp
+ * a genotype; positions and forces move by warp shuffles), else the atoms
+ * rounded up to 32 (128 threads a genotype with two atoms each at most;
+ * forces move through per-round slots in shared memory).  In round r lane a computes at most one pair with atom
+ * a first and receives the reaction forces of at most two pairs with atom a
+ * second.  The paper has no counterpart (its block-wide kernel sums forces
+ * through shared memory).  n_rounds: rounds (0 without pairs or rounds),
+ * normally max(ceil(pairs / atoms), ceil(max_degree / 3)); max_degree: the
+ * largest number of pairs an atom is in.  words [words_cap]: if words_cap >=
+ * lanes * n_rounds, word of lane a in round r at [lanes r + a]: partner lane
+ * (bits 0-7; a itself without a pair, 0 for a lane past the last atom), lanes
+ * whose pairs' reaction forces lane a receives (bits 8-15 and 16-23), H-bond
+ * flag (bit 24), whether each of the two receive slots is used (bits 25,
+ * 26).  perm [n_atoms] (may be NULL): caller's index of internal atom a.
+ * Errors: EINVAL as validate_ligand_torsion_tree, or words_cap too small for
+ * a non-NULL words.
  */
-int ligand_pair_rounds(const adgb_ligand_desc *lig, int *n_rounds, int *max_degree,
+int ligand_pair_rounds(const adgb_ligand_desc *lig, int *n_rounds, int *lanes, int *max_degree,
                        unsigned int *words, int words_cap, int *perm);
 
 /*

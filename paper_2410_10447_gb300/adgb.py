@@ -161,7 +161,7 @@ def load(build: bool = False):
     L.release_ligand.argtypes = [vp, C.c_int]
     L.validate_ligand_torsion_tree.argtypes = [C.POINTER(_Ligand), C.c_char_p, C.c_int]
     L.ligand_pair_rounds.argtypes = [C.POINTER(_Ligand), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                     vp, C.c_int, vp]
+                                     C.POINTER(C.c_int), vp, C.c_int, vp]
     L.pose_coords_dev.argtypes = [vp, C.c_int, vp, C.c_int, vp, vp]
     L.pose_coords.argtypes = [vp, C.c_int, vp, C.c_int, vp]
     L.score_poses_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, vp, vp, C.c_int, vp]
@@ -260,22 +260,21 @@ def validate_ligand_torsion_tree(lig: dict):
 
 
 def ligand_pair_rounds(lig: dict):
-    """(n_rounds, max_degree, words [n_rounds][32] uint32, perm [n_atoms]) of
-    the pair schedule the library builds for ligands of at most 32 atoms;
-    needs no GPU."""
+    """(n_rounds, lanes, max_degree, words [n_rounds][lanes] uint32, perm
+    [n_atoms]) of the pair schedule the library builds; needs no GPU."""
     d, _keep = _ligand_desc(lig)
-    nr, md = C.c_int(0), C.c_int(0)
+    nr, nl, md = C.c_int(0), C.c_int(0), C.c_int(0)
     L = load()
-    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(md), None, 0, None)
+    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(nl), C.byref(md), None, 0, None)
     if rc != ADGB_OK:
         raise AdgbError(rc, "ligand_pair_rounds")
-    words = np.zeros((max(nr.value, 1), 32), np.uint32)
+    words = np.zeros((max(nr.value, 1), max(nl.value, 1)), np.uint32)
     perm = np.zeros(int(lig["n_atoms"]), np.int32)
-    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(md), words.ctypes.data,
-                              words.size, perm.ctypes.data)
+    rc = L.ligand_pair_rounds(C.byref(d), C.byref(nr), C.byref(nl), C.byref(md),
+                              words.ctypes.data, words.size, perm.ctypes.data)
     if rc != ADGB_OK:
         raise AdgbError(rc, "ligand_pair_rounds")
-    return nr.value, md.value, words[:nr.value], perm
+    return nr.value, nl.value, md.value, words[:nr.value], perm
 
 
 class Context:

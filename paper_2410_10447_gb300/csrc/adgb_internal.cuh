@@ -54,12 +54,14 @@ struct LigDev {
     const uint16_t *inc;      // [2 Np] (pair index - q*PAIR_CHUNK) << 1 | (atom is the pair's
                               // second atom), ordered by chunk and atom (within an atom's
                               // list, in the order that spreads reads over the banks)
-    int n_rounds;             // matching rounds of the pair list (0 above 32 atoms): in a
-                              // round lane a computes at most one pair with atom a first
+    int n_rounds, r_lanes;    // matching rounds of the pair list and lanes a round (32 up to
+                              // 32 atoms, else the atoms rounded up to 32; 0 rounds: none):
+                              // in a round lane a computes at most one pair with atom a first
                               // and receives the forces of at most two pairs with atom a second
-    const uint32_t *rword;    // [n_rounds][32] partner lane | force-source lanes << 8, << 16 |
-                              // hb << 24 | source used << 25, << 26
-    const float4 *rconst;     // [n_rounds][32] the pair's constants as in pconst (zeros: no pair)
+    const uint32_t *rword;    // [n_rounds][r_lanes] partner lane | force-source lanes << 8,
+                              // << 16 | hb << 24 | source used << 25, << 26
+    const float4 *rconst;     // [n_rounds][r_lanes] the pair's constants as in pconst (zeros:
+                              // no pair)
     // the caller's per-type parameters, kept for the FP64 rescoring
     const float *t_R, *t_eps, *t_vol, *t_sol;
     const int *t_hb;
@@ -138,7 +140,11 @@ struct SmemLayout {
         p_sc = q;    q = al16(q + 8 * (ADGB_MAX_TORS + 4));
         p_red = q;   q = al16(q + 4 * 8 * warps_per_pose);
         p_stage = q; q = al16(q + (mma_stage ? 4 * 32 * 12 * warps_per_pose : 0));
+        // pairs of a force-buffer chunk; at least a round's slots for the
+        // block form of the matching rounds (one float4 a lane)
         chunk = ch > 0 ? ch : 1;
+        const int lanes = N <= 32 ? 32 : (N + 31) / 32 * 32;
+        if (chunk < lanes) chunk = lanes;
         p_force = q; q = al16(q + 16 * chunk);
         p_tq = q;    q = al16(q + (N > 32 ? 16 * N : 0));
         p_seg = q;   q = al16(q + (N > 32 ? 4 * 8 * ((N + 31) / 32) : 0));

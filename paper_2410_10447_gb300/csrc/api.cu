@@ -159,19 +159,22 @@ struct HostLigand {
     std::vector<float4> pconst;
     std::vector<int> inc_off;
     std::vector<uint16_t> inc;
-    int R = 0;                       // matching rounds (ligands of at most 32 atoms)
-    std::vector<uint32_t> rword;     // [R][32]
-    std::vector<float4> rconst;      // [R][32]
+    int R = 0, VP = 0;               // matching rounds, lanes a round
+    std::vector<uint32_t> rword;     // [R][VP]
+    std::vector<float4> rconst;      // [R][VP]
     std::vector<float> tR, teps, tvol, tsol;
     std::vector<int> thb;
     int max_type = 0;
 };
 
-// Matching rounds of the pair list for ligands of at most 32 atoms, where lane
-// a of a warp owns atom a.  A round gives every lane at most one pair to
-// compute (its atom first) and at most two pairs whose reaction force it
-// receives (its atom second), so that partner positions and reaction forces
-// travel by warp shuffles and no force buffer is needed.  Rounds:
+// Matching rounds of the pair list: lane a owns atom a (lanes: 32 for
+// ligands of at most 32 atoms, one warp a genotype, partner positions and
+// reaction forces by warp shuffles; else the atoms rounded up to 32, a block
+// of threads with at most two atoms each, forces through per-round slots in
+// shared memory).  A round gives every lane at most one pair to compute (its
+// atom first) and at most two pairs whose reaction force it receives (its
+// atom second), so that no per-pair force buffer or incidence list is
+// needed.  Rounds:
 // R = max(ceil(pairs / atoms), ceil(max degree / 3)), the least for which
 // an atom of the largest degree fits (one out, two in a round) and the
 // atoms' lanes hold every pair; R grows only if no orientation below fits.
@@ -188,11 +191,14 @@ struct HostLigand {
 //      colours (Konig's theorem): a colour a free at the tail and b free at
 //      the slot; if a is taken at the slot, swap a and b along the
 //      alternating path that starts there.  Colour = round.
-// Word of lane l in round r: partner lane (bits 0-4; l itself without a
-// pair), source lanes of the two received forces (bits 8-12 and 16-20), hb
-// flag (bit 24), whether each receive slot is used (bits 25 and 26).  A lane
-// without a pair has all-zero constants, which make the pair term exactly
-// zero.
+// Word of lane l in round r: partner lane (bits 0-7; l itself without a
+// pair, atom 0 for a lane past the last atom, so that every read is of a
+// real atom), source lanes of the two received forces (bits 8-15 and 16-23),
+// hb flag (bit 24), whether each receive slot is used (bits 25 and 26).  A
+// lane without a pair has all-zero constants, which make the pair term
+// exactly zero.
+constexpr int ROUNDS_BLOCK_MIN_ATOMS = 112;
+
 void build_rounds(HostLigand &h) {
     const int N = h.N, NP = h.NP, X = N;  // X: the extra vertex
     std::vector<int> ea(NP), eb(NP), deg(N, 0);
@@ -239,14 +245,14 @@ void build_rounds(HostLigand &h) {
     }
     const int maxdeg = *std::max_element(deg.begin(), deg.end());
     int R = std::max((NP + N - 1) / N, (maxdeg + 2) / 3);
-    std::vector<int> outd(N);
-    auto count_out = [&]() {
-        std::fill(outd.begin(), outd.end(), 0);
-        for (int p = 0; p < NP; p++) outd[tail[p]]++;
+    std::vector<std::vector<int>> outs(N);  // edges leaving each atom
+    auto rebuild_out = [&]() {
+        for (auto &o : outs) o.clear();
+        for (int p = 0; p < NP; p++) outs[tail[p]].push_back(p);
     };
-    count_out();
+    rebuild_out();
     for (int u = 0; u < N; u++) {
-        while (outd[u] > R) {
+        while ((int)outs[u].size() > R) {
             // breadth-first search along out-edges for an atom below R
             std::vector<int> via(N, -1);
             std::vector<char> seen(N, 0);
@@ -254,13 +260,16 @@ void build_rounds(HostLigand &h) {
             seen[u] = 1;
             int found = -1;
             for (size_t qi = 0; qi < queue.size() && found < 0; qi++) {
-                const int x = queue[qi];
-                for (int p = 0; p < NP && found < 0; p++) {
-                    if (tail[p] != x || seen[head[p]]) continue;
-                    seen[head[p]] = 1;
-                    via[head[p]] = p;
-                    if (outd[head[p]] < R) found = head[p];
-                    else queue.push_back(head[p]);
+                for (int p : outs[queue[qi]]) {
+                    const int y = head[p];
+                    if (seen[y]) continue;
+                    seen[y] = 1;
+                    via[y] = p;
+                    if ((int)outs[y].size() < R) {
+                        found = y;
+                        break;
+                    }
+                    queue.push_back(y);
                 }
             }
             if (found < 0) {  // every atom reachable from u is full: widen
@@ -273,7 +282,7 @@ void build_rounds(HostLigand &h) {
                 std::swap(tail[p], head[p]);
                 x = t;
             }
-            count_out();
+            rebuild_out();
         }
     }
     // receive slots: slot 2v + k, k = 0, 1; an atom's in-edges split in halves
@@ -319,26 +328,28 @@ void build_rounds(HostLigand &h) {
         at_t[(size_t)u * R + a] = p;
         at_s[(size_t)q * R + a] = p;
     }
+    const int VP = N <= 32 ? 32 : (N + 31) / 32 * 32;
     h.R = R;
-    h.rword.assign((size_t)R * 32, 0);
-    h.rconst.assign((size_t)R * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    h.VP = VP;
+    h.rword.assign((size_t)R * VP, 0);
+    h.rconst.assign((size_t)R * VP, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int r = 0; r < R; r++) {
-        uint32_t *wd = &h.rword[(size_t)r * 32];
-        for (int l = 0; l < 32; l++) {
-            uint32_t w = (uint32_t)l | (uint32_t)l << 8 | (uint32_t)l << 16;
+        uint32_t *wd = &h.rword[(size_t)r * VP];
+        for (int l = 0; l < VP; l++) {
+            uint32_t w = (uint32_t)(l < N ? l : 0) | (uint32_t)l << 8 | (uint32_t)l << 16;
             if (l < N) {
                 const int e = at_t[(size_t)l * R + r];
                 if (e >= 0) {
                     // lane l computes the pair with its own atom first: the
                     // pair term is symmetric (swapping the atoms negates dx,
                     // dy, dz exactly and hence the force)
-                    w = (w & ~31u) | (uint32_t)head[e] | ((h.pairs[e] >> 24) & 1u) << 24;
-                    h.rconst[(size_t)r * 32 + l] = h.pconst[e];
+                    w = (w & ~255u) | (uint32_t)head[e] | ((h.pairs[e] >> 24) & 1u) << 24;
+                    h.rconst[(size_t)r * VP + l] = h.pconst[e];
                 }
                 for (int k = 0; k < 2; k++) {
                     const int f = at_s[(size_t)(2 * l + k) * R + r];
                     if (f >= 0)
-                        w = (w & ~(31u << (8 + 8 * k))) | (uint32_t)tail[f] << (8 + 8 * k) |
+                        w = (w & ~(255u << (8 + 8 * k))) | (uint32_t)tail[f] << (8 + 8 * k) |
                             1u << (25 + k);
                 }
             }
@@ -642,7 +653,12 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
         const double ds = (double)h.sv[i].x * h.sv[j].y + (double)h.sv[j].x * h.sv[i].y;
         h.pconst[p] = make_float4(ab.x, ab.y, (float)qq, (float)ds);
     }
-    if (N <= 32 && NP > 0) build_rounds(h);
+    // matching rounds where they were measured faster than the force buffer
+    // (3000 genotypes, local search): up to 32 atoms (one warp, 1.12-1.28x)
+    // and above 112 (two atoms a thread of 128: 1.1x at 128 atoms, 1.3x at
+    // 192, 1.5x at 256); between, the rounds' idle lanes cost more than the
+    // owner gather they save
+    if (NP > 0 && (N <= 32 || N > ROUNDS_BLOCK_MIN_ATOMS)) build_rounds(h);
     return ADGB_OK;
 }
 
@@ -650,10 +666,11 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     EvalCfg cfg;
     cfg.variant = variant;
     // one warp a genotype up to 32 atoms (one atom a lane, matching rounds),
-    // two warps up to 48, else 128 threads a genotype: measured on 3000
-    // genotypes, 64 x 2 beats 128 x 1 by 13-16% at 40 and 48 atoms, 128 x 1
-    // beats 64 x 2 by 6-40% from 64 to 192 atoms
-    const int by_size = L.n_atoms <= 32 ? 32 : (L.n_atoms <= 48 ? 64 : 128);
+    // two warps up to 56, else 128 threads a genotype: measured on 3000
+    // genotypes, 64 x 2 beats 128 x 1 by 10-17% from 40 to 56 atoms, 128 x 1
+    // beats 64 x 2 from 64 atoms on (by 10% at 64, 15-20% at 80-128, more
+    // with the matching rounds above 112)
+    const int by_size = L.n_atoms <= 32 ? 32 : (L.n_atoms <= 56 ? 64 : 128);
     cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : by_size;
     int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
     while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;
@@ -700,7 +717,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_round
     HostLigand h;
     int rc = build_ligand(err, d, h);
     if (rc) return rc;
-    if (!use_pair_rounds(h, pair_rounds)) h.R = 0;
+    if (!use_pair_rounds(h, pair_rounds)) h.R = h.VP = 0;
     const int N = h.N, T = h.T, NP = h.NP, NT = d->n_types;
     const int Tz = T > 0 ? T : 1, NPz = NP > 0 ? NP : 1;
     size_t off = 0;
@@ -711,8 +728,8 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_round
     const size_t o_pconst = take(16 * NPz);
     const int NCH = (NP + PAIR_CHUNK - 1) / PAIR_CHUNK;
     const size_t o_incoff = take(4 * (size_t)(NCH > 0 ? NCH : 1) * (N + 1)), o_inc = take(2 * 2 * (size_t)NPz);
-    const int Rz = h.R > 0 ? h.R : 1;
-    const size_t o_rword = take(4 * 32 * (size_t)Rz), o_rconst = take(16 * 32 * (size_t)Rz);
+    const size_t RVz = h.R > 0 ? (size_t)h.R * h.VP : 1;
+    const size_t o_rword = take(4 * RVz), o_rconst = take(16 * RVz);
     const size_t o_tR = take(4 * NT), o_teps = take(4 * NT), o_tvol = take(4 * NT),
                  o_tsol = take(4 * NT), o_thb = take(4 * NT);
     std::vector<unsigned char> &buf = out.bytes;
@@ -734,8 +751,8 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_round
     if (NCH) memcpy(&buf[o_incoff], h.inc_off.data(), 4 * (size_t)NCH * (N + 1));
     if (NP) memcpy(&buf[o_inc], h.inc.data(), 2 * 2 * (size_t)NP);
     if (h.R) {
-        memcpy(&buf[o_rword], h.rword.data(), 4 * 32 * (size_t)h.R);
-        memcpy(&buf[o_rconst], h.rconst.data(), 16 * 32 * (size_t)h.R);
+        memcpy(&buf[o_rword], h.rword.data(), 4 * (size_t)h.R * h.VP);
+        memcpy(&buf[o_rconst], h.rconst.data(), 16 * (size_t)h.R * h.VP);
     }
     memcpy(&buf[o_tR], h.tR.data(), 4 * NT);
     memcpy(&buf[o_teps], h.teps.data(), 4 * NT);
@@ -749,6 +766,7 @@ int make_ligand_blob(std::string *err, const adgb_ligand_desc *d, int pair_round
     v.n_types = NT;
     v.n_chunks = NCH;
     v.n_rounds = h.R;
+    v.r_lanes = h.R ? h.VP : 0;
     // offsets travel in the pointer fields until bind_ligand relocates them
     auto at = [](size_t o) { return reinterpret_cast<const unsigned char *>((uintptr_t)o); };
     v.ref = reinterpret_cast<const float4 *>(at(o_ref));
@@ -1024,7 +1042,7 @@ int validate_ligand_torsion_tree(const adgb_ligand_desc *d, char *msg, int msg_l
     return rc;
 }
 
-int ligand_pair_rounds(const adgb_ligand_desc *d, int *n_rounds, int *max_degree,
+int ligand_pair_rounds(const adgb_ligand_desc *d, int *n_rounds, int *lanes, int *max_degree,
                        unsigned int *words, int words_cap, int *perm) {
     std::string err;
     HostLigand h;
@@ -1036,9 +1054,10 @@ int ligand_pair_rounds(const adgb_ligand_desc *d, int *n_rounds, int *max_degree
         deg[(c >> 8) & 255]++;
     }
     if (n_rounds) *n_rounds = h.R;
+    if (lanes) *lanes = h.VP;
     if (max_degree) *max_degree = h.N ? *std::max_element(deg.begin(), deg.end()) : 0;
     if (words) {
-        if (words_cap < 32 * h.R) return ADGB_EINVAL;
+        if ((size_t)words_cap < (size_t)h.R * h.VP) return ADGB_EINVAL;
         std::copy(h.rword.begin(), h.rword.end(), words);
     }
     if (perm) std::copy(h.perm.begin(), h.perm.end(), perm);
@@ -1632,6 +1651,10 @@ extern "C" int batch_create(adgb_ctx *c, int n_items, const int *receptor_ids, c
         return fail(c, ADGB_ENOMEM, "batch_create: %s", cudaGetErrorString(e));
     }
     b.cfg.variant = c->opts.reduce_variant;
+    if (c->opts.threads_per_pose > 0) {   // the context's launch shape, until tuned
+        b.cfg.tpp = c->opts.threads_per_pose;
+        b.cfg.ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / b.cfg.tpp;
+    }
     auto it = c->tune_table.find(tune_key(b));
     if (it != c->tune_table.end()) {
         b.cfg = it->second;

@@ -287,12 +287,15 @@ constexpr int TC_REGION = 10560;
 template <int VAR>
 __host__ __device__ constexpr int tc_front() { return VAR == ADGB_REDUCE_TCGEN05 ? TC_REGION : 0; }
 
-// The multi-ligand kernel keeps its current work-item index in the 16 bytes
-// before the ligand layout (inside the tcgen05 region's tail for that
-// variant).
+// The multi-ligand kernel keeps its current ligand's layout and work-item
+// index in a 128-byte header before the ligand layout (after the tcgen05
+// region for that variant): the layout read from shared memory instead of
+// held in registers across the work loop.
+constexpr int ITEMS_HDR = 128;
+static_assert(sizeof(SmemLayout) <= ITEMS_HDR - 16, "items header too small");
 template <int VAR>
 __host__ __device__ constexpr int items_front() {
-    return VAR == ADGB_REDUCE_TCGEN05 ? TC_REGION : 16;
+    return (VAR == ADGB_REDUCE_TCGEN05 ? TC_REGION : 0) + ITEMS_HDR;
 }
 
 __host__ __device__ constexpr int tc_ncols(int warps) {   // 16 D columns a warp
@@ -493,10 +496,14 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         const float m12 = o * u.y * u.z - s * u.x, m21 = o * u.y * u.z + s * u.x;
 
         // 2. coordinates and intermolecular terms.  With matching rounds
-        //    (one warp, at most 32 atoms: lane a owns atom a) the lane keeps
-        //    its atom's position and gradient in registers.
-        const bool rounds = TPP == 32 && lig.n_rounds > 0;
-        float3 xo = make_float3(0.f, 0.f, 0.f), go = xo;
+        //    (lane a owns atom a: one warp and shuffles up to 32 atoms, else
+        //    the pose's threads with atoms gt and gt + TPP, more lanes than
+        //    threads, and slots in shared memory) the thread keeps its atoms'
+        //    positions and gradients in registers.
+        const bool rounds = TPP == 32 && lig.n_rounds > 0 && lig.r_lanes == 32;
+        const bool brounds = TPP > 32 && lig.n_rounds > 0 && lig.r_lanes > TPP &&
+                             lig.r_lanes <= 2 * TPP;
+        float3 xo = make_float3(0.f, 0.f, 0.f), go = xo, xo1 = xo, go1 = xo;
         float e_part = 0.f;
         for (int i = gt; i < N; i += TPP) {
             const float4 r4 = s_ref[i];
@@ -509,14 +516,81 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
             xyz[i] = make_float4(x.x, x.y, x.z, r4.w);
             float3 g;
             e_part += inter_atom(rec, s_type[i], r4.w, x, g);
-            if (rounds) {
+            if (rounds || (brounds && i == gt)) {
                 xo = x;
                 go = g;
+            } else if (brounds) {
+                xo1 = x;
+                go1 = g;
             } else {
                 grd[i] = make_float4(g.x, g.y, g.z, 0.f);
             }
         }
         group_sync<TPP>(group);
+
+        // 3c. block form of the matching rounds: in each chunk of rounds every
+        //     lane writes its pair's force to its slot of the round, then
+        //     (after one barrier) takes the forces of the (at most two) pairs
+        //     whose second atom is its own from the slots its words name.
+        //     Every slot of a round is written (lanes without a pair write an
+        //     exact zero), so an unused receive slot, weighted by zero, reads a
+        //     finite value.
+        if (brounds) {
+            const int VP = lig.r_lanes, R = lig.n_rounds;
+            const int RC = max(1, L.chunk / VP);   // rounds a chunk (slots: RC x VP float4)
+            const bool has0 = gt < VP, has1 = gt + TPP < VP;
+            const uint32_t *rw = lig.rword;
+            const float4 *rcs = lig.rconst;
+            auto take = [&](float3 &g, uint32_t w, const float4 *slot) {
+                const float m1 = (w >> 25) & 1 ? 1.f : 0.f, m2 = (w >> 26) & 1 ? 1.f : 0.f;
+                const float4 f1 = slot[(w >> 8) & 255], f2 = slot[(w >> 16) & 255];
+                g.x -= m1 * f1.x + m2 * f2.x;
+                g.y -= m1 * f1.y + m2 * f2.y;
+                g.z -= m1 * f1.z + m2 * f2.z;
+            };
+            for (int r0 = 0; r0 < R; r0 += RC) {
+                const int r1 = min(R, r0 + RC);
+                for (int r = r0; r < r1; r++) {
+                    float4 *slot = fbuf + (r - r0) * VP;
+                    if (has1) {   // both atoms of the thread: packed arithmetic
+                        const uint32_t wa = __ldg(rw + (size_t)r * VP + gt);
+                        const uint32_t wb = __ldg(rw + (size_t)r * VP + gt + TPP);
+                        float3 fa, fb;
+                        e_part += pair_term2(xo, xo1, xyz3(xyz[wa & 255]), xyz3(xyz[wb & 255]),
+                                             __ldg(rcs + (size_t)r * VP + gt),
+                                             __ldg(rcs + (size_t)r * VP + gt + TPP),
+                                             (wa >> 24) & 1, (wb >> 24) & 1, fa, fb);
+                        go.x += fa.x;
+                        go.y += fa.y;
+                        go.z += fa.z;
+                        go1.x += fb.x;
+                        go1.y += fb.y;
+                        go1.z += fb.z;
+                        slot[gt] = make_float4(fa.x, fa.y, fa.z, 0.f);
+                        slot[gt + TPP] = make_float4(fb.x, fb.y, fb.z, 0.f);
+                    } else if (has0) {
+                        const uint32_t w = __ldg(rw + (size_t)r * VP + gt);
+                        float3 f;
+                        e_part += pair_term(make_float4(xo.x, xo.y, xo.z, 0.f), xyz[w & 255],
+                                            __ldg(rcs + (size_t)r * VP + gt), (w >> 24) & 1, f);
+                        go.x += f.x;
+                        go.y += f.y;
+                        go.z += f.z;
+                        slot[gt] = make_float4(f.x, f.y, f.z, 0.f);
+                    }
+                }
+                group_sync<TPP>(group);
+                for (int r = r0; r < r1; r++) {
+                    const float4 *slot = fbuf + (r - r0) * VP;
+                    if (has0) take(go, __ldg(rw + (size_t)r * VP + gt), slot);
+                    if (has1) take(go1, __ldg(rw + (size_t)r * VP + gt + TPP), slot);
+                }
+                group_sync<TPP>(group);   // the slots are rewritten by the next chunk
+            }
+            if (gt < N) grd[gt] = make_float4(go.x, go.y, go.z, 0.f);
+            if (gt + TPP < N) grd[gt + TPP] = make_float4(go1.x, go1.y, go1.z, 0.f);
+            group_sync<TPP>(group);   // gradients visible to the torsion scans
+        }
 
         // 3a. intramolecular pairs in matching rounds: the partner's position
         //     and the reaction forces of the (at most two) pairs whose second
@@ -574,7 +648,7 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
         //    atom's owner adds the forces of its pairs in the chunk (per-chunk
         //    incidence lists with known bounds).  No two threads ever write
         //    the same word.
-        for (int q = 0; q < (rounds ? 0 : lig.n_chunks); q++) {
+        for (int q = 0; q < (rounds || brounds ? 0 : lig.n_chunks); q++) {
             const int c0 = q * PAIR_CHUNK, c1 = min(NP, c0 + PAIR_CHUNK);
             int p = c0 + gt;
             for (; p + TPP < c1; p += 2 * TPP) {  // pairs p and p + TPP, packed arithmetic
@@ -1132,10 +1206,10 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = smem_raw + items_front<VAR>();
     int &s_item = *reinterpret_cast<int *>(sm - 16);
+    SmemLayout &L = *reinterpret_cast<SmemLayout *>(sm - ITEMS_HDR);
     constexpr int NG_MAX = (MAX_GENES + TPP - 1) / TPP;
     const int group = threadIdx.x / TPP, gt = threadIdx.x % TPP;
     int cur_lig = -1;
-    SmemLayout L;
     StagedLig sl;
     Tc05Warp tw;
     tc_begin<VAR>(smem_raw, tw);
@@ -1147,8 +1221,10 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
         const WorkItem w = a.items[it];
         if (w.lig != cur_lig) {
             const LigDev &lg = a.ligs[w.lig];
-            L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32,
-                                   uses_mma_stage(VAR));
+            if (threadIdx.x == 0)
+                L = SmemLayout::choose(lg.n_atoms, lg.n_tors, lg.n_pairs, a.ppb, TPP / 32,
+                                       uses_mma_stage(VAR));
+            __syncthreads();
             sl = stage_ligand(sm, L, lg);
             cur_lig = w.lig;
             __syncthreads();
@@ -1193,8 +1269,8 @@ __global__ void __launch_bounds__(128, ADGB_MIN_BLOCKS) eval_items_kernel(const 
 // no more blocks are resident on an SM than its 512 TMEM columns serve at
 // once (tcgen05.alloc would otherwise wait for a resident block to finish).
 int eval_smem_bytes(int layout_bytes, const EvalCfg &cfg, int device, bool items) {
-    if (cfg.variant != ADGB_REDUCE_TCGEN05) return layout_bytes + (items ? 16 : 0);
-    int total = TC_REGION + layout_bytes;
+    if (cfg.variant != ADGB_REDUCE_TCGEN05) return layout_bytes + (items ? ITEMS_HDR : 0);
+    int total = TC_REGION + (items ? ITEMS_HDR : 0) + layout_bytes;
     int sm_smem = 0, reserved = 0;
     if (cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) !=
             cudaSuccess ||

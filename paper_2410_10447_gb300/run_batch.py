@@ -4,6 +4,7 @@ from a CUDA graph, against the same work done ligand by ligand.
 
     python -m paper_2410_10447_gb300.run_batch [--ligands 512] [--poses 64]
         [--iters 300] [--reps 3] [--no-autotune] [--no-serial] [--variant V]
+        [--shape THREADS:POSES]
 
 Workload uneven_512: ligands with atom counts uniform in [10, 128] and
 torsions uniform in [0, 32] (10 atom types), 64 genotypes each, 300 ADADELTA
@@ -39,6 +40,8 @@ def main(argv=None):
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serial", action="store_true")
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--shape", default="", help="THREADS:POSES instead of autotuning")
+    ap.add_argument("--pair-rounds", type=int, default=0, help="adgb_options.pair_rounds")
     a = ap.parse_args(argv)
     P.load(build=True)
     w = synth.WORKLOADS["uneven_512"]
@@ -47,7 +50,12 @@ def main(argv=None):
     ligs = synth.make_uneven_batch(synth.generate.BASE_SEED + w["index"], a.ligands, w["atoms"],
                                    w["tors"], w["n_types"])
     t_gen = time.time() - t0
-    ctx = P.Context(0)
+    if a.shape:
+        tpp, ppb = (int(x) for x in a.shape.split(":"))
+        ctx = P.Context(0, threads_per_pose=tpp, poses_per_block=ppb, pair_rounds=a.pair_rounds)
+        a.no_autotune = True
+    else:
+        ctx = P.Context(0, pair_rounds=a.pair_rounds)
     rid = ctx.upload_receptor_grids(rec)
     lids = [ctx.upload_ligand_torsion_tree(L) for L in ligs]
     genes = [synth.make_poses(7000 + i, a.poses, rec, L["n_tors"]) for i, L in enumerate(ligs)]
@@ -76,7 +84,7 @@ def main(argv=None):
                atoms_mean=float(np.mean([L["n_atoms"] for L in ligs])),
                pairs_mean=float(np.mean([len(L["pairs"]) for L in ligs])),
                batch_ms=t_batch, batch_evals_per_s=evals / t_batch * 1e3, autotuned=tuned,
-               variant=a.variant,
+               variant=a.variant, shape=a.shape or None, pair_rounds=a.pair_rounds,
                first_call_ms_incl_capture=ms[0], generate_s=t_gen)
     if not a.no_serial:
         # the same work as one single-ligand launch per ligand, back to back

@@ -1,8 +1,8 @@
 """Ligand shapes across the kernels' internal boundaries, each against the
 FP64 oracle: atom counts just below and above one warp (32), two warps (64),
 four warps (128) and the maximum (256); torsion counts 0 and the maximum
-(40); pair lists below and above one force-buffer chunk (1024 pairs); up to
-32 atoms, both pair paths (matching rounds and force buffer).  For
+(40); pair lists below and above one force-buffer chunk (1024 pairs); both
+pair paths (matching rounds, warp or block form, and force buffer).  For
 every shape: scores with each reduction variant, a short ADADELTA search
 that must return its best, and the Solis-Wets start energy.
 Tolerances: energy max(1e-4 |E|, 1e-3 kcal/mol); gene gradient 1e-3 (FP32
@@ -48,8 +48,6 @@ def near_face(r, x, tol=1e-4):
 @pytest.mark.parametrize("pair_rounds", [0, 1])
 @pytest.mark.parametrize("n_atoms, n_tors", SHAPES)
 def test_shape_parity(pkg, torch, rec, n_atoms, n_tors, pair_rounds):
-    if pair_rounds and n_atoms > 32:
-        pytest.skip("one pair path above 32 atoms")
     lig = synth.make_ligand(31_000 + n_atoms, n_atoms, 8, n_tors)
     genes = synth.make_poses(32_000 + n_atoms, 6, rec, n_tors)
     R, L = oracle.Receptor(rec), oracle.Ligand(lig)

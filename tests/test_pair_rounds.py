@@ -1,13 +1,15 @@
-"""Host-side pair schedule for ligands of at most 32 atoms (no GPU): the
-library splits the intramolecular pair list (the pair sum of Eq. 1) into
-rounds in which each lane (atom) computes at most one pair and receives the
-reaction forces of at most two pairs.  Checked here from the exported round
-words alone: every caller pair exactly once, at most one computed and two
-received pairs a lane a round, the force-source lanes and their flags, the
-H-bond flag, and the round count max(ceil(pairs / atoms), ceil(max degree /
-3)), the lower bound of the scheme (one lane an atom; an atom in at most three
-pairs a round), reached through an out-degree-bounded orientation and a bipartite
-edge colouring (Konig's theorem)."""
+"""Host-side pair schedule (no GPU): the library splits the intramolecular
+pair list (the pair sum of Eq. 1) into rounds in which each lane (atom)
+computes at most one pair and receives the reaction forces of at most two
+pairs; 32 lanes up to 32 atoms (one warp), the atoms rounded up to 32 above
+112 atoms (a block of threads), none between (the force buffer is faster).  Checked here from the exported round words alone:
+every caller pair exactly once, at most one computed and two received pairs
+a lane a round, the force-source lanes and their flags, lanes past the last
+atom idle and pointing at a real atom, the H-bond flag, and the round count
+max(ceil(pairs / atoms), ceil(max degree / 3)), the lower bound of the scheme
+(one lane an atom; an atom in at most three pairs a round), reached through
+an out-degree-bounded orientation and a bipartite edge colouring (Konig's
+theorem)."""
 import numpy as np
 import pytest
 
@@ -31,15 +33,17 @@ def with_pairs(lig, pairs):
 def check_schedule(pkg, lig):
     N = int(lig["n_atoms"])
     pairs = np.asarray(lig["pairs"]).reshape(-1, 2)
-    R, maxdeg, words, perm = pkg.ligand_pair_rounds(lig)
+    R, lanes, maxdeg, words, perm = pkg.ligand_pair_rounds(lig)
     deg = np.zeros(N, int)
     for i, j in pairs:
         deg[i] += 1
         deg[j] += 1
     assert maxdeg == (deg.max() if len(pairs) else 0)
-    if N > 32 or len(pairs) == 0:
-        assert R == 0
+    if len(pairs) == 0 or 32 < N <= 112:   # no pairs; or the force buffer is faster
+        assert R == 0 and lanes == 0
         return R
+    assert lanes == (32 if N <= 32 else -(-N // 32) * 32)
+    assert words.shape == (R, lanes)
     assert R >= max(-(-len(pairs) // N), -(-maxdeg // 3))
     roles = np.asarray(lig["hb_role"])
     types = np.asarray(lig["type"])
@@ -48,32 +52,31 @@ def check_schedule(pkg, lig):
         ri, rj = roles[types[i]], roles[types[j]]
         want[frozenset((int(i), int(j)))] = int((ri, rj) in ((1, 2), (2, 1)))
     seen = {}
+    ids = np.arange(lanes)
     for r in range(R):
         w = words[r].astype(np.int64)
-        partner = w & 31
-        src = [(w >> 8) & 31, (w >> 16) & 31]
+        partner = w & 255
+        src = [(w >> 8) & 255, (w >> 16) & 255]
         used = [(w >> 25) & 1, (w >> 26) & 1]
         hb = (w >> 24) & 1
-        assert np.all(w & ~(31 | 31 << 8 | 31 << 16 | 7 << 24) == 0)
-        has = partner != np.arange(32)
-        assert not np.any(has[N:]), "lanes without an atom compute no pair"
-        assert not np.any(used[0][N:]) and not np.any(used[1][N:])
-        received = {b: [] for b in range(32)}
+        assert np.all(w & ~(255 | 255 << 8 | 255 << 16 | 7 << 24) == 0)
+        assert np.all(partner < N), "every partner is a real atom"
+        assert np.all(src[0] < lanes) and np.all(src[1] < lanes)
+        has = (partner != ids) & (ids < N)
+        assert np.all(partner[N:] == 0) and not np.any(used[0][N:]) and not np.any(used[1][N:])
+        received = {b: [] for b in range(lanes)}
         for k in range(2):
-            for b in range(32):
-                if used[k][b]:
-                    received[b].append(int(src[k][b]))
-        for a in range(32):
-            if has[a]:
-                key = frozenset((int(perm[a]), int(perm[partner[a]])))
-                assert key not in seen, "pair scheduled twice"
-                seen[key] = r
-                assert hb[a] == want[key]
-                b = int(partner[a])
-                assert b < N and received[b].count(a) == 1, "the partner receives the force once"
-            else:
-                assert hb[a] == 0
-        for b in range(32):
+            for b in np.nonzero(used[k])[0]:
+                received[int(b)].append(int(src[k][b]))
+        for a in np.nonzero(has)[0]:
+            key = frozenset((int(perm[a]), int(perm[partner[a]])))
+            assert key not in seen, "pair scheduled twice"
+            seen[key] = r
+            assert hb[a] == want[key]
+            b = int(partner[a])
+            assert received[b].count(int(a)) == 1, "the partner receives the force once"
+        assert not np.any(hb[~has])
+        for b in range(lanes):
             assert len(received[b]) <= 2
             for a in received[b]:
                 assert has[a] and partner[a] == b, "a used slot names a lane whose pair has atom b second"
@@ -82,7 +85,8 @@ def check_schedule(pkg, lig):
 
 
 @pytest.mark.parametrize("n_atoms, n_tors", [(2, 0), (5, 1), (16, 4), (24, 6), (31, 6), (32, 8),
-                                             (32, 0), (33, 8)])
+                                             (32, 0), (33, 8), (48, 12), (64, 16), (100, 20),
+                                             (129, 32), (256, 40)])
 def test_synthetic_ligands(pkg, n_atoms, n_tors):
     lig = synth.make_ligand(41_000 + n_atoms, n_atoms, 8, n_tors)
     check_schedule(pkg, lig)
@@ -115,9 +119,8 @@ def test_random_pair_sets(pkg, seed):
     else:
         pairs = [p for p in full if rng.random() < keep] or [(0, 1)]
     R = check_schedule(pkg, with_pairs(lig, pairs))
-    N = 32
-    deg = np.bincount(np.asarray(pairs).ravel(), minlength=N)
+    deg = np.bincount(np.asarray(pairs).ravel(), minlength=32)
     if keep != 1.0:
-        assert R == max(-(-len(pairs) // N), -(-deg.max() // 3))
+        assert R == max(-(-len(pairs) // 32), -(-deg.max() // 3))
     if keep == 1.0:
         assert R == 16          # 496 pairs / 32 lanes (degree 31 alone: 11 rounds)
