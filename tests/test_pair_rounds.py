@@ -2,8 +2,9 @@
 pair list (the pair sum of Eq. 1) into rounds in which each lane (atom)
 computes at most one pair and receives the reaction forces of at most two
 pairs; 32 lanes up to 32 atoms (one warp), the atoms rounded up to 32 above
-112 atoms (a block of threads), none between (the force buffer is faster).  Checked here from the exported round words alone:
-every caller pair exactly once, at most one computed and two received pairs
+112 atoms (a block of threads), none between (the force buffer is faster).
+Checked here from the exported round words alone: every caller pair exactly
+once, at most one computed and two received pairs
 a lane a round, the force-source lanes and their flags, lanes past the last
 atom idle and pointing at a real atom, the H-bond flag, and the round count
 max(ceil(pairs / atoms), ceil(max degree / 3)), the lower bound of the scheme
