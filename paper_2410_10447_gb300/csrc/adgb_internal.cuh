@@ -168,6 +168,13 @@ struct SmemLayout {
     }
 };
 
+// Threads a genotype by ligand size (one warp up to 32 atoms, two up to 56,
+// else 128; measured on 3000 genotypes, see the local-search launch-shape
+// sweep): the single-ligand calls and the serving loop's size classes alike.
+__host__ __device__ inline int threads_for_atoms(int n_atoms) {
+    return n_atoms <= 32 ? 32 : (n_atoms <= 56 ? 64 : 128);
+}
+
 // Reduction variants that stage each warp's values in shared memory for
 // mma.sync.
 __host__ __device__ inline bool uses_mma_stage(int variant) {

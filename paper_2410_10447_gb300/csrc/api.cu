@@ -670,7 +670,7 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     // genotypes, 64 x 2 beats 128 x 1 by 10-17% from 40 to 56 atoms, 128 x 1
     // beats 64 x 2 from 64 atoms on (by 10% at 64, 15-20% at 80-128, more
     // with the matching rounds above 112)
-    const int by_size = L.n_atoms <= 32 ? 32 : (L.n_atoms <= 56 ? 64 : 128);
+    const int by_size = threads_for_atoms(L.n_atoms);
     cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : by_size;
     int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
     while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;

@@ -36,7 +36,7 @@ using namespace adgb;
 namespace {
 
 enum { JOB_QUEUED = 1, JOB_RUNNING = 2, JOB_DONE = 0 };
-constexpr int NCLS = 2;   // ligand-size classes of the local-search launches
+constexpr int NCLS = 3;   // ligand-size classes of the local-search launches (32, 64, 128 threads)
 
 struct Job {
     long long id = 0;
@@ -110,8 +110,8 @@ struct adgb_server {
     cudaStream_t stream = nullptr;
     // the size classes' local-search launches run concurrently, one stream
     // each, between two events of the main stream (tables ready / all done)
-    cudaStream_t cls_stream[NCLS] = {nullptr, nullptr};
-    cudaEvent_t ev_tables = nullptr, ev_cls[NCLS] = {nullptr, nullptr};
+    cudaStream_t cls_stream[NCLS] = {};
+    cudaEvent_t ev_tables = nullptr, ev_cls[NCLS] = {};
     std::chrono::steady_clock::time_point t0;
     std::string err;
     // per-tick tables (pinned staging, device copies)
@@ -189,7 +189,7 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
         }
     }
     // multi-ligand local-search launches over every active individual: one
-    // per size class (one warp a genotype up to 32 atoms, 128 threads above),
+    // per size class (threads a genotype as for a single-ligand call),
     // each a persistent launch over that class's work items (a job's class
     // depends on its ligand alone)
     std::vector<int> cls(act.size());
@@ -197,14 +197,15 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     for (int c = 0; c < NCLS; c++) {
         ccfg[c] = s->cfg;
         if (!s->forced_shape) {
-            ccfg[c].tpp = c == 0 ? 32 : 128;
+            ccfg[c].tpp = 32 << c;
             ccfg[c].ppb = 128 / ccfg[c].tpp;
         }
     }
     int n_items = 0;
     for (size_t u = 0; u < act.size(); u++) {
         const int N = act[u]->lig.n_atoms;
-        cls[u] = s->forced_shape ? 0 : (N <= 32 ? 0 : 1);
+        const int t = threads_for_atoms(N);
+        cls[u] = s->forced_shape ? 0 : (t == 32 ? 0 : (t == 64 ? 1 : 2));
         n_items += (act[u]->d.n_runs * act[u]->d.pop + ccfg[cls[u]].ppb - 1) / ccfg[cls[u]].ppb;
     }
     e = grow_tables(s, n_items, (int)act.size());
