@@ -461,7 +461,7 @@ typedef struct adgb_server adgb_server;
 typedef struct {
     int max_active_jobs;          /* 0: limited by the memory budget only */
     long long mem_budget_bytes;   /* 0: a quarter of the free device memory at start */
-    int threads_per_pose;         /* 0: by ligand size (32 up to 32 atoms, 64 up to 96, else 128) */
+    int threads_per_pose;         /* 0: by ligand size (32 up to 32 atoms, 64 up to 56, else 128) */
     int poses_per_block;          /* 0: 128 / threads_per_pose */
     int reduce_variant;           /* -1: the context default */
 } adgb_serve_options;
