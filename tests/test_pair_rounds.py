@@ -125,3 +125,11 @@ def test_random_pair_sets(pkg, seed):
         assert R == max(-(-len(pairs) // 32), -(-deg.max() // 3))
     if keep == 1.0:
         assert R == 16          # 496 pairs / 32 lanes (degree 31 alone: 11 rounds)
+
+
+def test_largest_pair_list(pkg):
+    """The maximum: 256 atoms, every pair (32,640).  Lanes need all 8 bits of
+    the word's lane fields; 128 rounds = ceil(32640 / 256)."""
+    lig = synth.make_ligand(44_000, 256, 8, 40)
+    pairs = [(i, j) for i in range(256) for j in range(i + 1, 256)]
+    assert check_schedule(pkg, with_pairs(lig, pairs)) == 128
