@@ -65,10 +65,13 @@ def test_batch_scores_match_single_ligand_calls(pkg, torch, setup):
     ctx.close()
 
 
-@pytest.mark.parametrize("autotune, variant", [(False, -1), (True, -1), (False, 3)])
-def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune, variant):
+@pytest.mark.parametrize("autotune, variant, tpp", [(False, -1, 0), (True, -1, 0), (False, 3, 0),
+                                                   (False, -1, 128), (False, 3, 128)])
+def test_batch_local_search_returns_its_best(pkg, torch, setup, autotune, variant, tpp):
+    """tpp 128: the 256-atom ligand takes the block form of the matching
+    rounds inside the multi-ligand kernel (two atoms a thread)."""
     rec, ligs, n_poses, genes = setup
-    ctx = pkg.Context(0)
+    ctx = pkg.Context(0, threads_per_pose=tpp, poses_per_block=128 // tpp) if tpp else pkg.Context(0)
     rid = ctx.upload_receptor_grids(rec)
     lids = [ctx.upload_ligand_torsion_tree(L) for L in ligs]
     bid = ctx.batch_create([rid] * len(ligs), lids, n_poses)
