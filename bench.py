@@ -18,7 +18,11 @@ docking job makes (upload_ligand_torsion_tree, dock with host outputs,
 release_ligand).  The roofline line is for the local-search kernel (98-99%
 of the GPU time), measured from standalone launches of the same shape.
 `--impl reference` times the FP64 CPU oracle's docking on a bounded sample.
-Multi-GPU (torchrun) runs one independent replica per rank (weak scaling).
+Multi-GPU: `--gpus N` (N > 1) re-runs the command as N ranks of one node
+(torch.distributed.run, 127.0.0.1) unless it already runs under a launcher;
+every rank docks its own replica (weak scaling, no data-path collective),
+the slowest rank's time gives the job rate.  `--dry-run` checks that launch
+path with a host loop only.
 """
 from __future__ import annotations
 
@@ -44,23 +48,91 @@ EVALS_PER_DOCK = RUNS * POP * (1 + GENS * ITERS)
 # kernel launches of one dock(): state init, initial population, its scoring
 # and accounting, then GA + local search + accounting per generation, rescoring
 LAUNCHES_PER_DOCK = 4 + 3 * GENS + 1
-# Algorithmic ALU work per energy+gradient evaluation, counted from the
-# method (FMA = 2 flops; one MUFU op = 16 flop-equivalents, the FP32 pipe
-# being 8x wider than the special-function pipe):
-#   per atom  : pose transform 20 + 20 per enclosing torsion, grid term 80
-#   per pair  : 50 FP32 flops + 5 MUFU ops (rsqrt, 2 exp, 2 rcp)
-#   per gene  : ADADELTA 15;  per moving atom of a torsion 12 (torsion gradient)
-FLOP_ATOM, FLOP_ATOM_TORS, FLOP_GRID, FLOP_PAIR, MUFU_PAIR, MUFU_EQ = 20, 20, 80, 50, 5, 16
-FLOP_GENE, FLOP_MOVING = 15, 12
-SM_COUNT, FP32_LANES = 152, 128
+# Algorithmic work per energy+gradient evaluation, counted from the method
+# (what any implementation must compute; FMA = 2 flops), FP32 arithmetic and
+# special-function (MUFU) operations kept apart:
+#   grid terms      110 flops per atom (trilinear value and gradient of three
+#                   maps, 24 gathers of 4 bytes)
+#   pair terms      40 flops + 3 MUFU per pair: 1 reciprocal square root and
+#                   2 exponentials (the dielectric's and the desolvation's)
+#   pose            20 flops per moving atom of each torsion + 30 per atom
+#   gene gradient   12 flops per moving atom of each torsion
+#   reduction       8 adds per thread of a pose (the 8-wide reduce-and-broadcast)
+#   ADADELTA        15 flops + 2 square roots per gene
+# The roofline of the local-search kernel is the binding one of the FP32 pipe
+# and the MUFU pipe: each fraction is its operations / its peak, the pipes
+# working in parallel.
+FLOP_GRID, FLOP_PAIR, FLOP_POSE_MOV, FLOP_POSE_ATOM = 110, 40, 20, 30
+FLOP_GGRAD_MOV, FLOP_RED_THREAD, FLOP_GENE = 12, 8, 15
+RSQ_PAIR, EX2_PAIR, SQRT_GENE = 1, 2, 2
+SM_COUNT, FP32_LANES, SM_MHZ_MAX = 152, 128, 2070.0
+# special-function results an SM completes a clock, by operation (from the
+# ALU probe on GB300: ex2 10.0 T/s and rsqrt 5.0 T/s at 2070 MHz over 152 SMs)
+MUFU_EX2_PER_SM_CLK, MUFU_RSQ_PER_SM_CLK = 32, 16
 
 
-def eval_flops(lig) -> float:
+def eval_work(lig, threads_per_pose=32):
+    """(FP32 flops, reciprocal-square-root-class MUFU ops, ex2 MUFU ops) per
+    energy+gradient evaluation of `lig`."""
     N, T = lig["n_atoms"], lig["n_tors"]
     moving = int(lig["mov_off"][-1]) if T else 0     # sum of moving-set sizes
     P = len(lig["pairs"])
-    return (N * (FLOP_ATOM + FLOP_GRID) + moving * (FLOP_ATOM_TORS + FLOP_MOVING)
-            + P * (FLOP_PAIR + MUFU_PAIR * MUFU_EQ) + (6 + T) * FLOP_GENE)
+    G = 6 + T
+    flops = (FLOP_GRID * N + FLOP_PAIR * P + FLOP_POSE_MOV * moving + FLOP_POSE_ATOM * N
+             + FLOP_GGRAD_MOV * moving + FLOP_RED_THREAD * threads_per_pose + FLOP_GENE * G)
+    return float(flops), float(RSQ_PAIR * P + SQRT_GENE * G), float(EX2_PAIR * P)
+
+
+def alu_roofline(lig, evals_per_s, probe=None, sm_mhz=SM_MHZ_MAX):
+    """FP32 and MUFU roofline fractions of a kernel doing `evals_per_s`
+    evaluations of `lig`: against peaks derived from the unit counts and the
+    clock, and against the measured ALU probe when given."""
+    fl, rsq, ex2 = eval_work(lig)
+    clk = sm_mhz * 1e6
+    fp32_peak = SM_COUNT * FP32_LANES * 2 * clk / 1e12               # TFLOP/s
+    rsq_peak = SM_COUNT * MUFU_RSQ_PER_SM_CLK * clk                  # ops/s
+    ex2_peak = SM_COUNT * MUFU_EX2_PER_SM_CLK * clk
+    fp32 = evals_per_s * fl / 1e12
+    frac_fp32 = fp32 / fp32_peak
+    frac_mufu = evals_per_s * (rsq / rsq_peak + ex2 / ex2_peak)
+    out = {"bound": "alu", "achieved": fp32, "peak": fp32_peak, "unit": "TFLOP/s",
+           "frac": max(frac_fp32, frac_mufu), "frac_fp32": frac_fp32, "frac_mufu": frac_mufu,
+           "fp32_flops_per_eval": fl, "mufu_rsqrt_per_eval": rsq, "mufu_ex2_per_eval": ex2,
+           "peak_basis": "derived: FP32 152 SMs x 128 lanes x 2 flops x %.0f MHz; MUFU 152 SMs "
+                         "x (16 rsqrt-class, 32 ex2) a clock" % sm_mhz}
+    if probe:
+        out["frac_fp32_of_measured_ffma"] = fp32 / probe["ffma_tflops"]
+        out["frac_mufu_of_measured"] = evals_per_s * (rsq / (probe["rsqrt_gops"] * 1e9)
+                                                      + ex2 / (probe["ex2_gops"] * 1e9))
+        out["measured_probe"] = probe
+    return out
+
+
+def alu_probe(ctx, torch, waves=8, threads=256, reps=2000):
+    """Measured ALU peaks over the whole GPU: FP32 FMA TFLOP/s, packed FP32x2
+    FMA TFLOP/s, ex2.approx and rsqrt.approx Gop/s (alu_bench_dev)."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    nb = props.multi_processor_count * waves
+    out = torch.empty(nb * threads, device="cuda")
+    res = {"sms": props.multi_processor_count}
+    for kind, name in ((0, "ffma"), (1, "ex2"), (2, "rsqrt"), (3, "ffma2")):
+        ctx.alu_bench_dev(kind, nb, threads, 10, out)
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.alu_bench_dev(kind, nb, threads, reps, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rate = nb * threads * reps * 128.0 / (min(ms) / 1e3)
+        if kind == 0:
+            res["ffma_tflops"] = 2 * rate / 1e12
+        elif kind == 3:
+            res["ffma2_tflops"] = 4 * rate / 1e12
+        else:
+            res[name + "_gops"] = rate / 1e9
+    return res
 
 
 def dist_env():
@@ -224,6 +296,46 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def launch_ranks(n):
+    """Re-runs this command as n ranks of one node (torch.distributed.run,
+    rendezvous on 127.0.0.1) and returns their exit status; rank 0 prints
+    the line."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           "--nproc-per-node", str(n), "--master-addr", "127.0.0.1", "--master-port", str(port),
+           os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.run(cmd).returncode
+
+
+def dry_run(args, rank, world):
+    """The N-rank host path without device work: every rank times a short
+    host loop, the slowest rank's time gives the job rate, rank 0 prints."""
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+    t0 = time.perf_counter()
+    units = 0
+    for _ in range(args.steps):
+        units += int(np.arange(20000).sum() > 0)
+    t = max_over_ranks(dist, time.perf_counter() - t0, "cpu" if not torch.cuda.is_available()
+                       else "cuda")
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        print(json.dumps({"metric": "dry run (host loop iterations/s)", "dry_run": True,
+                          "value": job_rate(world, units, t), "unit": "iterations/s",
+                          "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "higher_is_better": True, "scaling": "weak"}), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,8 +347,16 @@ def main():
     ap.add_argument("--cpu-runs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-variants", action="store_true")
+    ap.add_argument("--dry-run", action="store_true",
+                    help="rank set-up, barrier and max-over-ranks timing of a tiny host loop "
+                         "only (no GPU work; gloo without CUDA): checks the launch path")
     args = ap.parse_args()
     rank, local_rank, world = dist_env()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        sys.exit(launch_ranks(args.gpus))
+    if args.dry_run:
+        dry_run(args, rank, world)
+        return
     if args.impl == "reference":
         reference_arm(args, rank, world)
         return
@@ -353,19 +473,17 @@ def main():
                 ms.append(a.elapsed_time(b))
             extra[name] = n * ITERS / (min(ms) / 1e3)
     # measured FP32 FMA and special-function throughput (after the timed region)
-    from paper_2410_10447_gb300.reduce_bench import alu_peaks
-    probe = alu_peaks(ctx, torch)
+    probe = alu_probe(ctx, torch)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    fl = eval_flops(lig)
     launch_s = statistics.mean(ls_ms) / 1e3
-    achieved = n * ITERS * fl / launch_s / 1e12
     clocks = clk.summary()
-    peak = SM_COUNT * FP32_LANES * 2 * 2070e6 / 1e12
-    traffic = profile_traffic(kernel_sha())
+    roof = alu_roofline(lig, n * ITERS / launch_s, probe)
+    roof["traffic"] = profile_traffic(kernel_sha())
+    roof["kernel"] = "eval_kernel (local search, 3000 genotypes x 300 evaluations)"
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -398,12 +516,7 @@ def main():
         "e2e": {"value": e2e, "unit": "evals/s", "h2d_bytes_per_step": int(lig_bytes),
                 "d2h_bytes_per_step": RUNS * (G * 4 + 8 + 8)},
         "gpu_launches": args.steps * LAUNCHES_PER_DOCK,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "eval_kernel (local search, 3000 genotypes x 300 evaluations)",
-                     "flops_per_eval": fl,
-                     "peak_basis": "FP32 FMA pipe, 152 SMs x 128 lanes x 2 x 2070 MHz",
-                     "peak_probe": dict(probe, frac_of_ffma_probe=achieved / probe["ffma_tflops"])},
+        "roofline": roof,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

@@ -4,8 +4,8 @@ thread receives.  Times each variant for block sizes 64..1024 and reports the
 speed-up over the per-component shuffle + shared-atomic reduction profiled in
 Sec. 3.
 
-    python -m paper_2410_10447_gb300.reduce_bench [--reps 1000] [--waves 4]
-    python -m paper_2410_10447_gb300.reduce_bench --alu
+    python -m benchmarks.reduce_bench [--reps 1000] [--waves 4]
+    python -m benchmarks.reduce_bench --alu
 
 --alu instead measures the arithmetic units the scoring kernels are bound by:
 FP32 fused multiply-add throughput (TFLOP/s) and special-function-unit
@@ -23,33 +23,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
-def alu_peaks(ctx, torch, waves=8, threads=256, reps=2000):
-    """FFMA TFLOP/s and special-function Gop/s over the whole GPU."""
-    props = torch.cuda.get_device_properties(0)
-    nb = props.multi_processor_count * waves
-    out = torch.empty(nb * threads, device="cuda")
-    res = {"sms": props.multi_processor_count}
-    for kind, name in ((0, "ffma"), (1, "ex2"), (2, "rsqrt"), (3, "ffma2")):
-        ctx.alu_bench_dev(kind, nb, threads, 10, out)
-        ms = []
-        for _ in range(3):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            ctx.alu_bench_dev(kind, nb, threads, reps, out)
-            e1.record()
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        ops = nb * threads * reps * 128.0
-        rate = ops / (min(ms) / 1e3)
-        if kind == 0:
-            res["ffma_tflops"] = 2 * rate / 1e12
-        elif kind == 3:
-            res["ffma2_tflops"] = 4 * rate / 1e12
-        else:
-            res[name + "_gops"] = rate / 1e9
-    return res
-
-
 def main(argv=None):
     import torch
 
@@ -64,7 +37,8 @@ def main(argv=None):
     P.load(build=True)
     ctx = P.Context(0)
     if a.alu:
-        print(json.dumps(alu_peaks(ctx, torch)), flush=True)
+        import bench
+        print(json.dumps(bench.alu_probe(ctx, torch)), flush=True)
         return
     names = {"paper_reducefs": P.REDUCE4_PAPER_FS, "paper_half": P.REDUCE4_PAPER_HALF,
              "shfl": 0, "mma_tf32x2": 1, "mma_bf16x3": 2,

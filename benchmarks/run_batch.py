@@ -2,7 +2,7 @@
 genotypes, locally searched by one persistent multi-ligand launch replayed
 from a CUDA graph, against the same work done ligand by ligand.
 
-    python -m paper_2410_10447_gb300.run_batch [--ligands 512] [--poses 64]
+    python -m benchmarks.run_batch [--ligands 512] [--poses 64]
         [--iters 300] [--reps 3] [--no-autotune] [--no-serial] [--variant V]
         [--shape THREADS:POSES]
 

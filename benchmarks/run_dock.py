@@ -1,6 +1,6 @@
 """Docking time with and without early stopping (convergence detection).
 
-    python -m paper_2410_10447_gb300.run_dock [--workload lga_n32] [--runs 20]
+    python -m benchmarks.run_dock [--workload lga_n32] [--runs 20]
         [--pop 150] [--gens 100] [--every 5] [--top 15] [--tol 0.15] [--reps 3]
 
 Docks the workload's ligand (runs x pop, up to `gens` generations of 300

@@ -1,6 +1,6 @@
 """Times local-search launches on a named synthetic workload.
 
-    python -m paper_2410_10447_gb300.run_ls [--workload lga_n32] [--iters 300]
+    python -m benchmarks.run_ls [--workload lga_n32] [--iters 300]
         [--n 0] [--cfgs 32:4,64:2] [--variants 0,1,2] [--reps 3] [--method adadelta|sw]
 
 For every launch shape "threads_per_pose:poses_per_block" and reduction

@@ -1,7 +1,7 @@
 """Serving benchmark: an open-loop Poisson stream of docking jobs into the
 continuous-batching server.
 
-    python -m paper_2410_10447_gb300.serve_bench [--rate 200] [--duration 60]
+    python -m benchmarks.serve_bench [--rate 200] [--duration 60]
         [--runs 10] [--pop 150] [--evals-per-run 2.5e6] [--ls-iters 300]
         [--pool 48] [--max-active 0] [--seed 1] [--variant -1] [--serial]
 

@@ -168,8 +168,8 @@ int validate_ligand_torsion_tree(const adgb_ligand_desc *lig, char *msg, int msg
 
 /*
  * ligand_pair_rounds - the host-side schedule of the intramolecular pairs
- * (Sec. 2.1, Eq. 1's pair sum) that upload_ligand_torsion_tree builds,
- * without a context or a device: for ligands of at most 32 atoms and of more
+ * (the pair sum in Sec. 2.1's scoring function) that
+ * upload_ligand_torsion_tree builds, without a context or a device: for ligands of at most 32 atoms and of more
  * than 112 (between, the per-pair force buffer is faster and no rounds are
  * built).  Lane a owns internal atom a: lanes = 32 up to 32 atoms (one warp
  * a genotype; positions and forces move by warp shuffles), else the atoms
@@ -348,8 +348,12 @@ int dock(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *
  * return ADGB_EINVAL.  All calls share the array: calls whose work overlaps
  * on the GPU (other streams, other contexts, other host threads) race and
  * must be serialised by the caller.  Every part of the array a call reads is
- * first written by that call.  The first call on a device looks up the
- * array's device address; make that first call before any stream capture.
+ * first written by that call.  Every call made outside a stream capture
+ * looks up the array's device address (so a device reset, which reloads the
+ * library's module, leaves no stale address); a call made while `stream` is
+ * being captured reuses the address its device's last uncaptured call found,
+ * and fails with EDEVICE if there was none: make one uncaptured call on a
+ * device (after any reset) before capturing.
  */
 int dock_noalloc_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, const adgb_dock_params *p,
                      float *best_genes_dev, double *best_energy_dev, long long *evals_dev,
@@ -539,6 +543,21 @@ int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
  */
 int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, float *out_dev,
                   adgb_stream stream);
+
+/*
+ * philox4x32_10_dev - the counter-based generator every random decision of
+ * the library draws from (GA selection, crossover and mutation, initial
+ * genotypes, Solis-Wets deviates): Philox4x32 with 10 rounds, Salmon,
+ * Moraes, Dror and Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+ * (SC'11), the generator behind the Lamarckian GA of Sec. 2.1 here.  Exposed
+ * so that the device implementation can be checked against the published
+ * known-answer vectors.  in_dev [n][6] uint32 = (counter words 0-3, key words
+ * 0-1), out_dev [n][4] uint32 receives the four output words; both device
+ * buffers are caller-owned and used on `stream`.  n = 0 does nothing.
+ * Errors: EINVAL (null buffers with n > 0, n < 0), EDEVICE.
+ */
+int philox4x32_10_dev(adgb_ctx *ctx, const unsigned int *in_dev, int n, unsigned int *out_dev,
+                      adgb_stream stream);
 
 #ifdef __cplusplus
 }

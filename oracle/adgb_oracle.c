@@ -31,11 +31,11 @@
  *    test are this project's readings, written out where they are defined
  *    below.
  *
- * Parity unpinned: the Philox4x32-10 stream (no published known-answer
- * vectors are available here; pinned by statistics only) and therefore the
- * exact GA decisions and Solis-Wets deviates built on it; the GA rules and
- * the Solis-Wets constants have no printed values in the paper to compare
- * with.
+ * Pins beyond the paper: the Philox4x32-10 generator is checked against the
+ * known-answer vectors published with it (Salmon et al., SC'11), so the GA
+ * decisions and Solis-Wets deviates drawn from it rest on a pinned stream.
+ * Parity unpinned: the GA rules and the Solis-Wets constants themselves have
+ * no printed values in the paper to compare with (checked by invariants).
  */
 #include "adgb_oracle.h"
 

@@ -38,7 +38,8 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "local_search_sw_dev", "local_search_sw", "alu_bench_dev",
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
-           "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget"]
+           "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget",
+           "philox4x32_10_dev"]
 MAX_GENES = 46
 
 
@@ -200,6 +201,7 @@ def load(build: bool = False):
                                     vp]
     L.ga_converged_dev.argtypes = [vp, C.POINTER(_DockParams), vp, vp, vp]
     L.alu_bench_dev.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.philox4x32_10_dev.argtypes = [vp, vp, C.c_int, vp, vp]
     _lib = L
     return L
 
@@ -417,6 +419,19 @@ class Context:
     def alu_bench_dev(self, kind, n_blocks, threads, reps, out):
         """ALU throughput probe (kind 0 FFMA, 1 ex2.approx, 2 rsqrt.approx, 3 packed FFMA2)."""
         self._chk(self.lib.alu_bench_dev(self.h, kind, n_blocks, threads, reps, _ptr(out), _stream()))
+
+    def philox4x32_10_dev(self, ctr_key, out):
+        """Philox4x32-10 words: ctr_key [n][6] (counter 0-3, key 0-1) -> out [n][4],
+        both int32/uint32-sized CUDA tensors."""
+        import torch
+        for t, name in ((ctr_key, "ctr_key"), (out, "out")):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32
+                    and t.is_contiguous()):
+                raise TypeError("%s must be a contiguous int32 CUDA tensor" % name)
+        if ctr_key.dim() != 2 or ctr_key.shape[1] != 6 or tuple(out.shape) != (ctr_key.shape[0], 4):
+            raise ValueError("ctr_key must be [n][6] and out [n][4]")
+        self._chk(self.lib.philox4x32_10_dev(self.h, _ptr(ctr_key), ctr_key.shape[0], _ptr(out),
+                                             _stream()))
 
     def ga_converged_dev(self, params, energy, converged):
         """Early-stopping test of params (conv_top, conv_tol) on energy

@@ -232,6 +232,7 @@ cudaError_t launch_job_best(const DockCfg &d, int G, int gen, DockScratch &w, in
                             float *best_genes, cudaStream_t s);
 cudaError_t launch_ga_converged(int n_runs, int pop, int top, float tol, const float *energy,
                                 int *converged, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t *in, int n, uint32_t *out, cudaStream_t s);
 cudaError_t launch_alu_bench(int kind, int n_blocks, int threads, int reps, float *out,
                              cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,

@@ -1445,6 +1445,15 @@ int alu_bench_dev(adgb_ctx *c, int kind, int n_blocks, int threads, int reps, fl
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "alu_bench");
 }
 
+int philox4x32_10_dev(adgb_ctx *c, const unsigned int *in_dev, int n, unsigned int *out_dev,
+                      adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || (n > 0 && (!in_dev || !out_dev))) return fail(c, ADGB_EINVAL, "philox4x32_10: bad arguments");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_philox(in_dev, n, out_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "philox4x32_10");
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -1468,14 +1477,21 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 
-// Device address of g_dock_scratch on the current device (looked up once per
-// device; the host-side symbol is only a stand-in for it).
-cudaError_t noalloc_base(int device, void **out) {
+// Device address of g_dock_scratch on the current device (the host-side
+// symbol is only a stand-in for it).  Looked up again on every call made
+// outside a stream capture, so that a device reset (which reloads the module
+// and may move the array) never leaves a stale address; a call made during a
+// capture uses the address of the last uncaptured call on that device.
+cudaError_t noalloc_base(int device, cudaStream_t s, void **out) {
     if (device < 0 || device >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_noalloc_ptr[device]) {
+        if (cap != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
         void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_dock_scratch);
+        e = cudaGetSymbolAddress(&p, g_dock_scratch);
         if (e != cudaSuccess) return e;
         g_noalloc_ptr[device] = p;
     }
@@ -1528,7 +1544,7 @@ extern "C" int dock_noalloc_dev(adgb_ctx *c, int receptor_id, int ligand_id,
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, ADGB_EDEVICE, "cannot select device %d", c->device);
     void *base = nullptr;
-    cudaError_t e = noalloc_base(c->device, &base);
+    cudaError_t e = noalloc_base(c->device, (cudaStream_t)stream, &base);
     if (e != cudaSuccess) return cuda_fail(c, e, "dock_noalloc: scratch address");
     DockScratch w;
     noalloc_layout(&w, (unsigned char *)base, d.n_runs * d.pop, G, d.n_runs);

@@ -394,7 +394,26 @@ __global__ void rescore_fp64_kernel(const RecDev R, const LigDev L, int n, const
     if (lane == 0) out[pose] = e;
 }
 
+// Raw Philox4x32-10 words: in [n][6] = (counter 0-3, key 0-1), out [n][4].
+__global__ void philox_kernel(const uint32_t *in, int n, uint32_t *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t *c = in + (size_t)i * 6;
+    const Philox4 o = philox4x32_10(c[0], c[1], c[2], c[3], c[4], c[5]);
+    uint32_t *d = out + (size_t)i * 4;
+    d[0] = o.x;
+    d[1] = o.y;
+    d[2] = o.z;
+    d[3] = o.w;
+}
+
 }  // namespace
+
+cudaError_t launch_philox(const uint32_t *in, int n, uint32_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    philox_kernel<<<(n + 255) / 256, 256, 0, s>>>(in, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_init_population(const RecDev &rec, int n_tors, uint64_t seed, int n_runs, int pop,
                                    float *genes, int *iters, cudaStream_t s) {

@@ -58,3 +58,18 @@ def test_two_gloo_ranks_agree_on_the_slowest_time():
         assert t == pytest.approx(2.5)
         assert rate == pytest.approx(2 * 1000 / 2.5)
         assert printed == ""
+
+
+def test_bench_gpus_2_launches_two_ranks():
+    """`bench.py --gpus 2` re-runs itself as two ranks (torch.distributed.run
+    on 127.0.0.1; gloo without CUDA) and reports n_gpus = the ranks run."""
+    import json
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                          "--dry-run", "--steps", "2"], capture_output=True, text=True,
+                         timeout=240, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    rec = json.loads(lines[0])
+    assert rec["n_gpus"] == 2 and rec["dry_run"] is True

@@ -57,6 +57,27 @@ def ang(a, b):
     return (a - b + np.pi) % (2 * np.pi) - np.pi
 
 
+def test_philox_device_known_answer_vectors(pkg, torch, philox_kat):
+    """The device generator (philox.cuh) gives the published Philox4x32-10
+    known-answer words (Salmon et al., SC'11; tests/golden) and the oracle's
+    words on 4096 seeded random counters and keys, bit for bit."""
+    kat = philox_kat
+    rng = np.random.default_rng(2410)
+    rand = rng.integers(0, 1 << 32, size=(4096, 6), dtype=np.uint64)
+    inp = np.array([c + k for c, k, _ in kat] + rand.tolist(), np.uint64).astype(np.uint32)
+    ctx = pkg.Context(0)
+    dev_in = torch.from_numpy(inp.view(np.int32)).cuda()
+    dev_out = torch.empty(inp.shape[0], 4, dtype=torch.int32, device="cuda")
+    ctx.philox4x32_10_dev(dev_in, dev_out)
+    got = dev_out.cpu().numpy().view(np.uint32)
+    for i, (_, _, want) in enumerate(kat):
+        assert got[i].tolist() == want
+    for i in range(len(kat), inp.shape[0]):
+        want = oracle.philox(inp[i, :4].tolist(), inp[i, 4:].tolist())
+        assert got[i].tolist() == list(want), i
+    ctx.philox4x32_10_dev(dev_in[:0], dev_out[:0])      # n = 0 is a no-op
+
+
 def test_initial_population_matches_oracle(pkg, torch, w):
     ctx = pkg.Context(0)
     rid = ctx.upload_receptor_grids(w["receptor"])

@@ -1,8 +1,9 @@
 """Pins of the oracle's Lamarckian GA pieces (Sec. 2.1; the rules are this
-project's reading, stated in oracle/adgb_oracle.c): properties every
-generation must have, whatever the random stream, plus statistics of the
-Philox4x32-10 stream.  Cross-implementation agreement with the CUDA
-library is checked by the GPU tests."""
+project's reading, stated in oracle/adgb_oracle.c): the Philox4x32-10
+generator against its published known-answer vectors, properties every
+generation must have whatever the random stream, and statistics of the
+stream.  Cross-implementation agreement with the CUDA library is checked by
+the GPU tests."""
 import math
 
 import numpy as np
@@ -14,6 +15,16 @@ import synth
 @pytest.fixture(scope="module")
 def w():
     return synth.workload("plain_n16", n_poses=40)
+
+
+def test_philox_known_answer_vectors(oracle_mod, philox_kat):
+    # Salmon et al. (SC'11) publish these words with their reference
+    # implementation; a swapped round multiplier, a wrong Weyl key increment
+    # or a key bumped before the first round changes every output word
+    kat = philox_kat
+    assert len(kat) == 3
+    for ctr, key, want in kat:
+        assert list(oracle_mod.philox(ctr, key)) == want, (ctr, key)
 
 
 def test_philox_statistics(oracle_mod):

@@ -1,6 +1,7 @@
 """Host-side pair schedule (no GPU): the library splits the intramolecular
-pair list (the pair sum of Eq. 1) into rounds in which each lane (atom)
-computes at most one pair and receives the reaction forces of at most two
+pair list (the pair sum in Sec. 2.1's scoring function; the schedule has no
+paper counterpart) into rounds in which each lane (atom) computes at most
+one pair and receives the reaction forces of at most two
 pairs; 32 lanes up to 32 atoms (one warp), the atoms rounded up to 32 above
 112 atoms (a block of threads), none between (the force buffer is faster).
 Checked here from the exported round words alone: every caller pair exactly
