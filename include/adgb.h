@@ -84,6 +84,10 @@ typedef struct {
     int pair_rounds;       /* intramolecular pairs: 0 = matching rounds (ligand_pair_rounds;
                               the default, faster at every size measured), 1 = per-pair
                               force buffer and incidence lists */
+    int genotypes_per_warp; /* ligands of at most 32 atoms (with matching rounds, at most 26
+                              torsions, one warp a genotype's atoms): 0 = two genotypes a
+                              warp, their arithmetic in packed FP32x2 instructions (the
+                              default), 1 = one genotype a warp */
 } adgb_options;
 
 /* Receptor grid (Sec. 2.1: the receptor is fixed; its interaction with a
@@ -543,6 +547,28 @@ int reduce4_bench_dev(adgb_ctx *ctx, int variant, const float *in_dev,
  */
 int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, float *out_dev,
                   adgb_stream stream);
+
+/*
+ * ls_ablation_dev - measurement aid with no counterpart in the paper: the
+ * two-genotypes-a-warp local search of local_search_dev with some of its
+ * steps left out at compile time, so that a step's share of the time is the
+ * difference to the whole search.  The outputs are NOT energies or searched
+ * genotypes.  skip_mask (values built): 0 (nothing left out), 1 (pair
+ * rounds), 2 (grid terms), 12 (the reduce-and-broadcast and the torsions'
+ * moving-set sums: each lane keeps its own partials), 8 (the moving-set sums
+ * of the shuffle form), 16 (the torsion-tree walk of the coordinates), 32
+ * (the gene-gradient formulas), 64 (sines and cosines: zero angles), 3
+ * (pairs and grid), 128 (the pair terms' arithmetic, the exchanges kept),
+ * 256 (the pair rounds' shuffles, the arithmetic kept).
+ * variant: ADGB_REDUCE_SHFL or ADGB_REDUCE_TCGEN05.  genes_dev [n][6+T]
+ * in/out, best_energy_dev [n] out, on `stream`.  The ligand must run two
+ * genotypes a warp (at most 32 atoms with matching rounds, at most 26
+ * torsions, the context's default launch shape).  Errors: EINVAL (other
+ * masks, variants or ligands), ENOTFOUND, EDEVICE.
+ */
+int ls_ablation_dev(adgb_ctx *ctx, int receptor_id, int ligand_id, float *genes_dev, int n,
+                    int iters, int variant, int skip_mask, float *best_energy_dev,
+                    adgb_stream stream);
 
 /*
  * philox4x32_10_dev - the counter-based generator every random decision of

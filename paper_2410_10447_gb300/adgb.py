@@ -39,7 +39,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget",
-           "philox4x32_10_dev"]
+           "philox4x32_10_dev", "ls_ablation_dev"]
 MAX_GENES = 46
 
 
@@ -51,7 +51,8 @@ class AdgbError(RuntimeError):
 
 class _Options(C.Structure):
     _fields_ = [("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
-                ("reduce_variant", C.c_int), ("pair_rounds", C.c_int)]
+                ("reduce_variant", C.c_int), ("pair_rounds", C.c_int),
+                ("genotypes_per_warp", C.c_int)]
 
 
 class _Grid(C.Structure):
@@ -202,6 +203,8 @@ def load(build: bool = False):
     L.ga_converged_dev.argtypes = [vp, C.POINTER(_DockParams), vp, vp, vp]
     L.alu_bench_dev.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.philox4x32_10_dev.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.ls_ablation_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                  vp, vp]
     _lib = L
     return L
 
@@ -283,10 +286,12 @@ class Context:
     """One adgb context on one CUDA device."""
 
     def __init__(self, device: int = 0, threads_per_pose: int = 0, poses_per_block: int = 0,
-                 reduce_variant: int = REDUCE_SHFL, pair_rounds: int = 0):
+                 reduce_variant: int = REDUCE_SHFL, pair_rounds: int = 0,
+                 genotypes_per_warp: int = 0):
         self.lib = load()
         self.h = C.c_void_p()
-        opts = _Options(threads_per_pose, poses_per_block, reduce_variant, pair_rounds)
+        opts = _Options(threads_per_pose, poses_per_block, reduce_variant, pair_rounds,
+                        genotypes_per_warp)
         rc = self.lib.adgb_create(C.byref(self.h), device, C.byref(opts))
         if rc != ADGB_OK:
             raise AdgbError(rc, "adgb_create(device=%d)" % device)
@@ -354,6 +359,15 @@ class Context:
         self._chk(self.lib.local_search_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
                                             C.byref(p), _ptr(best_energy), _ptr(state),
                                             _stream()))
+
+    def ls_ablation_dev(self, rid, lid, genes, best_energy, iters, variant, skip_mask):
+        """Measurement aid: the two-genotypes-a-warp local search with the steps
+        in skip_mask left out (outputs are not energies)."""
+        _check_dev(genes, "genes")
+        _check_dev(best_energy, "best_energy")
+        self._chk(self.lib.ls_ablation_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
+                                           int(iters), int(variant), int(skip_mask),
+                                           _ptr(best_energy), _stream()))
 
     def reduce4_bench_dev(self, variant, x, threads, reps=1, out=None):
         import torch

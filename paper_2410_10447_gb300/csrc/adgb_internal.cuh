@@ -168,6 +168,54 @@ struct SmemLayout {
     }
 };
 
+// Shared-memory layout of the two-genotypes-a-warp kernel (ligands of at
+// most 32 atoms): the ligand's constants once, then per warp the two
+// genotypes' coordinates (atom i: [2i] genotype A, [2i+1] genotype B), genes
+// (float2 per gene) and sin / (1 - cos) of every angle (float4: A's pair,
+// B's pair), a staging tile, and the lanes' grid-cell corner copies.  All offsets in
+// bytes from the layout's base, 16-byte aligned.
+struct PairSmem {
+    int ref, type, frag, tparent, tatoms, taxis, tbref;
+    int warp0, warp_stride;
+    int w_xyz, w_genes, w_sc, w_stage, w_grid;
+    int total;
+
+    static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
+
+    // stage: room for the warp's 32 x 12-float staging tile (the mma.sync
+    // reductions and the shuffle form's torsion sums; not the tcgen05 form);
+    // grid: room for the lanes' grid-corner copies (the tcgen05 form)
+    __host__ __device__ inline void make(int N, int T, int warps, bool stage, bool grid) {
+        const int Tn = T > 0 ? T : 1;
+        int o = 0;
+        ref = o;     o = al16(o + 16 * N);
+        type = o;    o = al16(o + 4 * N);
+        frag = o;    o = al16(o + 4 * N);
+        tparent = o; o = al16(o + 4 * Tn);
+        tatoms = o;  o = al16(o + 16 * Tn);
+        taxis = o;   o = al16(o + 16 * Tn);
+        tbref = o;   o = al16(o + 16 * Tn);
+        warp0 = o;
+        int q = 0;
+        w_xyz = q;   q = al16(q + 32 * 32);
+        w_genes = q; q = al16(q + 8 * MAX_GENES);
+        w_sc = q;    q = al16(q + 16 * (ADGB_MAX_TORS + 4));
+        w_stage = q; q = al16(q + (stage ? 4 * 32 * 12 : 0));
+        w_grid = q;  q = al16(q + (grid ? 2 * 6 * 32 * 16 : 0));
+        warp_stride = q;
+        total = warp0 + warps * warp_stride;
+    }
+};
+
+// Whether a ligand runs two genotypes a warp: at most 32 atoms with the
+// warp form of the matching rounds (or no pairs), at most 32 genes (one gene
+// slot a lane), one warp a genotype.
+__host__ __device__ inline bool pair_eligible(int n_atoms, int n_tors, int n_pairs, int n_rounds,
+                                              int r_lanes, int tpp) {
+    return tpp == 32 && n_atoms <= 32 && 6 + n_tors <= 32 &&
+           (n_pairs == 0 || (n_rounds > 0 && r_lanes == 32));
+}
+
 // Threads a genotype by ligand size (one warp up to 32 atoms, two up to 56,
 // else 128; measured on 3000 genotypes, see the local-search launch-shape
 // sweep): the single-ligand calls and the serving loop's size classes alike.
@@ -202,6 +250,7 @@ struct EvalCfg {
     int variant;    // ADGB_REDUCE_*
     int chunk;      // pairs per force-buffer chunk
     int stage_pairs;  // copy the pair list and incidence lists to shared memory
+    int paired;     // two genotypes a warp where the ligand is eligible (pair_eligible)
 };
 
 // Host-side launchers (eval.cu, reduce_bench.cu).
@@ -210,6 +259,26 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                         int iters, float rho, float eps, int resume, float *energy,
                         float *grad, float *state, cudaStream_t s,
                         const int *iters_per_pose = nullptr);
+// Two genotypes a warp (pair_eligible ligands only; EvalCfg::paired); fail
+// (may be null) is set to 1 if a tensor-core completion wait gave up.
+cudaError_t launch_eval_pair(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, int mode,
+                             const float *genes_in, float *genes_out, int n, int iters, float rho,
+                             float eps, int resume, float *energy, float *grad, float *state,
+                             cudaStream_t s, const int *iters_per_pose, int *fail);
+int pair_smem_bytes(int layout_bytes, int warps, int variant, int device);
+// Measurement-only paired local search without the steps in `skip`
+// (ls_ablation_dev); cudaErrorInvalidValue for masks or variants not built.
+cudaError_t launch_pair_ablation(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
+                                 float *genes, int n, int iters, float *energy, cudaStream_t s,
+                                 int skip);
+int pair_layout_bytes(int n_atoms, int n_tors, int ppb, int variant);
+int pair_items_grid(const EvalCfg &cfg, int budget, int device);
+cudaError_t launch_eval_pair_items(const WorkItem *items, int n_items, const LigDev *ligs,
+                                   const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
+                                   int grid, cudaStream_t s, int *fail);
+// Shared-memory bytes of one ligand's layout in a multi-ligand launch of
+// shape cfg (the launch's budget is the largest over its ligands).
+int items_layout_bytes(const EvalCfg &cfg, int n_atoms, int n_tors, int n_pairs);
 // Solis-Wets searches; budget [n] (evaluations each genotype may spend) or
 // null for c.max_evals; evals [n] receives the evaluations spent (it may be
 // the budget array itself).
@@ -272,5 +341,6 @@ int ctx_device(const adgb_ctx *c);
 int ctx_default_variant(const adgb_ctx *c);
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps);
 int ctx_pair_rounds(const adgb_ctx *c);
+int ctx_genotypes_per_warp(const adgb_ctx *c);
 
 }  // namespace adgb

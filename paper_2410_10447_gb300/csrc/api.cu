@@ -51,7 +51,7 @@ struct Batch {
     // what the captured graph was built for
     const float *k_genes = nullptr;
     const float *k_energy = nullptr;
-    int k_iters = -1, k_tpp = 0, k_ppb = 0, k_var = -1, budget = 0, grid = 0;
+    int k_iters = -1, k_tpp = 0, k_ppb = 0, k_var = -1, k_paired = -1, budget = 0, grid = 0;
     float k_rho = 0.f, k_eps = 0.f;
 };
 }  // namespace
@@ -684,6 +684,8 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
         if (lay.total <= 100 * 1024 || ppb == 1) break;
     }
     cfg.ppb = ppb;
+    cfg.paired = c->opts.genotypes_per_warp == 0 &&
+                 pair_eligible(L.n_atoms, L.n_tors, L.n_pairs, L.dev.n_rounds, L.dev.r_lanes, cfg.tpp);
     return cfg;
 }
 
@@ -877,6 +879,7 @@ int ctx_device(const adgb_ctx *c) { return c->device; }
 int ctx_default_variant(const adgb_ctx *c) { return c->opts.reduce_variant; }
 
 int ctx_pair_rounds(const adgb_ctx *c) { return c->opts.pair_rounds; }
+int ctx_genotypes_per_warp(const adgb_ctx *c) { return c->opts.genotypes_per_warp; }
 
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps) {
     auto it = c->recs.find(rid);
@@ -906,7 +909,8 @@ int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts) {
     }
     if (c->opts.poses_per_block < 0 || c->opts.poses_per_block > 8 ||
         c->opts.reduce_variant < 0 || c->opts.reduce_variant >= ADGB_REDUCE_N ||
-        c->opts.pair_rounds < 0 || c->opts.pair_rounds > 1) {
+        c->opts.pair_rounds < 0 || c->opts.pair_rounds > 1 || c->opts.genotypes_per_warp < 0 ||
+        c->opts.genotypes_per_warp > 1) {
         delete c;
         return ADGB_EINVAL;
     }
@@ -1445,6 +1449,27 @@ int alu_bench_dev(adgb_ctx *c, int kind, int n_blocks, int threads, int reps, fl
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "alu_bench");
 }
 
+int ls_ablation_dev(adgb_ctx *c, int receptor_id, int ligand_id, float *genes_dev, int n, int iters,
+                    int variant, int skip_mask, float *best_energy_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if (n < 0 || iters < 0 || skip_mask < 0 || (n > 0 && (!genes_dev || !best_energy_dev)))
+        return fail(c, ADGB_EINVAL, "ls_ablation: bad arguments");
+    if (variant != ADGB_REDUCE_SHFL && variant != ADGB_REDUCE_TCGEN05)
+        return fail(c, ADGB_EINVAL, "ls_ablation: variant %d not built (shuffle and tcgen05 only)", variant);
+    Receptor *R = nullptr;
+    Ligand *L = nullptr;
+    int rc = lookup(c, receptor_id, ligand_id, &R, &L);
+    if (rc) return rc;
+    EvalCfg cfg = pick_cfg(c, *L, variant);
+    if (!pair_eligible(L->n_atoms, L->n_tors, L->n_pairs, L->dev.n_rounds, L->dev.r_lanes, cfg.tpp))
+        return fail(c, ADGB_EINVAL, "ls_ablation: the ligand does not run two genotypes a warp");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_pair_ablation(R->dev, L->dev, cfg, genes_dev, n, iters, best_energy_dev,
+                                         (cudaStream_t)stream, skip_mask);
+    if (e == cudaErrorInvalidValue) return fail(c, ADGB_EINVAL, "ls_ablation: mask %d not built", skip_mask);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ls_ablation");
+}
+
 int philox4x32_10_dev(adgb_ctx *c, const unsigned int *in_dev, int n, unsigned int *out_dev,
                       adgb_stream stream) {
     if (!c) return ADGB_EINVAL;
@@ -1562,9 +1587,16 @@ namespace {
 int batch_budget(const Batch &b, const EvalCfg &cfg) {
     int budget = 1024;
     for (size_t u = 0; u < b.ligs.size(); u++)
-        budget = std::max(budget, SmemLayout::choose(b.lig_n[u], b.lig_t[u], b.lig_np[u], cfg.ppb,
-                                                     cfg.tpp / 32, uses_mma_stage(cfg.variant)).total);
+        budget = std::max(budget, items_layout_bytes(cfg, b.lig_n[u], b.lig_t[u], b.lig_np[u]));
     return budget;
+}
+
+// Two genotypes a warp only when every ligand of the batch qualifies (one
+// launch shape serves the whole batch).
+bool batch_pairable(const Batch &b, const EvalCfg &cfg) {
+    for (const LigDev &l : b.ligs)
+        if (!pair_eligible(l.n_atoms, l.n_tors, l.n_pairs, l.n_rounds, l.r_lanes, cfg.tpp)) return false;
+    return true;
 }
 
 // Items of ppb genotypes of one ligand, longest (most work) first.
@@ -1667,6 +1699,7 @@ extern "C" int batch_create(adgb_ctx *c, int n_items, const int *receptor_ids, c
         return fail(c, ADGB_ENOMEM, "batch_create: %s", cudaGetErrorString(e));
     }
     b.cfg.variant = c->opts.reduce_variant;
+    b.cfg.paired = c->opts.genotypes_per_warp == 0;
     if (c->opts.threads_per_pose > 0) {   // the context's launch shape, until tuned
         b.cfg.tpp = c->opts.threads_per_pose;
         b.cfg.ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / b.cfg.tpp;
@@ -1712,10 +1745,12 @@ extern "C" int batch_local_search_dev(adgb_ctx *c, int batch_id, float *genes_de
     DeviceGuard g(c->device);
     EvalCfg cfg = b.cfg;
     if (!b.tuned || p->reduce_variant >= 0) cfg.variant = variant;
+    cfg.paired = cfg.paired && batch_pairable(b, cfg);
     cudaError_t e = cudaSuccess;
     const bool same = b.exec && b.k_genes == genes_dev && b.k_energy == best_energy_dev &&
                       b.k_iters == p->iters && b.k_rho == p->rho && b.k_eps == p->eps &&
-                      b.k_tpp == cfg.tpp && b.k_ppb == cfg.ppb && b.k_var == cfg.variant;
+                      b.k_tpp == cfg.tpp && b.k_ppb == cfg.ppb && b.k_var == cfg.variant &&
+                      b.k_paired == cfg.paired;
     if (!same) {
         if (b.exec) cudaGraphExecDestroy(b.exec);
         b.exec = nullptr;
@@ -1743,6 +1778,7 @@ extern "C" int batch_local_search_dev(adgb_ctx *c, int batch_id, float *genes_de
         b.k_tpp = cfg.tpp;
         b.k_ppb = cfg.ppb;
         b.k_var = cfg.variant;
+        b.k_paired = cfg.paired;
     }
     e = cudaGraphLaunch(b.exec, (cudaStream_t)stream);
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "batch_local_search: graph launch");
@@ -1756,10 +1792,17 @@ extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev,
     Batch &b = it->second;
     if (iters < 1 || (b.total > 0 && !genes_dev)) return fail(c, ADGB_EINVAL, "batch_autotune: bad arguments");
     DeviceGuard g(c->device);
-    const EvalCfg cands[] = {{32, 4, ADGB_REDUCE_SHFL, 1, 0}, {32, 4, ADGB_REDUCE_MMA_TF32X2, 1, 0},
-                             {32, 4, ADGB_REDUCE_MMA_BF16X3, 1, 0}, {32, 4, ADGB_REDUCE_TCGEN05, 1, 0},
-                             {32, 2, ADGB_REDUCE_SHFL, 1, 0}, {64, 2, ADGB_REDUCE_SHFL, 1, 0},
-                             {128, 1, ADGB_REDUCE_SHFL, 1, 0}};
+    // one genotype a warp (the last field 0) and, where every ligand of the
+    // batch qualifies, two genotypes a warp
+    const EvalCfg all[] = {{32, 4, ADGB_REDUCE_SHFL, 1, 0, 0}, {32, 4, ADGB_REDUCE_MMA_TF32X2, 1, 0, 0},
+                           {32, 4, ADGB_REDUCE_MMA_BF16X3, 1, 0, 0}, {32, 4, ADGB_REDUCE_TCGEN05, 1, 0, 0},
+                           {32, 2, ADGB_REDUCE_SHFL, 1, 0, 0}, {64, 2, ADGB_REDUCE_SHFL, 1, 0, 0},
+                           {128, 1, ADGB_REDUCE_SHFL, 1, 0, 0},
+                           {32, 4, ADGB_REDUCE_SHFL, 1, 0, 1}, {32, 8, ADGB_REDUCE_SHFL, 1, 0, 1},
+                           {32, 4, ADGB_REDUCE_TCGEN05, 1, 0, 1}, {32, 8, ADGB_REDUCE_TCGEN05, 1, 0, 1}};
+    std::vector<EvalCfg> cands;
+    for (const EvalCfg &cf : all)
+        if (!cf.paired || (c->opts.genotypes_per_warp == 0 && batch_pairable(b, cf))) cands.push_back(cf);
     const size_t gbytes = sizeof(float) * (size_t)b.total * (6 + ADGB_MAX_TORS);
     float *tg = nullptr, *te = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1811,6 +1854,7 @@ extern "C" int batch_autotune(adgb_ctx *c, int batch_id, const float *genes_dev,
         chosen->poses_per_block = best.ppb;
         chosen->reduce_variant = best.variant;
         chosen->pair_rounds = c->opts.pair_rounds;
+        chosen->genotypes_per_warp = best.paired ? 0 : 1;
     }
     return ADGB_OK;
 }

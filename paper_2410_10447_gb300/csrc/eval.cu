@@ -1306,9 +1306,18 @@ static cudaError_t launch_items_v(const ItemsArgs &a, int variant, int smem, int
     return cudaErrorInvalidValue;
 }
 
+int items_layout_bytes(const EvalCfg &cfg, int n_atoms, int n_tors, int n_pairs) {
+    if (cfg.paired) return pair_layout_bytes(n_atoms, n_tors, cfg.ppb, cfg.variant);
+    return SmemLayout::choose(n_atoms, n_tors, n_pairs, cfg.ppb, cfg.tpp / 32,
+                              uses_mma_stage(cfg.variant)).total;
+}
+
 cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *ligs,
                               const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
                               int grid, cudaStream_t s) {
+    if (cfg.paired)
+        return launch_eval_pair_items(items, n_items, ligs, recs, counter, cfg, budget, grid, s,
+                                      nullptr);
     ItemsArgs a;
     a.items = items;
     a.ligs = ligs;
@@ -1351,6 +1360,7 @@ static int resident_blocks(const cudaFuncAttributes &fa, const cudaDeviceProp &p
 
 // Resident blocks of the persistent launch: SMs x blocks an SM can hold.
 int items_grid(const EvalCfg &cfg, int budget, int device) {
+    if (cfg.paired) return pair_items_grid(cfg, budget, device);
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return 0;
     int per_sm = 0;
@@ -1410,6 +1420,10 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                         float eps, int resume, float *energy, float *grad, float *state,
                         cudaStream_t s, const int *iters_per_pose) {
     if (n == 0) return cudaSuccess;
+    if (cfg.paired &&
+        pair_eligible(lig.n_atoms, lig.n_tors, lig.n_pairs, lig.n_rounds, lig.r_lanes, cfg.tpp))
+        return launch_eval_pair(rec, lig, cfg, mode, genes_in, genes_out, n, iters, rho, eps,
+                                resume, energy, grad, state, s, iters_per_pose, nullptr);
     EvalArgs a;
     a.iters_pp = iters_per_pose;
     a.rec = rec;

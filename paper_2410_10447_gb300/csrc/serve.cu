@@ -36,7 +36,9 @@ using namespace adgb;
 namespace {
 
 enum { JOB_QUEUED = 1, JOB_RUNNING = 2, JOB_DONE = 0 };
-constexpr int NCLS = 3;   // ligand-size classes of the local-search launches (32, 64, 128 threads)
+// ligand-size classes of the local-search launches: two genotypes a warp
+// (pair_eligible ligands), then 32, 64 and 128 threads a genotype
+constexpr int NCLS = 4;
 
 struct Job {
     long long id = 0;
@@ -97,7 +99,9 @@ struct adgb_server {
     int device = 0;
     adgb_serve_options opts{};
     EvalCfg cfg{32, 4, 0, 1, 0};
-    bool forced_shape = false;   // threads/poses a block set by the caller: one class
+    bool forced_shape = false;   // threads/poses a block set by the caller: one class (and
+                                 // the two-genotypes-a-warp class for eligible ligands)
+    bool paired = true;          // two genotypes a warp where the ligand qualifies
     size_t budget = 0, used = 0;
     std::thread th;
     std::mutex mu;
@@ -196,16 +200,22 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
     EvalCfg ccfg[NCLS];
     for (int c = 0; c < NCLS; c++) {
         ccfg[c] = s->cfg;
-        if (!s->forced_shape) {
-            ccfg[c].tpp = 32 << c;
+        ccfg[c].paired = 0;
+        if (!s->forced_shape && c > 0) {
+            ccfg[c].tpp = 32 << (c - 1);
             ccfg[c].ppb = 128 / ccfg[c].tpp;
         }
     }
+    ccfg[0].tpp = 32;   // two genotypes a warp, the single-ligand calls' shape
+    ccfg[0].ppb = s->forced_shape ? s->cfg.ppb : 4;
+    ccfg[0].paired = 1;
     int n_items = 0;
     for (size_t u = 0; u < act.size(); u++) {
-        const int N = act[u]->lig.n_atoms;
-        const int t = threads_for_atoms(N);
-        cls[u] = s->forced_shape ? 0 : (t == 32 ? 0 : (t == 64 ? 1 : 2));
+        const LigDev &l = act[u]->lig;
+        const int t = s->forced_shape ? s->cfg.tpp : threads_for_atoms(l.n_atoms);
+        const bool pair = s->paired && pair_eligible(l.n_atoms, l.n_tors, l.n_pairs, l.n_rounds,
+                                                     l.r_lanes, t);
+        cls[u] = pair ? 0 : (s->forced_shape ? 1 : (t == 32 ? 1 : (t == 64 ? 2 : 3)));
         n_items += (act[u]->d.n_runs * act[u]->d.pop + ccfg[cls[u]].ppb - 1) / ccfg[cls[u]].ppb;
     }
     e = grow_tables(s, n_items, (int)act.size());
@@ -223,9 +233,8 @@ cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
             if (cls[u] != c) continue;
             Job *j = act[u];
             const int src = j->gen < 0 ? 0 : (j->cur ^ 1);   // population the LS works on
-            budget[c] = std::max(budget[c], SmemLayout::choose(j->lig.n_atoms, j->lig.n_tors,
-                                                               j->lig.n_pairs, cf.ppb, cf.tpp / 32,
-                                                               uses_mma_stage(cf.variant)).total);
+            budget[c] = std::max(budget[c], items_layout_bytes(cf, j->lig.n_atoms, j->lig.n_tors,
+                                                               j->lig.n_pairs));
             const int n = j->d.n_runs * j->d.pop;
             const int cost = j->lig.n_pairs + 8 * j->lig.n_atoms + 64;
             for (int p = 0; p < n; p += cf.ppb) {
@@ -439,6 +448,7 @@ int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out
     }
     s->cfg = EvalCfg{tpp, ppb, variant, 1, 0};
     s->forced_shape = s->opts.threads_per_pose > 0 || s->opts.poses_per_block > 0;
+    s->paired = ctx_genotypes_per_warp(ctx) == 0;
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
