@@ -3,14 +3,15 @@ continuous-batching server.
 
     python -m benchmarks.serve_bench [--rate 200] [--duration 60]
         [--runs 10] [--pop 150] [--evals-per-run 2.5e6] [--ls-iters 300]
-        [--pool 48] [--max-active 0] [--seed 1] [--variant -1] [--serial]
+        [--pool 48] [--max-active 0] [--seed 1] [--variant -1] [--serial] [--burst N]
 
 Jobs: ligands of 10-256 atoms and 0-40 torsions (a seeded pool, sampled
 uniformly), each against one of four resident receptors (48^3, 64^3, 80^3,
 96^3 grids at 0.375 A, 10 + 2 maps).  Prints one JSON line: offered and
 completed jobs, evaluations/s over the busy period, and the p50/p99 of
 time-to-result (submission to results ready) and of queueing delay.
---variant: the server's reduction (REDUCE_*; -1 = the context's default,
+--burst N: instead of the stream, N jobs submitted at once (the saturation
+measurement).  --variant: the server's reduction (REDUCE_*; -1 = the context's default,
 the shuffle form).  --serial: afterwards the same jobs are docked one after
 another through the plain dock() call with the shuffle reduction, and the
 line adds their wall time, evaluations/s and the served/serial ratio of
@@ -48,6 +49,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--serial", action="store_true")
+    ap.add_argument("--burst", type=int, default=0)
     a = ap.parse_args(argv)
     P.load(build=True)
     w = synth.WORKLOADS["serving"]
@@ -64,8 +66,8 @@ def main(argv=None):
     rids = [ctx.upload_receptor_grids(r) for r in recs]
     srv = P.Server(ctx, max_active_jobs=a.max_active, reduce_variant=a.variant)
     # arrival times and job choices, all seeded
-    n_jobs = rng.poisson(a.rate * a.duration)
-    arrivals = np.sort(rng.uniform(0.0, a.duration, n_jobs))
+    n_jobs = a.burst if a.burst else rng.poisson(a.rate * a.duration)
+    arrivals = np.zeros(n_jobs) if a.burst else np.sort(rng.uniform(0.0, a.duration, n_jobs))
     choice = rng.integers(0, a.pool, n_jobs)
     recv = rng.integers(0, len(rids), n_jobs)
     gens = int(a.evals_per_run // (a.pop * a.ls_iters)) + 2

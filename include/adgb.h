@@ -436,17 +436,27 @@ int batch_release(adgb_ctx *ctx, int batch_id);
 /*
  * Serving: continuous batching of docking jobs.
  *
- * serve_start creates a server on ctx's device with its own host thread and
- * stream.  The thread runs ticks; a tick advances every active job by one
- * step of its Lamarckian GA (initial population, or one generation), runs
- * one multi-ligand local-search launch per ligand-size class over the
- * individuals of all active jobs, updates each job's run bests and evaluation counts, and finishes the
- * jobs whose runs are done (FP64 rescoring, results copied to host, device
- * memory released).  Queued jobs are admitted in arrival order whenever
- * their device memory fits the server's budget and the active-job cap.
- * Populations, ligands and counters stay on the device between ticks.  A
- * job's results do not depend on the other jobs in the mix (the same bits
- * alone or batched).
+ * serve_start creates a server on ctx's device with its own host thread.
+ * Every admitted job runs as an independent chain of launches on a stream of
+ * its own: initial population, then one Lamarckian-GA generation after
+ * another (GA, the generation's local searches - ADADELTA or Solis-Wets as
+ * the job's parameters say - run bests and evaluation accounting), in the
+ * kernels, launch shape and order of a dock() call of the job, so a served
+ * job returns the same bits as dock() and the same bits alone or among other
+ * jobs.  The GPU interleaves the active jobs' kernels.  The server thread
+ * keeps two generations of each job queued and reads their counters from
+ * pinned memory as they land (event queries, no synchronisation); a job is
+ * done at its generation limit or once every run reached its evaluation
+ * budget or stopped early, and is then rescored in FP64, its results copied
+ * to host memory and its device memory released.  Queued jobs are admitted
+ * in arrival order while the job fits the device's free memory at that
+ * moment (plus what the library's stream-ordered pool holds unused, less a
+ * reserve of 1/64 of the device memory, at least 256 MiB), the caller's
+ * budget if one is set, and the active-job cap (by default two jobs, and
+ * more while their local searches together fill less than twice the GPU:
+ * one job's generations then cover the other's gaps, while more large jobs
+ * only compete for L2 and SMs).  Populations, ligands and
+ * counters stay on the device between generations.
  *
  * dock_submit validates the ligand and parameters on the calling thread and
  * queues the job (ADGB_EREJECTED if it can never fit the budget or the
@@ -456,7 +466,8 @@ int batch_release(adgb_ctx *ctx, int batch_id);
  * best genotypes [n_runs][6+T], FP64 best energies [n_runs] and evaluation
  * counts [n_runs] (ADGB_ETIMEOUT while it is queued or running, the job's
  * error status if it did not finish); dock_cancel asks for cancellation
- * (queued: dropped; running: dropped at the end of the current tick);
+ * (queued: dropped; running: no further generation is queued and the job
+ * ends once those in flight have completed);
  * dock_forget frees the host record of a job that is no longer queued or
  * running.  serve_stop cancels all jobs, joins the thread and frees the
  * server.  The submit/poll/wait/result/cancel calls may come from any host
@@ -467,10 +478,11 @@ int batch_release(adgb_ctx *ctx, int batch_id);
 typedef struct adgb_server adgb_server;
 
 typedef struct {
-    int max_active_jobs;          /* 0: limited by the memory budget only */
-    long long mem_budget_bytes;   /* 0: a quarter of the free device memory at start */
-    int threads_per_pose;         /* 0: by ligand size (32 up to 32 atoms, 64 up to 56, else 128) */
-    int poses_per_block;          /* 0: 128 / threads_per_pose */
+    int max_active_jobs;          /* 0: two jobs, more while their local searches together need
+                                     fewer resident warps than two GPU-fulls (16 warps an SM) */
+    long long mem_budget_bytes;   /* 0: the device's free memory at each admission (less a reserve) */
+    int threads_per_pose;         /* 0: the context's rule (by ligand size unless its options set it) */
+    int poses_per_block;          /* 0: the context's rule */
     int reduce_variant;           /* -1: the context default */
 } adgb_serve_options;
 
@@ -484,7 +496,8 @@ typedef struct {
 
 typedef struct {
     int queued, active;
-    long long ticks, items_run;
+    long long ticks;       /* generations queued (initial populations included), all jobs */
+    long long items_run;   /* genotypes of those generations */
     long long device_bytes_in_use, device_bytes_budget;
     double busy_s, uptime_s;
 } adgb_serve_stats;

@@ -100,7 +100,7 @@ def dock_params(**kw) -> _DockParams:
 class _ServeOptions(C.Structure):
     _fields_ = [("max_active_jobs", C.c_int), ("mem_budget_bytes", C.c_longlong),
                 ("threads_per_pose", C.c_int), ("poses_per_block", C.c_int),
-                ("reduce_variant", C.c_int), ("pair_rounds", C.c_int)]
+                ("reduce_variant", C.c_int)]
 
 
 class _JobInfo(C.Structure):

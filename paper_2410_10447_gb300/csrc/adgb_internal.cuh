@@ -297,6 +297,12 @@ cudaError_t launch_ga_generation(const DockCfg &d, int G, int gen, const float *
 cudaError_t launch_job_start(const RecDev &rec, int n_tors, const DockCfg &d, DockScratch &w,
                              cudaStream_t s);
 cudaError_t launch_job_ga(const DockCfg &d, int G, int gen, DockScratch &w, int cur, cudaStream_t s);
+// The local searches of one LGA generation (ADADELTA or Solis-Wets per
+// d.ls_method, per-individual budgets in w.iters; Solis-Wets writes back the
+// evaluations it spent), as dock() runs them.
+cudaError_t launch_dock_ls(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
+                           const DockCfg &d, float *genes, int gen, DockScratch &w,
+                           cudaStream_t s);
 cudaError_t launch_job_best(const DockCfg &d, int G, int gen, DockScratch &w, int cur,
                             float *best_genes, cudaStream_t s);
 cudaError_t launch_ga_converged(int n_runs, int pop, int top, float tol, const float *energy,
@@ -342,5 +348,9 @@ int ctx_default_variant(const adgb_ctx *c);
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps);
 int ctx_pair_rounds(const adgb_ctx *c);
 int ctx_genotypes_per_warp(const adgb_ctx *c);
+void ctx_launch_opts(const adgb_ctx *c, int *tpp, int *ppb);
+// The launch shape of a ligand (threads a genotype, genotypes a block, two
+// genotypes a warp or one); tpp_opt / ppb_opt 0 = by ligand size.
+EvalCfg launch_cfg(const LigDev &L, int tpp_opt, int ppb_opt, int variant, int genotypes_per_warp);
 
 }  // namespace adgb

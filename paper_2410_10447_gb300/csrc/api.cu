@@ -662,7 +662,12 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
     return ADGB_OK;
 }
 
-EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
+}  // namespace
+
+// The launch shape of a ligand (every single-ligand call, dock() and each
+// served job take it, so that they compute the same bits).
+EvalCfg adgb::launch_cfg(const LigDev &L, int tpp_opt, int ppb_opt, int variant,
+                         int genotypes_per_warp) {
     EvalCfg cfg;
     cfg.variant = variant;
     // one warp a genotype up to 32 atoms (one atom a lane, matching rounds),
@@ -671,8 +676,8 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
     // beats 64 x 2 from 64 atoms on (by 10% at 64, 15-20% at 80-128, more
     // with the matching rounds above 112)
     const int by_size = threads_for_atoms(L.n_atoms);
-    cfg.tpp = c->opts.threads_per_pose > 0 ? c->opts.threads_per_pose : by_size;
-    int ppb = c->opts.poses_per_block > 0 ? c->opts.poses_per_block : 128 / cfg.tpp;
+    cfg.tpp = tpp_opt > 0 ? tpp_opt : by_size;
+    int ppb = ppb_opt > 0 ? ppb_opt : 128 / cfg.tpp;
     while (ppb > 1 && cfg.tpp * ppb > 128) ppb--;
     cfg.stage_pairs = 8 * L.n_pairs <= 24 * 1024;
     cfg.chunk = std::max(1, std::min(L.n_pairs, PAIR_CHUNK));
@@ -684,9 +689,16 @@ EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
         if (lay.total <= 100 * 1024 || ppb == 1) break;
     }
     cfg.ppb = ppb;
-    cfg.paired = c->opts.genotypes_per_warp == 0 &&
-                 pair_eligible(L.n_atoms, L.n_tors, L.n_pairs, L.dev.n_rounds, L.dev.r_lanes, cfg.tpp);
+    cfg.paired = genotypes_per_warp == 0 &&
+                 pair_eligible(L.n_atoms, L.n_tors, L.n_pairs, L.n_rounds, L.r_lanes, cfg.tpp);
     return cfg;
+}
+
+namespace {
+
+EvalCfg pick_cfg(const adgb_ctx *c, const Ligand &L, int variant) {
+    return launch_cfg(L.dev, c->opts.threads_per_pose, c->opts.poses_per_block, variant,
+                      c->opts.genotypes_per_warp);
 }
 
 int check_variant(adgb_ctx *c, int &variant) {
@@ -880,6 +892,10 @@ int ctx_default_variant(const adgb_ctx *c) { return c->opts.reduce_variant; }
 
 int ctx_pair_rounds(const adgb_ctx *c) { return c->opts.pair_rounds; }
 int ctx_genotypes_per_warp(const adgb_ctx *c) { return c->opts.genotypes_per_warp; }
+void ctx_launch_opts(const adgb_ctx *c, int *tpp, int *ppb) {
+    *tpp = c->opts.threads_per_pose;
+    *ppb = c->opts.poses_per_block;
+}
 
 int ctx_receptor(adgb_ctx *c, int rid, RecDev *out, int *n_type_maps) {
     auto it = c->recs.find(rid);

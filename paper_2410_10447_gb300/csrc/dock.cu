@@ -474,6 +474,30 @@ cudaError_t launch_rescore_fp64(const RecDev &rec, const LigDev &lig, int n, con
     return cudaGetLastError();
 }
 
+// One local-search launch over every run's individuals (budgets in w.iters;
+// the Solis-Wets search writes back the evaluations it spent).
+cudaError_t launch_dock_ls(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
+                           const DockCfg &d, float *genes, int gen, DockScratch &w,
+                           cudaStream_t s) {
+    const int n = d.n_runs * d.pop;
+    if (d.ls_method == 1) {
+        SwCfg c;
+        c.max_evals = 0;
+        c.max_succ = d.sw_max_succ;
+        c.max_fail = d.sw_max_fail;
+        c.resume = 0;
+        c.rho0 = d.sw_rho0;
+        c.rho_min = d.sw_rho_min;
+        c.angle_scale = d.sw_angle_scale;
+        c.seed = d.seed;
+        c.call = (uint32_t)gen & 0xFFFFu;
+        c.pose_base = 0;
+        return launch_sw(rec, lig, cfg, c, genes, n, w.energy, w.iters, nullptr, s, w.iters);
+    }
+    return launch_eval(rec, lig, cfg, MODE_LS, genes, genes, n, 0, d.rho, d.eps, 0, w.energy,
+                       nullptr, nullptr, s, w.iters);
+}
+
 cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, const DockCfg &d,
                         float *best_genes, double *best_energy, long long *evals_out,
                         DockScratch &w, cudaStream_t s) {
@@ -483,25 +507,8 @@ cudaError_t launch_dock(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     init_pop_kernel<<<(n + 127) / 128, 128, 0, s>>>(rec, lig.n_tors, d.seed, d.n_runs, d.pop,
                                                      w.genes[0], w.iters);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // one local-search launch over every run's individuals (budgets in w.iters;
-    // the Solis-Wets search writes back the evaluations it spent)
     auto local_search = [&](float *genes, int gen) -> cudaError_t {
-        if (d.ls_method == 1) {
-            SwCfg c;
-            c.max_evals = 0;
-            c.max_succ = d.sw_max_succ;
-            c.max_fail = d.sw_max_fail;
-            c.resume = 0;
-            c.rho0 = d.sw_rho0;
-            c.rho_min = d.sw_rho_min;
-            c.angle_scale = d.sw_angle_scale;
-            c.seed = d.seed;
-            c.call = (uint32_t)gen & 0xFFFFu;
-            c.pose_base = 0;
-            return launch_sw(rec, lig, cfg, c, genes, n, w.energy, w.iters, nullptr, s, w.iters);
-        }
-        return launch_eval(rec, lig, cfg, MODE_LS, genes, genes, n, 0, d.rho, d.eps, 0, w.energy,
-                           nullptr, nullptr, s, w.iters);
+        return launch_dock_ls(rec, lig, cfg, d, genes, gen, w, s);
     };
     if ((e = local_search(w.genes[0], 0)) != cudaSuccess) return e;
     const int bt = 128;

@@ -1,22 +1,31 @@
 // Continuous-batching docking server (dock_submit / dock_poll / dock_wait /
 // dock_result / dock_cancel).
 //
-// One host thread drives the device through its own stream in ticks.  A tick
-// advances every active job by one step of its Lamarckian GA: new jobs get
-// their initial population, the others one GA generation (per-job launches);
-// then ONE persistent multi-ligand local-search launch runs the individuals
-// of all active jobs together (work items of the jobs' ligands against their
-// receptors); then each job's run bests and evaluation counts are updated.
-// A job whose runs are all done is rescored in FP64, its results copied to
-// host memory and its device memory released; queued jobs are admitted in
-// arrival order as soon as the device-memory budget allows.  Populations,
-// ligands, counters and RNG state (counter-based, nothing to store) stay on
-// the device between ticks.
+// Every admitted job is an independent chain of launches on a stream of its
+// own: its initial population and then one Lamarckian-GA generation after
+// another (GA, the generation's local searches, run bests and evaluation
+// accounting) - the same kernels, launch shape and order as one dock() call
+// of the job, so a served job returns exactly the bits dock() returns.  The
+// GPU interleaves the blocks of all active jobs' kernels; no job waits for
+// another's generation.
 //
-// A job's arithmetic does not depend on the other jobs in the launch: the
-// kernels are per individual, the shared-memory layout of a ligand depends
-// on the ligand alone, and the GA stream is keyed by the job's seed.  A job
-// therefore returns the same bits alone and in any mix.
+// One host thread feeds the streams: it keeps two generations of each job in
+// flight (the next one is queued before the previous one's counters have
+// been read), reads a generation's evaluation counts and stop flags from
+// pinned memory once its event has completed (cudaEventQuery, never a
+// stream or device synchronisation), and when a job is done - its generation
+// limit, or every run at its evaluation budget or stopped early - queues the
+// FP64 rescoring and the copies of the results, publishes them once those
+// land, and frees the job's stream-ordered device memory.  A generation
+// queued after a job's runs had all stopped changes nothing (stopped runs
+// keep their population and do no evaluations).
+//
+// Admission is first come, first served while the job fits the device's
+// live free memory (cudaMemGetInfo plus what the stream-ordered pool holds
+// unused, less a reserve), the caller's budget if it set one, and the
+// active-job cap (by default: two jobs, more while their local searches
+// together need less than two GPUs' worth of resident warps).  Populations, ligands and counters stay on the device
+// between generations; random numbers are counter-based (nothing to store).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -36,9 +45,14 @@ using namespace adgb;
 namespace {
 
 enum { JOB_QUEUED = 1, JOB_RUNNING = 2, JOB_DONE = 0 };
-// ligand-size classes of the local-search launches: two genotypes a warp
-// (pair_eligible ligands), then 32, 64 and 128 threads a genotype
-constexpr int NCLS = 4;
+constexpr int IN_FLIGHT = 2;   // generations of a job queued ahead of the host
+
+// A pinned host buffer from the server's pool (host memory that the device
+// copies into asynchronously; reused, freed when the server stops).
+struct Pinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
 
 struct Job {
     long long id = 0;
@@ -48,14 +62,26 @@ struct Job {
     LigandBlob blob;
     LigDev lig{};
     DockCfg d{};
-    int G = 0, cur = 0, gen = -1;   // gen -1: initial population not yet scored (server thread)
-    int gen_pub = 0;                // generations done, published under the server lock
+    EvalCfg cfg{};
+    int G = 0;
     size_t bytes = 0;
+    double fill = 0;   // resident warps its local-search launch needs, in GPU-fulls
+    // server thread only
     unsigned char *mem = nullptr;
     DockScratch w{};
     float *d_best_genes = nullptr;
     double *d_best_e = nullptr;
-    long long *h_evals = nullptr;   // pinned, per run; followed by the runs' stop flags (int)
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev[IN_FLIGHT] = {}, ev_fin = nullptr;
+    Pinned cnt;        // [IN_FLIGHT][runs] evaluation counts, [IN_FLIGHT][runs] stop flags, blob
+    Pinned res;        // results: [runs][G] genes, [runs] FP64 energies, [runs] counts
+    int launched = 0;  // generations queued (0 = the initial population)
+    int processed = 0; // generations whose counters have been read
+    int cur = 0;       // population buffer of the last queued generation
+    int gen_done = 0;  // generation at which the job is complete
+    bool stop_launch = false, finishing = false, failed = false;
+    // published under the server lock
+    int gen_pub = 0;
     std::vector<float> best_genes;
     std::vector<double> best_e;
     std::vector<long long> evals;
@@ -98,11 +124,14 @@ struct adgb_server {
     adgb_ctx *ctx = nullptr;
     int device = 0;
     adgb_serve_options opts{};
-    EvalCfg cfg{32, 4, 0, 1, 0};
-    bool forced_shape = false;   // threads/poses a block set by the caller: one class (and
-                                 // the two-genotypes-a-warp class for eligible ligands)
-    bool paired = true;          // two genotypes a warp where the ligand qualifies
-    size_t budget = 0, used = 0;
+    int variant = 0, tpp_opt = 0, ppb_opt = 0, gpw = 0;
+    size_t budget = 0;           // the caller's budget (0: live free memory only)
+    size_t used = 0;             // device bytes of the admitted jobs
+    size_t reserve = 0;          // device memory admission leaves free
+    size_t total_mem = 0;
+    size_t last_avail = 0;       // the live estimate at the last admission check
+    double warps_gpu = 0;        // resident warps of the whole GPU (SMs x 16, the kernels' usual)
+    double fill_active = 0;      // sum of the active jobs' fill
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -111,228 +140,230 @@ struct adgb_server {
     std::map<long long, std::unique_ptr<Job>> jobs;
     bool stop = false;
     long long next_id = 1;
-    cudaStream_t stream = nullptr;
-    // the size classes' local-search launches run concurrently, one stream
-    // each, between two events of the main stream (tables ready / all done)
-    cudaStream_t cls_stream[NCLS] = {};
-    cudaEvent_t ev_tables = nullptr, ev_cls[NCLS] = {};
     std::chrono::steady_clock::time_point t0;
     std::string err;
-    // per-tick tables (pinned staging, device copies)
-    WorkItem *h_items = nullptr, *d_items = nullptr;
-    LigDev *h_ligs = nullptr, *d_ligs = nullptr;
-    RecDev *h_recs = nullptr, *d_recs = nullptr;
-    int cap_items = 0, cap_jobs = 0;
-    int *d_counter = nullptr;        // 2 ints per size class (work counter, finished blocks)
+    std::vector<Pinned> pinned_free;   // server thread only
+    std::vector<void *> pinned_all;
     long long ticks = 0, items_run = 0;
     double busy_s = 0;
 };
 
 namespace {
 
-cudaError_t grow_tables(adgb_server *s, int items, int njobs) {
-    cudaError_t e = cudaSuccess;
-    if (items > s->cap_items) {
-        const int cap = std::max(items, 2 * s->cap_items);
-        if (s->h_items) cudaFreeHost(s->h_items);
-        if (s->d_items) cudaFree(s->d_items);
-        s->h_items = nullptr;
-        s->d_items = nullptr;
-        e = cudaHostAlloc((void **)&s->h_items, sizeof(WorkItem) * cap, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_items, sizeof(WorkItem) * cap);
-        if (e != cudaSuccess) return e;
-        s->cap_items = cap;
+Pinned pinned_take(adgb_server *s, size_t bytes) {
+    size_t best = (size_t)-1;
+    for (size_t i = 0; i < s->pinned_free.size(); i++)
+        if (s->pinned_free[i].bytes >= bytes &&
+            (best == (size_t)-1 || s->pinned_free[i].bytes < s->pinned_free[best].bytes))
+            best = i;
+    if (best != (size_t)-1) {
+        Pinned p = s->pinned_free[best];
+        s->pinned_free.erase(s->pinned_free.begin() + best);
+        return p;
     }
-    if (njobs > s->cap_jobs) {
-        const int cap = std::max(njobs, 2 * s->cap_jobs);
-        if (s->h_ligs) cudaFreeHost(s->h_ligs);
-        if (s->h_recs) cudaFreeHost(s->h_recs);
-        if (s->d_ligs) cudaFree(s->d_ligs);
-        if (s->d_recs) cudaFree(s->d_recs);
-        s->h_ligs = nullptr;
-        s->h_recs = nullptr;
-        s->d_ligs = nullptr;
-        s->d_recs = nullptr;
-        e = cudaHostAlloc((void **)&s->h_ligs, sizeof(LigDev) * cap, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_recs, sizeof(RecDev) * cap, cudaHostAllocDefault);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_ligs, sizeof(LigDev) * cap);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_recs, sizeof(RecDev) * cap);
-        if (e != cudaSuccess) return e;
-        s->cap_jobs = cap;
+    Pinned p;
+    if (cudaHostAlloc(&p.p, bytes, cudaHostAllocDefault) == cudaSuccess) {
+        p.bytes = bytes;
+        s->pinned_all.push_back(p.p);
+    } else {
+        p.p = nullptr;
+    }
+    return p;
+}
+
+void pinned_give(adgb_server *s, Pinned &p) {
+    if (p.p) s->pinned_free.push_back(p);
+    p = Pinned{};
+}
+
+// Device memory a new job may take now: the free memory, plus what the
+// stream-ordered pool holds without using it, less the reserve.
+size_t live_available(adgb_server *s) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+    cudaMemPool_t pool;
+    unsigned long long reserved = 0, in_use = 0;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &in_use) == cudaSuccess &&
+        reserved > in_use)
+        free_b += (size_t)(reserved - in_use);
+    return free_b > s->reserve ? free_b - s->reserve : 0;
+}
+
+// Everything the job holds on the device and in the pools (server thread).
+void release_job(adgb_server *s, Job *j) {
+    if (j->mem) cudaFreeAsync(j->mem, j->stream);
+    j->mem = nullptr;
+    for (cudaEvent_t &e : j->ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (j->ev_fin) cudaEventDestroy(j->ev_fin);
+    j->ev_fin = nullptr;
+    if (j->stream) cudaStreamDestroy(j->stream);   // resources go once its work is done
+    j->stream = nullptr;
+    if (!j->failed) {   // a failed job's copies may still be in flight: its buffers stay out
+        pinned_give(s, j->cnt);
+        pinned_give(s, j->res);
+    }
+}
+
+// Device state of a newly admitted job: stream, events, memory, pinned
+// buffers, ligand blob, initial population.
+cudaError_t setup_job(adgb_server *s, Job *j) {
+    cudaError_t e = cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking);
+    for (int k = 0; k < IN_FLIGHT && e == cudaSuccess; k++)
+        e = cudaEventCreateWithFlags(&j->ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->ev_fin, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&j->mem, j->bytes, j->stream);
+    if (e != cudaSuccess) return e;
+    job_layout(*j, j->mem);
+    const int runs = j->d.n_runs;
+    j->cnt = pinned_take(s, IN_FLIGHT * (size_t)runs * 12 + j->blob.bytes.size());
+    j->res = pinned_take(s, al256(4 * (size_t)runs * j->G) + 16 * (size_t)runs);
+    if (!j->cnt.p || !j->res.p) return cudaErrorMemoryAllocation;
+    // the ligand blob through pinned memory (an asynchronous copy)
+    unsigned char *stage = (unsigned char *)j->cnt.p + IN_FLIGHT * (size_t)runs * 12;
+    std::copy(j->blob.bytes.begin(), j->blob.bytes.end(), stage);
+    e = cudaMemcpyAsync(j->mem, stage, j->blob.bytes.size(), cudaMemcpyHostToDevice, j->stream);
+    if (e == cudaSuccess) e = launch_job_start(j->rec, j->lig.n_tors, j->d, j->w, j->stream);
+    return e;
+}
+
+long long *cnt_evals(const Job *j, int g) {
+    return (long long *)j->cnt.p + (size_t)(g % IN_FLIGHT) * j->d.n_runs;
+}
+int *cnt_done(const Job *j, int g) {
+    return (int *)((long long *)j->cnt.p + (size_t)IN_FLIGHT * j->d.n_runs) +
+           (size_t)(g % IN_FLIGHT) * j->d.n_runs;
+}
+
+// Queues generation g of a job (g = 0: the initial population's scoring), as
+// launch_dock orders it, then the copies of its counters and its event.
+cudaError_t queue_generation(adgb_server *s, Job *j, int g) {
+    cudaError_t e = cudaSuccess;
+    if (g > 0) {
+        e = launch_job_ga(j->d, j->G, g, j->w, j->cur, j->stream);
+        j->cur ^= 1;
+    }
+    if (e == cudaSuccess)
+        e = launch_dock_ls(j->rec, j->lig, j->cfg, j->d, j->w.genes[j->cur], g, j->w, j->stream);
+    if (e == cudaSuccess) e = launch_job_best(j->d, j->G, g, j->w, j->cur, j->d_best_genes, j->stream);
+    const int runs = j->d.n_runs;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cnt_evals(j, g), j->w.evals, 8 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cnt_done(j, g), j->w.done, 4 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(j->ev[g % IN_FLIGHT], j->stream);
+    if (e == cudaSuccess) {
+        s->ticks++;
+        s->items_run += (long long)j->d.n_runs * j->d.pop;
     }
     return e;
 }
 
-void release_job_device(adgb_server *s, Job *j) {
-    if (j->mem) cudaFreeAsync(j->mem, s->stream);
-    if (j->h_evals) cudaFreeHost(j->h_evals);
-    j->mem = nullptr;
-    j->h_evals = nullptr;
-}
-
-// One tick over the active jobs (device work on the server's stream).
-cudaError_t tick(adgb_server *s, std::vector<Job *> &act) {
-    cudaError_t e = cudaSuccess;
-    // admission work and GA generations
-    for (Job *j : act) {
-        if (j->gen < 0) {
-            if (!j->mem) {
-                e = cudaMallocAsync((void **)&j->mem, j->bytes, s->stream);
-                if (e != cudaSuccess) return e;
-                job_layout(*j, j->mem);
-                e = cudaMemcpyAsync(j->mem, j->blob.bytes.data(), j->blob.bytes.size(),
-                                    cudaMemcpyHostToDevice, s->stream);
-                if (e == cudaSuccess)
-                    e = cudaHostAlloc((void **)&j->h_evals, 12 * (size_t)j->d.n_runs, cudaHostAllocDefault);
-                if (e == cudaSuccess) e = launch_job_start(j->rec, j->lig.n_tors, j->d, j->w, s->stream);
-                if (e != cudaSuccess) return e;
-            }
-        } else {
-            e = launch_job_ga(j->d, j->G, j->gen + 1, j->w, j->cur, s->stream);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    // multi-ligand local-search launches over every active individual: one
-    // per size class (threads a genotype as for a single-ligand call),
-    // each a persistent launch over that class's work items (a job's class
-    // depends on its ligand alone)
-    std::vector<int> cls(act.size());
-    EvalCfg ccfg[NCLS];
-    for (int c = 0; c < NCLS; c++) {
-        ccfg[c] = s->cfg;
-        ccfg[c].paired = 0;
-        if (!s->forced_shape && c > 0) {
-            ccfg[c].tpp = 32 << (c - 1);
-            ccfg[c].ppb = 128 / ccfg[c].tpp;
-        }
-    }
-    ccfg[0].tpp = 32;   // two genotypes a warp, the single-ligand calls' shape
-    ccfg[0].ppb = s->forced_shape ? s->cfg.ppb : 4;
-    ccfg[0].paired = 1;
-    int n_items = 0;
-    for (size_t u = 0; u < act.size(); u++) {
-        const LigDev &l = act[u]->lig;
-        const int t = s->forced_shape ? s->cfg.tpp : threads_for_atoms(l.n_atoms);
-        const bool pair = s->paired && pair_eligible(l.n_atoms, l.n_tors, l.n_pairs, l.n_rounds,
-                                                     l.r_lanes, t);
-        cls[u] = pair ? 0 : (s->forced_shape ? 1 : (t == 32 ? 1 : (t == 64 ? 2 : 3)));
-        n_items += (act[u]->d.n_runs * act[u]->d.pop + ccfg[cls[u]].ppb - 1) / ccfg[cls[u]].ppb;
-    }
-    e = grow_tables(s, n_items, (int)act.size());
-    if (e != cudaSuccess) return e;
-    for (size_t u = 0; u < act.size(); u++) {
-        s->h_ligs[u] = act[u]->lig;
-        s->h_recs[u] = act[u]->rec;
-    }
-    int k = 0, first[NCLS], count[NCLS], budget[NCLS];
-    for (int c = 0; c < NCLS; c++) {
-        first[c] = k;
-        budget[c] = 1024;
-        const EvalCfg &cf = ccfg[c];
-        for (size_t u = 0; u < act.size(); u++) {
-            if (cls[u] != c) continue;
-            Job *j = act[u];
-            const int src = j->gen < 0 ? 0 : (j->cur ^ 1);   // population the LS works on
-            budget[c] = std::max(budget[c], items_layout_bytes(cf, j->lig.n_atoms, j->lig.n_tors,
-                                                               j->lig.n_pairs));
-            const int n = j->d.n_runs * j->d.pop;
-            const int cost = j->lig.n_pairs + 8 * j->lig.n_atoms + 64;
-            for (int p = 0; p < n; p += cf.ppb) {
-                WorkItem &w = s->h_items[k++];
-                w.lig = (int)u;
-                w.rec = (int)u;
-                w.count = std::min(cf.ppb, n - p);
-                w.gstride = j->G;
-                w.genes = j->w.genes[src] + (size_t)p * j->G;
-                w.energy = j->w.energy + p;
-                w.iters = j->w.iters + p;
-                w.iters_all = 0;
-                w.cost = cost;
-                w.rho = j->d.rho;
-                w.eps = j->d.eps;
-            }
-        }
-        count[c] = k - first[c];
-        std::stable_sort(s->h_items + first[c], s->h_items + k, [](const WorkItem &x, const WorkItem &y) {
-            return x.cost > y.cost;
-        });
-    }
-    e = cudaMemcpyAsync(s->d_items, s->h_items, sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_ligs, s->h_ligs, sizeof(LigDev) * act.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_recs, s->h_recs, sizeof(RecDev) * act.size(), cudaMemcpyHostToDevice, s->stream);
-    if (e != cudaSuccess) return e;
-    // one persistent launch per size class, concurrently: a class with few
-    // items no longer leaves the GPU idle while it drains
-    e = cudaEventRecord(s->ev_tables, s->stream);
-    if (e != cudaSuccess) return e;
-    for (int c = 0; c < NCLS; c++) {
-        if (!count[c]) continue;
-        const int grid = items_grid(ccfg[c], budget[c], s->device);
-        if (grid < 1) return cudaErrorInvalidConfiguration;
-        e = cudaStreamWaitEvent(s->cls_stream[c], s->ev_tables, 0);
-        if (e == cudaSuccess)
-            e = launch_eval_items(s->d_items + first[c], count[c], s->d_ligs, s->d_recs,
-                                  s->d_counter + 2 * c, ccfg[c], budget[c], grid, s->cls_stream[c]);
-        if (e == cudaSuccess) e = cudaEventRecord(s->ev_cls[c], s->cls_stream[c]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_cls[c], 0);
-        if (e != cudaSuccess) return e;
-    }
-    s->items_run += n_items;
-    // accounting per job
-    for (Job *j : act) {
-        const int src = j->gen < 0 ? 0 : (j->cur ^ 1);
-        e = launch_job_best(j->d, j->G, j->gen < 0 ? 0 : j->gen + 1, j->w, src, j->d_best_genes,
-                            s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(j->h_evals, j->w.evals, 8 * j->d.n_runs, cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(j->h_evals + j->d.n_runs, j->w.done, 4 * j->d.n_runs,
-                                cudaMemcpyDeviceToHost, s->stream);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return e;
-    for (Job *j : act) {
-        if (j->gen >= 0) j->cur ^= 1;
-        j->gen += 1;
-    }
-    return cudaSuccess;
-}
-
-// Every run has stopped: generation limit, evaluation budget or early stopping.
-bool job_finished(const Job *j) {
-    if (j->gen >= j->d.max_gens) return true;
-    const int *stopped = reinterpret_cast<const int *>(j->h_evals + j->d.n_runs);
+// Every run has stopped after generation g: generation limit, evaluation
+// budget or early stopping.
+bool finished_after(const Job *j, int g) {
+    if (g >= j->d.max_gens) return true;
+    const long long *h_ev = cnt_evals(j, g);
+    const int *h_done = cnt_done(j, g);
     for (int r = 0; r < j->d.n_runs; r++)
-        if (j->h_evals[r] < j->d.max_evals && !stopped[r]) return false;
+        if (h_ev[r] < j->d.max_evals && !h_done[r]) return false;
     return true;
 }
 
-cudaError_t finish_job(adgb_server *s, Job *j) {
-    cudaError_t e = launch_rescore_fp64(j->rec, j->lig, j->d.n_runs, j->d_best_genes, j->d_best_e, s->stream);
-    j->best_genes.resize((size_t)j->d.n_runs * j->G);
-    j->best_e.resize(j->d.n_runs);
-    j->evals.resize(j->d.n_runs);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(j->best_genes.data(), j->d_best_genes, 4 * j->best_genes.size(),
-                            cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(j->best_e.data(), j->d_best_e, 8 * j->best_e.size(), cudaMemcpyDeviceToHost,
-                            s->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(j->evals.data(), j->w.evals, 8 * j->evals.size(), cudaMemcpyDeviceToHost,
-                            s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return e;
+void job_error(adgb_server *s, Job *j, cudaError_t e) {
+    j->failed = true;
+    j->stop_launch = true;
+    s->err = std::string("serving: ") + cudaGetErrorString(e);
+}
+
+// Advances one active job as far as the device allows without waiting.
+// Returns true if anything changed; sets *complete when the job is over
+// (results in its vectors, or cancelled / failed) and nothing of it is in
+// flight any more.
+bool service(adgb_server *s, Job *j, bool *complete) {
+    bool progress = false;
+    cudaError_t e = cudaSuccess;
+    *complete = false;
+    if (!j->stream && !j->failed) {
+        progress = true;
+        if ((e = setup_job(s, j)) != cudaSuccess) job_error(s, j, e);
+    }
+    // generations whose counters have landed
+    while (j->stream && j->processed < j->launched) {
+        const cudaError_t q = cudaEventQuery(j->ev[j->processed % IN_FLIGHT]);
+        if (q == cudaErrorNotReady) break;
+        if (q != cudaSuccess) {
+            job_error(s, j, q);
+            break;
+        }
+        const int g = j->processed++;
+        progress = true;
+        if (!j->stop_launch) {
+            j->gen_pub = g;
+            if (finished_after(j, g)) {
+                j->stop_launch = true;
+                j->gen_done = g;
+            }
+        }
+    }
+    if (j->cancel) j->stop_launch = true;
+    // keep IN_FLIGHT generations queued
+    while (!j->stop_launch && j->launched - j->processed < IN_FLIGHT && j->launched <= j->d.max_gens) {
+        if ((e = queue_generation(s, j, j->launched)) != cudaSuccess) {
+            job_error(s, j, e);
+            break;
+        }
+        j->launched++;
+        progress = true;
+    }
+    if (!j->stop_launch || (j->processed < j->launched && !j->failed)) return progress;
+    // nothing of the job's generations is in flight any more
+    if (j->cancel || j->failed) {
+        *complete = true;
+        return true;
+    }
+    const int runs = j->d.n_runs;
+    float *h_g = (float *)j->res.p;
+    double *h_e = (double *)((char *)j->res.p + al256(4 * (size_t)runs * j->G));
+    long long *h_v = (long long *)(h_e + runs);
+    if (!j->finishing) {
+        e = launch_rescore_fp64(j->rec, j->lig, runs, j->d_best_genes, j->d_best_e, j->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_g, j->d_best_genes, 4 * (size_t)runs * j->G, cudaMemcpyDeviceToHost, j->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_e, j->d_best_e, 8 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_v, j->w.evals, 8 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(j->ev_fin, j->stream);
+        if (e != cudaSuccess) {
+            job_error(s, j, e);
+            *complete = true;
+            return true;
+        }
+        j->finishing = true;
+        return true;
+    }
+    const cudaError_t q = cudaEventQuery(j->ev_fin);
+    if (q == cudaErrorNotReady) return progress;
+    if (q != cudaSuccess) {
+        job_error(s, j, q);
+    } else {
+        j->best_genes.assign(h_g, h_g + (size_t)runs * j->G);
+        j->best_e.assign(h_e, h_e + runs);
+        j->evals.assign(h_v, h_v + runs);
+    }
+    *complete = true;
+    return true;
 }
 
 void server_loop(adgb_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
+    double t_busy0 = -1;
     for (;;) {
-        // admission in arrival order while the memory budget allows
+        // admission in arrival order while memory and the active-job cap allow
         while (!s->queue.empty()) {
             Job *j = s->queue.front();
             if (j->cancel) {
@@ -343,51 +374,62 @@ void server_loop(adgb_server *s) {
                 continue;
             }
             if (s->opts.max_active_jobs > 0 && (int)s->active.size() >= s->opts.max_active_jobs) break;
-            if (s->used + j->bytes > s->budget) break;
+            // default: two jobs (each fills the other's gaps between its own
+            // launches), more while together they fill less than two GPUs'
+            // worth of resident warps (measured: more concurrent large jobs
+            // only compete for L2 and SMs)
+            if (s->opts.max_active_jobs == 0 && s->active.size() >= 2 &&
+                s->fill_active + j->fill > 2.0)
+                break;
+            if (s->budget > 0 && s->used + j->bytes > s->budget) break;
+            s->last_avail = live_available(s);
+            if (j->bytes > s->last_avail) break;
             s->queue.pop_front();
             s->used += j->bytes;
+            s->fill_active += j->fill;
             j->status = JOB_RUNNING;
             j->t_start = now_s(s->t0);
             s->active.push_back(j);
         }
         if (s->active.empty()) {
+            if (t_busy0 >= 0) {
+                s->busy_s += now_s(s->t0) - t_busy0;
+                t_busy0 = -1;
+            }
             if (s->stop && s->queue.empty()) break;
             s->cv_work.wait(lk);
             continue;
         }
+        if (t_busy0 < 0) t_busy0 = now_s(s->t0);
         std::vector<Job *> act = s->active;
         lk.unlock();
-        const double t_tick = now_s(s->t0);
-        cudaError_t e = tick(s, act);
-        std::vector<Job *> finished;
-        if (e == cudaSuccess) {
-            for (Job *j : act)
-                if (j->cancel || job_finished(j)) finished.push_back(j);
-            for (Job *j : finished)
-                if (!j->cancel && e == cudaSuccess) e = finish_job(s, j);
+        bool progress = false;
+        std::vector<Job *> complete;
+        for (Job *j : act) {
+            bool done = false;
+            progress |= service(s, j, &done);
+            if (done) {
+                release_job(s, j);
+                complete.push_back(j);
+            }
         }
-        for (Job *j : (e == cudaSuccess ? finished : act)) release_job_device(s, j);
-        cudaStreamSynchronize(s->stream);
         lk.lock();
-        s->busy_s += now_s(s->t0) - t_tick;
-        s->ticks++;
-        for (Job *j : act) j->gen_pub = j->gen < 0 ? 0 : j->gen;
-        if (e != cudaSuccess) {
-            s->err = std::string("serving tick: ") + cudaGetErrorString(e);
-            finished = act;
-        }
-        for (Job *j : finished) {
-            j->status = e != cudaSuccess ? (int)ADGB_EDEVICE
-                                         : (j->cancel ? (int)ADGB_ECANCELLED : (int)JOB_DONE);
+        for (Job *j : complete) {
+            j->status = j->failed ? (int)ADGB_EDEVICE
+                                  : (j->cancel ? (int)ADGB_ECANCELLED : (int)JOB_DONE);
+            if (j->status == JOB_DONE) j->gen_pub = j->gen_done;
             j->t_finish = now_s(s->t0);
             s->used -= j->bytes;
+            s->fill_active -= j->fill;
             s->active.erase(std::find(s->active.begin(), s->active.end(), j));
         }
-        if (!finished.empty()) s->cv_done.notify_all();
+        if (!complete.empty()) s->cv_done.notify_all();
         if (s->stop) {
             for (Job *j : s->active) j->cancel = true;
             for (Job *j : s->queue) j->cancel = true;
         }
+        // nothing to do until a generation lands or a job arrives
+        if (!progress && complete.empty()) s->cv_work.wait_for(lk, std::chrono::microseconds(100));
     }
 }
 
@@ -411,21 +453,6 @@ void fill_info(const adgb_server *s, const Job *j, adgb_job_info *info) {
 
 extern "C" {
 
-static void release_streams(adgb_server *s) {
-    for (int c = 0; c < NCLS; c++) {
-        if (s->cls_stream[c]) cudaStreamDestroy(s->cls_stream[c]);
-        if (s->ev_cls[c]) cudaEventDestroy(s->ev_cls[c]);
-        s->cls_stream[c] = nullptr;
-        s->ev_cls[c] = nullptr;
-    }
-    if (s->ev_tables) cudaEventDestroy(s->ev_tables);
-    if (s->d_counter) cudaFree(s->d_counter);
-    if (s->stream) cudaStreamDestroy(s->stream);
-    s->ev_tables = nullptr;
-    s->d_counter = nullptr;
-    s->stream = nullptr;
-}
-
 int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out) {
     if (!ctx || !out) return ADGB_EINVAL;
     *out = nullptr;
@@ -434,42 +461,39 @@ int serve_start(adgb_ctx *ctx, const adgb_serve_options *opts, adgb_server **out
     s->ctx = ctx;
     s->device = ctx_device(ctx);
     if (opts) s->opts = *opts;
-    const int tpp = s->opts.threads_per_pose > 0 ? s->opts.threads_per_pose : 32;
-    int ppb = s->opts.poses_per_block > 0 ? s->opts.poses_per_block : 128 / tpp;
-    if ((tpp != 32 && tpp != 64 && tpp != 128) || ppb < 1 || tpp * ppb > 128 ||
-        s->opts.max_active_jobs < 0 || s->opts.mem_budget_bytes < 0) {
+    const int tpp = s->opts.threads_per_pose, ppb = s->opts.poses_per_block;
+    if ((tpp != 0 && tpp != 32 && tpp != 64 && tpp != 128) || ppb < 0 || ppb > 8 ||
+        (tpp > 0 && ppb > 0 && tpp * ppb > 128) || s->opts.max_active_jobs < 0 ||
+        s->opts.mem_budget_bytes < 0) {
         delete s;
         return ADGB_EINVAL;
     }
-    const int variant = s->opts.reduce_variant >= 0 ? s->opts.reduce_variant : ctx_default_variant(ctx);
-    if (variant >= ADGB_REDUCE_N) {
+    s->variant = s->opts.reduce_variant >= 0 ? s->opts.reduce_variant : ctx_default_variant(ctx);
+    if (s->variant >= ADGB_REDUCE_N) {
         delete s;
         return ADGB_EINVAL;
     }
-    s->cfg = EvalCfg{tpp, ppb, variant, 1, 0};
-    s->forced_shape = s->opts.threads_per_pose > 0 || s->opts.poses_per_block > 0;
-    s->paired = ctx_genotypes_per_warp(ctx) == 0;
+    // the context's launch rule unless the server's options set one
+    ctx_launch_opts(ctx, &s->tpp_opt, &s->ppb_opt);
+    if (tpp > 0) s->tpp_opt = tpp;
+    if (ppb > 0) s->ppb_opt = ppb;
+    s->gpw = ctx_genotypes_per_warp(ctx);
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     size_t free_b = 0, total_b = 0;
-    cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    for (int c = 0; c < NCLS && e == cudaSuccess; c++) {
-        e = cudaStreamCreateWithFlags(&s->cls_stream[c], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_cls[c], cudaEventDisableTiming);
-    }
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_tables, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_counter, 2 * NCLS * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(s->d_counter, 0, 2 * NCLS * sizeof(int));
+    const cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+    if (prev >= 0) cudaSetDevice(prev);
     if (e != cudaSuccess) {
-        release_streams(s);
-        if (prev >= 0) cudaSetDevice(prev);
         delete s;
         return ADGB_EDEVICE;
     }
-    if (prev >= 0) cudaSetDevice(prev);
-    s->budget = s->opts.mem_budget_bytes > 0 ? (size_t)s->opts.mem_budget_bytes : free_b / 4;
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    s->warps_gpu = 16.0 * (sms > 0 ? sms : 1);
+    s->total_mem = total_b;
+    s->reserve = std::max<size_t>(total_b / 64, (size_t)256 << 20);
+    s->budget = (size_t)s->opts.mem_budget_bytes;
     s->t0 = std::chrono::steady_clock::now();
     s->th = std::thread(server_loop, s);
     *out = s;
@@ -489,14 +513,8 @@ int serve_stop(adgb_server *s) {
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
-    cudaStreamSynchronize(s->stream);
-    if (s->h_items) cudaFreeHost(s->h_items);
-    if (s->h_ligs) cudaFreeHost(s->h_ligs);
-    if (s->h_recs) cudaFreeHost(s->h_recs);
-    cudaFree(s->d_items);
-    cudaFree(s->d_ligs);
-    cudaFree(s->d_recs);
-    release_streams(s);
+    cudaDeviceSynchronize();   // the jobs' stream-ordered frees and copies are done
+    for (void *p : s->pinned_all) cudaFreeHost(p);
     if (prev >= 0) cudaSetDevice(prev);
     s->cv_done.notify_all();
     delete s;
@@ -512,11 +530,7 @@ int dock_submit(adgb_server *s, int receptor_id, const adgb_ligand_desc *lig,
     if (!j) return ADGB_ENOMEM;
     std::string err;
     int variant = 0;
-    int rc = dock_cfg_from_params(p, s->cfg.variant, j->d, variant, &err);
-    if (rc == ADGB_OK && j->d.ls_method != 0) {
-        rc = ADGB_EINVAL;
-        err = "dock_submit: the serving loop runs the ADADELTA local search only";
-    }
+    int rc = dock_cfg_from_params(p, s->variant, j->d, variant, &err);
     if (rc == ADGB_OK) rc = make_ligand_blob(&err, lig, ctx_pair_rounds(s->ctx), j->blob);
     int n_type_maps = 0;
     if (rc == ADGB_OK && ctx_receptor(s->ctx, receptor_id, &j->rec, &n_type_maps) != ADGB_OK) {
@@ -533,9 +547,17 @@ int dock_submit(adgb_server *s, int receptor_id, const adgb_ligand_desc *lig,
         return rc;
     }
     j->G = 6 + j->blob.rel.n_tors;
+    j->cfg = launch_cfg(j->blob.rel, s->tpp_opt, s->ppb_opt, variant, s->gpw);
     j->bytes = job_layout(*j, nullptr);
-    if (j->bytes > s->budget) {
-        s->err = "dock_submit: the job needs more device memory than the server's budget";
+    {
+        const double genotypes = (double)j->d.n_runs * j->d.pop;
+        const double warps = j->cfg.paired ? genotypes / 2 : genotypes * (j->cfg.tpp / 32);
+        j->fill = warps / s->warps_gpu;
+    }
+    const size_t limit = s->budget > 0 ? s->budget
+                                       : (s->total_mem > s->reserve ? s->total_mem - s->reserve : 0);
+    if (j->bytes > limit) {
+        s->err = "dock_submit: the job needs more device memory than the server can ever give it";
         return ADGB_EREJECTED;
     }
     if (s->stop) {
@@ -624,7 +646,7 @@ int serve_stats(adgb_server *s, adgb_serve_stats *out) {
     out->ticks = s->ticks;
     out->items_run = s->items_run;
     out->device_bytes_in_use = (long long)s->used;
-    out->device_bytes_budget = (long long)s->budget;
+    out->device_bytes_budget = (long long)(s->budget > 0 ? s->budget : s->used + s->last_avail);
     out->busy_s = s->busy_s;
     out->uptime_s = now_s(s->t0);
     return ADGB_OK;

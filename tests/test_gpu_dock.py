@@ -292,10 +292,12 @@ def test_dock_with_solis_wets(pkg, torch, w):
     _, be_o, ev_o = oracle.dock(w["receptor"], w["ligand"], oracle_params(gp8))
     assert abs(np.median(be_g) - np.median(be_o)) <= 0.15 * abs(np.median(be_o)) + 1.0, (be_g, be_o)
     assert abs(np.mean(ev_g) - np.mean(ev_o)) <= 0.25 * np.mean(ev_o)
-    # the serving loop runs ADADELTA only
+    # the serving loop runs Solis-Wets jobs as dock() does
     srv = pkg.Server(ctx)
-    with pytest.raises(pkg.AdgbError):
-        srv.submit(rid, w["ligand"], gp)
+    j = srv.submit(rid, w["ligand"], gp)
+    assert srv.wait(j, 60000)["status"] == 0
+    gs, es, vs = srv.result(j)
+    assert np.array_equal(es, be) and np.array_equal(vs, ev) and np.array_equal(gs, bg)
     srv.stop()
     ctx.close()
 

@@ -1,6 +1,6 @@
 """GPU tests of the continuous-batching server: a job returns the same bits
 alone and in a mix of other jobs (other ligands, receptors and sizes), the
-same as dock() for a ligand whose launch layout is the same, and admission,
+same bits as dock() (ADADELTA and Solis-Wets jobs), and admission,
 rejection, cancellation and waiting behave as documented.  Failures are
 made on the host (cancelled or oversized jobs); nothing faults the GPU."""
 import numpy as np
@@ -85,9 +85,32 @@ def test_job_equals_dock_call(pkg, torch, world, conv):
     if conv and conv[2] > 1e5:
         assert info["generations"] == 1      # every run converged at the first test
     gs, es, vs = srv.result(j)
+    # the same kernels, launch shape and launch order as dock(): the same bits
     assert np.array_equal(vd, vs)
-    assert np.allclose(gs, gd[:, :gs.shape[1]], atol=1e-5, rtol=0)
-    assert np.allclose(es, ed, rtol=1e-9, atol=1e-9)
+    assert np.array_equal(gs, gd[:, :gs.shape[1]])
+    assert np.array_equal(es, ed)
+    srv.stop()
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_solis_wets_job_equals_dock_call(pkg, torch, world, variant):
+    """Jobs whose local search is Solis-Wets (ls_method 1) are served too, with
+    dock()'s bits; mixed with ADADELTA jobs of other ligands."""
+    recs, ligs = world
+    ctx = pkg.Context(0)
+    rids = [ctx.upload_receptor_grids(r) for r in recs]
+    lid = ctx.upload_ligand_torsion_tree(ligs[1])
+    prm = params(pkg, 17, runs=3, pop=20, gens=3, iters=30, ls_method=1, reduce_variant=variant)
+    gd, ed, vd = ctx.dock(rids[1], lid, prm)
+    srv = pkg.Server(ctx)
+    other = srv.submit(rids[0], ligs[0], params(pkg, 18, reduce_variant=variant))
+    j = srv.submit(rids[1], ligs[1], prm)
+    assert srv.wait(j, 60000)["status"] == 0 and srv.wait(other, 60000)["status"] == 0
+    gs, es, vs = srv.result(j)
+    assert np.array_equal(vd, vs) and np.array_equal(es, ed)
+    assert np.array_equal(gs, gd[:, :gs.shape[1]])
+    assert vs.sum() > 0
     srv.stop()
     ctx.close()
 
