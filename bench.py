@@ -9,7 +9,7 @@ best/evaluation accounting), FP64 rescoring of the 20 run bests:
 20 * 150 * (1 + 27 * 300) = 24.3M energy+gradient evaluations.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adgb|reference]
-                  [--variant shfl|mma_tf32x2|mma_bf16x3]
+                  [--variant shfl|mma_tf32x2|mma_bf16x3|tcgen05] [--no-extras]
 
 Prints ONE JSON line (rank 0).  `value`: device time (CUDA events on the
 launching stream; receptor and ligand resident; L2 flushed between steps,
@@ -17,6 +17,19 @@ flush not timed).  `e2e`: the same metric through the host C calls a
 docking job makes (upload_ligand_torsion_tree, dock with host outputs,
 release_ligand).  The roofline line is for the local-search kernel (98-99%
 of the GPU time), measured from standalone launches of the same shape.
+
+After the timed region (rank 0, unless --no-extras) the line also carries:
+  variants_ls_evals_per_s   the dock's local-search launch with each
+                            reduction variant, two genotypes a warp (the
+                            default) and one genotype a warp (the plain form)
+  batch_uneven_512          one persistent graph-replayed launch of 512
+                            ligands (autotuned, shuffle, tcgen05) vs the
+                            plain form ligand by ligand
+  serving                   10 serving-mix jobs served together vs docked one
+                            after another; a Poisson stream at half the
+                            saturation rate: time-to-result p50 / p99
+  tensor_core_vs_plain_shfl the tensor-core forms over the plain FP32
+                            warp-shuffle form on the same inputs
 `--impl reference` times the FP64 CPU oracle's docking on a bounded sample.
 Multi-GPU: `--gpus N` (N > 1) re-runs the command as N ranks of one node
 (torch.distributed.run, 127.0.0.1) unless it already runs under a launcher;
@@ -232,7 +245,7 @@ def profile_traffic(kernel_sha):
 
 def kernel_sha():
     h = hashlib.sha1()
-    for f in ("eval.cu", "reduce.cuh", "tcgen05.cuh", "adgb_internal.cuh"):
+    for f in ("eval_pair.cu", "eval.cu", "reduce.cuh", "tcgen05.cuh", "adgb_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2410_10447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -296,6 +309,184 @@ def reference_arm(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_launch(torch, fn, reps=3, flush=None):
+    """Best CUDA-event time (ms) of fn() over `reps` runs after one warm-up,
+    L2 flushed before each when a flush buffer is given."""
+    ms = []
+    for r in range(reps + 1):
+        if flush is not None:
+            flush.fill_(r & 255)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return min(ms[1:])
+
+
+def ls_variants(pkg, torch, w, rid_of, flush):
+    """The local-search launch of the dock (3000 genotypes x 300 evaluations)
+    with each reduction variant, in both kernel forms: two genotypes a warp
+    (the library's default for this ligand) and one genotype a warp (the
+    plain warp-shuffle form of the method)."""
+    import synth
+    n = RUNS * POP
+    g0 = torch.from_numpy(synth.make_poses(7, n, w["receptor"], w["ligand"]["n_tors"])).cuda()
+    g = torch.empty_like(g0)
+    best = torch.empty(n, device="cuda")
+    out = {}
+    for gpw, key in ((0, "two_genotypes_a_warp"), (1, "one_genotype_a_warp")):
+        ctx = pkg.Context(torch.cuda.current_device(), genotypes_per_warp=gpw)
+        rid = ctx.upload_receptor_grids(w["receptor"])
+        lid = ctx.upload_ligand_torsion_tree(w["ligand"])
+        row = {}
+        for name, v in pkg.VARIANTS.items():
+            def run():
+                g.copy_(g0)
+                ctx.local_search_dev(rid, lid, g, best, ITERS, variant=v)
+            row[name] = n * ITERS / (time_launch(torch, run, 3, flush) / 1e3)
+        out[key] = row
+        ctx.close()
+    return out
+
+
+def batch_phase(pkg, torch, flush, iters=300, poses=64):
+    """uneven_512 (512 ligands of 10-128 atoms and 0-32 torsions, 64
+    genotypes each, 300 evaluations, 72^3 grid): one graph-replayed
+    persistent launch (autotuned shape; then with the tcgen05 reduction
+    forced) against the plain form, one single-ligand shuffle launch per
+    ligand with one genotype a warp."""
+    import numpy as np
+    import synth
+    wb = synth.WORKLOADS["uneven_512"]
+    rec = synth.make_receptor(synth.generate.BASE_SEED + wb["index"], wb["grid"], wb["n_type_maps"])
+    ligs = synth.make_uneven_batch(synth.generate.BASE_SEED + wb["index"], wb["n_ligands"],
+                                   wb["atoms"], wb["tors"], wb["n_types"])
+    genes = [synth.make_poses(7000 + i, poses, rec, L["n_tors"]) for i, L in enumerate(ligs)]
+    packed = np.zeros((len(ligs) * poses, pkg.adgb.MAX_GENES), np.float32)
+    for i, gg in enumerate(genes):
+        packed[i * poses:(i + 1) * poses, :gg.shape[1]] = gg
+    dev = torch.cuda.current_device()
+    ctx = pkg.Context(dev)
+    rid = ctx.upload_receptor_grids(rec)
+    lids = [ctx.upload_ligand_torsion_tree(L) for L in ligs]
+    g0 = torch.from_numpy(packed).cuda()
+    g = torch.empty_like(g0)
+    e = torch.empty(g0.shape[0], device="cuda")
+    bid = ctx.batch_create([rid] * len(ligs), lids, [poses] * len(ligs))
+    tuned = ctx.batch_autotune(bid, g0, iters=15)
+    evals = len(ligs) * poses * iters
+    res = {"workload": "uneven_512: 512 ligands (10-128 atoms, 0-32 torsions) x 64 genotypes x "
+                       "%d ADADELTA evaluations, 72^3 x (10+2) maps" % iters, "autotuned": tuned}
+    for name, v in (("batched_autotuned", -1), ("batched_shfl", 0), ("batched_tcgen05", 3)):
+        def run():
+            g.copy_(g0)
+            ctx.batch_local_search_dev(bid, g, e, iters, variant=v)
+        res[name + "_evals_per_s"] = evals / (time_launch(torch, run, 3, flush) / 1e3)
+    ctx.batch_release(bid)
+    ctx.close()
+    plain = pkg.Context(dev, genotypes_per_warp=1)
+    rid = plain.upload_receptor_grids(rec)
+    lids = [plain.upload_ligand_torsion_tree(L) for L in ligs]
+    gs = [torch.from_numpy(x).cuda() for x in genes]
+    gs0 = [x.clone() for x in gs]
+    es = [torch.empty(poses, device="cuda") for _ in genes]
+
+    def run_plain():
+        for i in range(len(ligs)):
+            gs[i].copy_(gs0[i])
+            plain.local_search_dev(rid, lids[i], gs[i], es[i], iters, variant=0)
+    res["plain_shfl_ligand_by_ligand_evals_per_s"] = evals / (time_launch(torch, run_plain, 1, flush) / 1e3)
+    plain.close()
+    base = res["plain_shfl_ligand_by_ligand_evals_per_s"]
+    res["batched_tcgen05_vs_plain_shfl"] = res["batched_tcgen05_evals_per_s"] / base
+    res["batched_autotuned_vs_plain_shfl"] = res["batched_autotuned_evals_per_s"] / base
+    return res
+
+
+def serving_phase(pkg, burst=10, window=30.0, pool_n=24, seed=1):
+    """The serving workload's jobs (ligands of 10-256 atoms and 0-40 torsions
+    against one of four resident receptors, 48^3-96^3 grids with 10+2 maps;
+    10 runs x 150 genotypes and 2.5e6 evaluations a run): a burst of `burst`
+    jobs served together (the saturation throughput) against the same jobs
+    docked one after another with dock(), then a Poisson stream at half the
+    saturation rate for `window` seconds (time-to-result p50 / p99)."""
+    import numpy as np
+    import synth
+    ws = synth.WORKLOADS["serving"]
+    rng = np.random.default_rng(seed)
+    recs = [synth.make_receptor(synth.generate.BASE_SEED + ws["index"] + 10 * k, n, ws["n_type_maps"])
+            for k, n in enumerate(ws["grids"])]
+    pool = []
+    for k in range(pool_n):
+        na = int(rng.integers(ws["atoms"][0], ws["atoms"][1] + 1))
+        nt = int(rng.integers(ws["tors"][0], ws["tors"][1] + 1))
+        pool.append(synth.make_ligand(90000 + k, na, ws["n_type_maps"], nt))
+    ctx = pkg.Context(0)
+    rids = [ctx.upload_receptor_grids(r) for r in recs]
+    runs, pop, evals_run, iters = 10, 150, 2_500_000, 300
+    gens = evals_run // (pop * iters) + 2
+
+    def prm(k, variant=-1):
+        return pkg.adgb.dock_params(n_runs=runs, pop=pop, max_gens=gens, max_evals=evals_run,
+                                    ls_iters=iters, seed=seed * 1_000_000 + k, reduce_variant=variant)
+    choice = rng.integers(0, pool_n, burst)
+    recv = rng.integers(0, len(rids), burst)
+    out = {"job": "10 runs x 150 genotypes, 2.5e6 evaluations a run, ligands of 10-256 atoms "
+                  "and 0-40 torsions, receptors 48^3-96^3 x (10+2) maps", "burst_jobs": burst}
+
+    def served(variant):
+        srv = pkg.Server(ctx, reduce_variant=variant)
+        t0 = time.perf_counter()
+        ids = [srv.submit(rids[recv[k]], pool[choice[k]], prm(k, variant)) for k in range(burst)]
+        infos = [srv.wait(j, -1) for j in ids]
+        wall = time.perf_counter() - t0
+        srv.stop()
+        assert all(i["status"] == 0 for i in infos)
+        return wall, sum(i["evals"] for i in infos)
+    wall_s, ev_s = served(-1)
+    wall_tc, ev_tc = served(3)
+    # the same jobs one after another: each arrives with its ligand (upload,
+    # which builds the pair schedule as dock_submit does), is docked, released
+    t_ser, ev_ser = 0.0, 0
+    for k in range(burst):
+        t1 = time.perf_counter()
+        lid = ctx.upload_ligand_torsion_tree(pool[int(choice[k])])
+        _, _, ev = ctx.dock(rids[recv[k]], lid, prm(k, 0))
+        ctx.release_ligand(lid)
+        t_ser += time.perf_counter() - t1
+        ev_ser += int(ev.sum())
+    sat = burst / wall_s
+    out.update(served_evals_per_s=ev_s / wall_s, served_tcgen05_evals_per_s=ev_tc / wall_tc,
+               serial_dock_shfl_evals_per_s=ev_ser / t_ser,
+               served_vs_serial=(ev_s / wall_s) / (ev_ser / t_ser),
+               served_tcgen05_vs_serial_shfl=(ev_tc / wall_tc) / (ev_ser / t_ser),
+               saturation_jobs_per_s=sat)
+    # Poisson arrivals at half the saturation rate
+    rate = 0.5 * sat
+    n_jobs = int(rng.poisson(rate * window))
+    arrivals = np.sort(rng.uniform(0.0, window, n_jobs))
+    ch = rng.integers(0, pool_n, n_jobs)
+    rv = rng.integers(0, len(rids), n_jobs)
+    srv = pkg.Server(ctx)
+    t0 = time.perf_counter()
+    ids = []
+    for k in range(n_jobs):
+        d = arrivals[k] - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        ids.append(srv.submit(rids[rv[k]], pool[ch[k]], prm(1000 + k)))
+    infos = [srv.wait(j, -1) for j in ids]
+    srv.stop()
+    lat = np.array([i["finish_s"] - i["submit_s"] for i in infos if i["status"] == 0])
+    out.update(poisson_rate_jobs_per_s=rate, poisson_window_s=window, poisson_jobs=n_jobs,
+               serve_p50_ms=1e3 * float(np.percentile(lat, 50)) if len(lat) else None,
+               serve_p99_ms=1e3 * float(np.percentile(lat, 99)) if len(lat) else None)
+    ctx.close()
+    return out
+
+
 def launch_ranks(n):
     """Re-runs this command as n ranks of one node (torch.distributed.run,
     rendezvous on 127.0.0.1) and returns their exit status; rank 0 prints
@@ -346,7 +537,9 @@ def main():
     ap.add_argument("--ref-runs", type=int, default=16)
     ap.add_argument("--cpu-runs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare-variants", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the reduction-variant, uneven-batch and serving phases")
+    ap.add_argument("--serve-window", type=float, default=30.0)
     ap.add_argument("--dry-run", action="store_true",
                     help="rank set-up, barrier and max-over-ranks timing of a tiny host loop "
                          "only (no GPU work; gloo without CUDA): checks the launch path")
@@ -460,18 +653,10 @@ def main():
         ls_ms.append(a.elapsed_time(b))
     ls_ms = ls_ms[1:]
     extra = {}
-    if args.compare_variants:
-        for name, vv in pkg.VARIANTS.items():
-            ms = []
-            for i in range(3):
-                gls.copy_(g0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                ctx.local_search_dev(rid, lid, gls, bls, ITERS, variant=vv)
-                b.record(stream)
-                torch.cuda.synchronize()
-                ms.append(a.elapsed_time(b))
-            extra[name] = n * ITERS / (min(ms) / 1e3)
+    if not args.no_extras and rank == 0:
+        extra["variants_ls_evals_per_s"] = ls_variants(pkg, torch, w, rid, flush)
+        extra["batch_uneven_512"] = batch_phase(pkg, torch, flush)
+        extra["serving"] = serving_phase(pkg, window=args.serve_window)
     # measured FP32 FMA and special-function throughput (after the timed region)
     probe = alu_probe(ctx, torch)
 
@@ -483,7 +668,8 @@ def main():
     clocks = clk.summary()
     roof = alu_roofline(lig, n * ITERS / launch_s, probe)
     roof["traffic"] = profile_traffic(kernel_sha())
-    roof["kernel"] = "eval_kernel (local search, 3000 genotypes x 300 evaluations)"
+    roof["kernel"] = ("eval_pair_kernel (local search, two genotypes a warp, 3000 genotypes x 300 "
+                      "evaluations)")
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -521,7 +707,14 @@ def main():
         "cpu_baseline": cpu,
     }
     if extra:
-        line["variants_ls_evals_per_s"] = extra
+        v = extra["variants_ls_evals_per_s"]
+        plain = v["one_genotype_a_warp"]["shfl"]
+        extra["tensor_core_vs_plain_shfl"] = {
+            "ls_two_genotypes_a_warp_tcgen05": v["two_genotypes_a_warp"]["tcgen05"] / plain,
+            "ls_two_genotypes_a_warp_shfl": v["two_genotypes_a_warp"]["shfl"] / plain,
+            "batched_tcgen05": extra["batch_uneven_512"]["batched_tcgen05_vs_plain_shfl"],
+            "served_tcgen05": extra["serving"]["served_tcgen05_vs_serial_shfl"]}
+        line.update(extra)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
