@@ -154,6 +154,21 @@ def score(rec, lig, genes):
     return e.value, gg, x, ag
 
 
+def score_magnitude(rec, lig, genes, with_positions=False):
+    """[G] magnitude of each gene-gradient component: the chain rule over the
+    absolute values of every contribution (sets where a relative tolerance on
+    a component is meaningful in floating point).  with_positions: also the
+    components' sensitivity to rounding the coordinates (a second [G])."""
+    R, L = _rec(rec), _lig(lig)
+    g = _d(genes)
+    m = np.zeros(L.G)
+    pm = np.zeros(L.G)
+    rc = lib().orc_score_magnitude(C.byref(R.c), C.byref(L.c), _pd(g), _pd(m), _pd(pm))
+    if rc:
+        raise ValueError("orc_score_magnitude failed (%d)" % rc)
+    return (m, pm) if with_positions else m
+
+
 def adadelta_step(grad, genes, eg2, ed2, rho=0.8, eps=1e-2):
     """One ADADELTA update; returns new (genes, eg2, ed2)."""
     grad = _d(grad)

@@ -348,6 +348,211 @@ int orc_score(const orc_receptor *R, const orc_ligand *L, const double *genes,
     return 0;
 }
 
+/*
+ * Magnitude of every gene-gradient component: the chain rule of orc_score
+ * applied to the absolute values of all its contributions (each map corner's
+ * share of an atom's grid gradient, the out-of-grid wall, every term of every
+ * pair force, and every lever arm).  A floating-point evaluation in unit
+ * roundoff u of the same sums has an error of order u times this magnitude,
+ * so |g_j| / A_j says how many relative digits of g_j survive cancellation
+ * (test infrastructure: it sets where a relative tolerance is meaningful).
+ */
+static void trilinear_abs(const orc_receptor *R, int m, double w, const double p[3],
+                          double ag[3]) {
+    const int n[3] = {R->nx, R->ny, R->nz};
+    int i0[3];
+    double f[3];
+    for (int d = 0; d < 3; d++) {
+        double u = (p[d] - R->origin[d]) / R->spacing;
+        int c = (int)floor(u);
+        if (c < 0) c = 0;
+        if (c > n[d] - 2) c = n[d] - 2;
+        i0[d] = c;
+        f[d] = u - c;
+    }
+    const double *map = R->maps + (size_t)m * R->nx * R->ny * R->nz;
+    for (int cz = 0; cz < 2; cz++)
+        for (int cy = 0; cy < 2; cy++)
+            for (int cx = 0; cx < 2; cx++) {
+                size_t idx = ((size_t)(i0[2] + cz) * R->ny + (i0[1] + cy)) * R->nx + (i0[0] + cx);
+                double v = fabs(w * map[idx]) / R->spacing;
+                double wx = cx ? f[0] : 1 - f[0];
+                double wy = cy ? f[1] : 1 - f[1];
+                double wz = cz ? f[2] : 1 - f[2];
+                ag[0] += wy * wz * v;
+                ag[1] += wx * wz * v;
+                ag[2] += wx * wy * v;
+            }
+}
+
+/* pos_mag (may be NULL): the same chain rule over the contributions'
+ * sensitivity to rounding the coordinates - a coordinate of magnitude |x| is
+ * off by about u |x|, which moves every pair force by its derivative times
+ * that and every lever arm by that (stiff r^-12 terms amplify it; the
+ * forces' errors cancel in the rigid-body sums by Newton's third law but not
+ * over a torsion's moving set). */
+int orc_score_magnitude(const orc_receptor *R, const orc_ligand *L, const double *genes,
+                        double *mag, double *pos_mag) {
+    const int N = L->n_atoms, T = L->n_tors;
+    double *x = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *p = (double *)malloc(sizeof(double) * 3 * (size_t)N);
+    double *ag = (double *)calloc(3 * (size_t)N, sizeof(double));
+    double *pg = (double *)calloc((size_t)L->n_pairs + 1, sizeof(double));   /* per pair */
+    if (!x || !p || !ag || !pg) { free(x); free(p); free(ag); free(pg); return -2; }
+    if (torsion_coords(L, genes, p)) { free(x); free(p); free(ag); free(pg); return -1; }
+    rigid_motion(N, genes, p, x);
+    const int n[3] = {R->nx, R->ny, R->nz};
+    double *xs = (double *)malloc(sizeof(double) * (size_t)N);   /* coordinate scale |x|_inf */
+    if (!xs) { free(x); free(p); free(ag); free(pg); return -2; }
+    for (int i = 0; i < N; i++) {
+        xs[i] = 0.0;
+        for (int d = 0; d < 3; d++) xs[i] = fmax(xs[i], fabs(x[3 * i + d]));
+    }
+    for (int i = 0; i < N; i++) {
+        double q = L->charge[i], pc[3];
+        int inside[3];
+        for (int d = 0; d < 3; d++) {
+            double lo = R->origin[d], hi = R->origin[d] + (n[d] - 1) * R->spacing;
+            pc[d] = x[3 * i + d] < lo ? lo : (x[3 * i + d] > hi ? hi : x[3 * i + d]);
+            inside[d] = (x[3 * i + d] >= lo && x[3 * i + d] <= hi);
+        }
+        double t[3] = {0, 0, 0};
+        trilinear_abs(R, L->type[i], 1.0, pc, t);
+        trilinear_abs(R, R->n_type_maps, q, pc, t);
+        trilinear_abs(R, R->n_type_maps + 1, fabs(q), pc, t);
+        for (int d = 0; d < 3; d++)
+            ag[3 * i + d] += (inside[d] ? t[d] : 0.0) + fabs(2.0 * ORC_W_OUT * (x[3 * i + d] - pc[d]));
+    }
+    for (int k = 0; k < L->n_pairs; k++) {
+        int i = L->pairs[2 * k], j = L->pairs[2 * k + 1];
+        int ti = L->type[i], tj = L->type[j];
+        double rv[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+        double r = sqrt(dot(rv, rv));
+        double rc = r > ORC_R_MIN ? r : ORC_R_MIN;
+        int hb = (L->hb_role[ti] == 1 && L->hb_role[tj] == 2) ||
+                 (L->hb_role[ti] == 2 && L->hb_role[tj] == 1);
+        double a = 0;    /* |dE/dr| summed term by term */
+        double a2 = 0;   /* |d2E/dr2| summed term by term */
+        if (hb) {
+            double Rh = L->hb_R, eh = L->hb_eps;
+            a += fabs(ORC_W_HB * eh) * (60.0 * pow(Rh / rc, 12) + 60.0 * pow(Rh / rc, 10)) / rc;
+            a2 += fabs(ORC_W_HB * eh) * (780.0 * pow(Rh / rc, 12) + 660.0 * pow(Rh / rc, 10)) / (rc * rc);
+        } else {
+            double Rij = 0.5 * (L->R[ti] + L->R[tj]), eij = sqrt(L->eps[ti] * L->eps[tj]);
+            a += fabs(ORC_W_VDW * eij) * (12.0 * pow(Rij / rc, 12) + 12.0 * pow(Rij / rc, 6)) / rc;
+            a2 += fabs(ORC_W_VDW * eij) * (156.0 * pow(Rij / rc, 12) + 84.0 * pow(Rij / rc, 6)) / (rc * rc);
+        }
+        double deps, epsr = dielectric(rc, &deps);
+        double C = ORC_W_EL * ORC_ELEC * L->charge[i] * L->charge[j];
+        a += fabs(C) * (fabs(epsr) + rc * fabs(deps)) / ((rc * epsr) * (rc * epsr));
+        /* C / (r eps): second derivative bounded term by term (eps'' ~ lambda B eps') */
+        a2 += fabs(C) * (2.0 / (rc * rc * rc * fabs(epsr)) + 4.0 * fabs(deps) / (rc * rc * epsr * epsr)
+                         + 2.0 * deps * deps / (rc * fabs(epsr * epsr * epsr))
+                         + 0.003627 * 86.9525 * fabs(deps) / (rc * epsr * epsr));
+        if (r < ORC_R_MIN) a = a2 = 0.0;
+        double Si = L->solpar[ti] + ORC_QSOL * fabs(L->charge[i]);
+        double Sj = L->solpar[tj] + ORC_QSOL * fabs(L->charge[j]);
+        double s2 = 2.0 * ORC_DS_SIGMA * ORC_DS_SIGMA;
+        double ads = fabs(ORC_W_DS * (Si * L->vol[tj] + Sj * L->vol[ti])) * exp(-r * r / s2);
+        const double sg2 = ORC_DS_SIGMA * ORC_DS_SIGMA;
+        a2 += ads * (r * r / (sg2 * sg2) + 1.0 / sg2);
+        const double X = xs[i] + xs[j];   /* rounding of the separation: about u X */
+        for (int d = 0; d < 3; d++) {
+            double m = (r > 0 ? a * fabs(rv[d]) / r : 0.0) + ads * fabs(rv[d]) / sg2;
+            ag[3 * i + d] += m;
+            ag[3 * j + d] += m;
+        }
+        /* the force's change under that rounding, per component: its
+         * magnitude's derivative along the separation plus its turn
+         * (|dE/dr| / r), and the desolvation force's own */
+        pg[k] = (a2 + (r > 0 ? a / r : 0.0) + ads / sg2) * X;
+    }
+    /* the chain rule of orc_score with absolute values */
+    double u[3];
+    axis_from_angles(genes[3], genes[4], u);
+    double al = genes[5];
+    double up[3] = {-sin(genes[4]) * sin(genes[3]), sin(genes[4]) * cos(genes[3]), 0.0};
+    double ut[3] = {cos(genes[4]) * cos(genes[3]), cos(genes[4]) * sin(genes[3]), -sin(genes[4])};
+    double sa = sin(al), omc = 1.0 - cos(al), ca = cos(al);
+    /* velocity of atom i under each gene (the chain rule's factors) */
+    double *vel = (double *)calloc(3 * (size_t)N * (6 + T), sizeof(double));
+    if (!vel) { free(x); free(p); free(ag); free(pg); free(xs); return -2; }
+#define VEL(i, k) (vel + 3 * ((size_t)(k) * N + (i)))
+    for (int i = 0; i < N; i++) {
+        const double *pi = p + 3 * i;
+        for (int d = 0; d < 3; d++) VEL(i, d)[d] = 1.0;
+        double t1[3], t2[3], t3[3], t4[3];
+        cross(up, pi, t1);
+        cross(u, pi, t2);
+        cross(up, t2, t3);
+        cross(u, t1, t4);
+        for (int d = 0; d < 3; d++) VEL(i, 3)[d] = sa * t1[d] + omc * (t3[d] + t4[d]);
+        cross(ut, pi, t1);
+        cross(ut, t2, t3);
+        cross(u, t1, t4);
+        for (int d = 0; d < 3; d++) VEL(i, 4)[d] = sa * t1[d] + omc * (t3[d] + t4[d]);
+        cross(u, t2, t3);
+        for (int d = 0; d < 3; d++) VEL(i, 5)[d] = ca * t2[d] + sa * t3[d];
+    }
+    double *axl = (double *)malloc(sizeof(double) * (T > 0 ? T : 1));
+    if (!axl) { free(vel); free(x); free(p); free(ag); free(pg); free(xs); return -2; }
+    for (int k = 0; k < T; k++) {
+        const double *xa = x + 3 * L->tors_bond[2 * k], *xb = x + 3 * L->tors_bond[2 * k + 1];
+        double ax[3] = {xb[0] - xa[0], xb[1] - xa[1], xb[2] - xa[2]};
+        double len = sqrt(dot(ax, ax));
+        axl[k] = len;
+        for (int d = 0; d < 3; d++) ax[d] /= len;
+        for (int m = L->mov_off[k]; m < L->mov_off[k + 1]; m++) {
+            int i = L->mov_atoms[m];
+            double v[3] = {x[3 * i] - xb[0], x[3 * i + 1] - xb[1], x[3 * i + 2] - xb[2]};
+            cross(ax, v, VEL(i, 6 + k));
+        }
+    }
+    /* pass 0: |contribution| sums */
+    for (int k = 0; k < 6 + T; k++) {
+        double acc = 0;
+        for (int i = 0; i < N; i++)
+            for (int d = 0; d < 3; d++) acc += ag[3 * i + d] * fabs(VEL(i, k)[d]);
+        mag[k] = acc;
+    }
+    /* pass 1: coordinate rounding - every pair force's change enters a gene
+     * through the difference of its atoms' velocities (it cancels in the
+     * translation; pairs inside a torsion's moving set see only their
+     * separation), the lever arms round by about u |x|, and a torsion's axis
+     * turns by about u (|x_a| + |x_b|) / |x_b - x_a| */
+    if (pos_mag) {
+        for (int k = 0; k < 6 + T; k++) {
+            double acc = 0;
+            for (int q = 0; q < L->n_pairs; q++) {
+                const int i = L->pairs[2 * q], j = L->pairs[2 * q + 1];
+                for (int d = 0; d < 3; d++) acc += pg[q] * fabs(VEL(i, k)[d] - VEL(j, k)[d]);
+            }
+            if (k >= 3) {
+                const double xb = k >= 6 ? xs[L->tors_bond[2 * (k - 6) + 1]] : 0.0;
+                for (int i = 0; i < N; i++) {
+                    const double *vi = VEL(i, k);
+                    if (k >= 6 && vi[0] == 0.0 && vi[1] == 0.0 && vi[2] == 0.0) continue;
+                    for (int d = 0; d < 3; d++) acc += ag[3 * i + d] * (xs[i] + xb);
+                }
+            }
+            if (k >= 6) {
+                const int ka = L->tors_bond[2 * (k - 6)], kb = L->tors_bond[2 * (k - 6) + 1];
+                acc += mag[k] * (xs[ka] + xs[kb]) / axl[k - 6];
+            }
+            pos_mag[k] = acc;
+        }
+    }
+#undef VEL
+    free(vel);
+    free(axl);
+    free(x);
+    free(p);
+    free(ag);
+    free(pg);
+    free(xs);
+    return 0;
+}
+
 static double wrap_angle(double a) {
     return a - 2.0 * PI * floor((a + PI) / (2.0 * PI));
 }

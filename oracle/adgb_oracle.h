@@ -58,6 +58,13 @@ int orc_energy(const orc_receptor *R, const orc_ligand *L, const double *xyz,
 int orc_score(const orc_receptor *R, const orc_ligand *L, const double *genes,
               double *energy, double *gene_grad, double *xyz_out,
               double *atom_grad);
+/* Magnitude [6+T] of each gene-gradient component: orc_score's chain rule
+ * over the absolute values of all contributions (the scale of the rounding
+ * error of any floating-point evaluation of the same sums); pos_mag [6+T]
+ * (may be NULL): the components' sensitivity to rounding the coordinates
+ * (a coordinate off by u |x|), in the same units. */
+int orc_score_magnitude(const orc_receptor *R, const orc_ligand *L, const double *genes,
+                        double *mag, double *pos_mag);
 int orc_adadelta_step(int G, const double *grad, double rho, double eps,
                       double *genes, double *eg2, double *ed2);
 int orc_local_search(const orc_receptor *R, const orc_ligand *L, double *genes,

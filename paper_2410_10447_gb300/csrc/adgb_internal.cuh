@@ -146,8 +146,8 @@ struct SmemLayout {
         const int lanes = N <= 32 ? 32 : (N + 31) / 32 * 32;
         if (chunk < lanes) chunk = lanes;
         p_force = q; q = al16(q + 16 * chunk);
-        p_tq = q;    q = al16(q + (N > 32 ? 16 * N : 0));
-        p_seg = q;   q = al16(q + (N > 32 ? 4 * 8 * ((N + 31) / 32) : 0));
+        p_tq = q;    // (unused: no torsion prefix scans)
+        p_seg = q;
         pose_stride = q;
         total = pose0 + ppb * pose_stride;
     }

@@ -694,7 +694,6 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
 
         // 4. partial sums of (E, sum g, torque about the centre); torsion gradients
         float v[8] = {e_part, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float4 *tq = reinterpret_cast<float4 *>(P + L.p_tq);
         for (int i = gt; i < N; i += TPP) {
             const float4 g = rounds ? make_float4(go.x, go.y, go.z, 0.f) : grd[i];
             const float4 x = rounds ? make_float4(xo.x, xo.y, xo.z, 0.f) : xyz[i];
@@ -707,115 +706,80 @@ __device__ __forceinline__ void search_pose(unsigned char *sm, const SmemLayout 
             v[4] += c.x;
             v[5] += c.y;
             v[6] += c.z;
-            if (N > 32) tq[i] = make_float4(c.x, c.y, c.z, 0.f);
         }
         // the tensor-core reduction of the partials runs while the torsion
-        // scans below are computed
+        // sums below are computed
         if constexpr (VAR == ADGB_REDUCE_TCGEN05) tc05_issue(v, tw);
         if (N <= 32) {
-            // one atom per lane of the group's first warp; atoms are in
-            // depth-first order, so a torsion's moving set [s, e) sums to
-            // P[e-1] - P[s-1] of the inclusive prefix P of (g, (x - t) x g).
-            if (gt < 32) {
-                float w[6] = {v[1], v[2], v[3], v[4], v[5], v[6]};
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-                    for (int c = 0; c < 6; c++) {
-                        const float y = __shfl_up_sync(0xffffffffu, w[c], off);
-                        if (gt >= off) w[c] += y;
-                    }
-                }
-                for (int k0 = 0; k0 < T; k0 += 32) {
-                    const int k = k0 + gt;
-                    const int4 ta = k < T ? s_tat[k] : make_int4(0, 0, 0, 0);
-                    const int hi = max(ta.w - 1, 0), lo = max(ta.z - 1, 0);
-                    float sm6[6];
-#pragma unroll
-                    for (int c = 0; c < 6; c++) {
-                        const float ph = __shfl_sync(0xffffffffu, w[c], hi);
-                        const float pl = __shfl_sync(0xffffffffu, w[c], lo);
-                        sm6[c] = ph - (ta.z > 0 ? pl : 0.f);
-                    }
-                    if (k < T) {
-                        float gk = 0.f;
-                        if (ta.w > ta.z) {
-                            const float4 xa = xyz[ta.x], xb = xyz[ta.y];
-                            const float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
-                            const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
-                            // sum (x - x_b) x g = sum (x - t) x g - (x_b - t) x sum g
-                            const float3 bt = make_float3(xb.x - tr.x, xb.y - tr.y, xb.z - tr.z);
-                            const float3 acc = make_float3(
-                                sm6[3] - (bt.y * sm6[2] - bt.z * sm6[1]),
-                                sm6[4] - (bt.z * sm6[0] - bt.x * sm6[2]),
-                                sm6[5] - (bt.x * sm6[1] - bt.y * sm6[0]));
-                            gk = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
-                        }
-                        ggrad[6 + k] = gk;
-                    }
-                }
-            }
-        } else {
-            // any N: two-level inclusive scan of (g, (x - t) x g) over the
-            // depth-first atom order (32-atom segments by warp shuffles,
-            // then segment offsets), then range differences per torsion
-            group_sync<TPP>(group);
-            float *seg = reinterpret_cast<float *>(P + L.p_seg);
-            const int nseg = (N + 31) >> 5, lane = gt & 31;
-            for (int sgi = gt >> 5; sgi < nseg; sgi += TPP / 32) {
-                const int i = 32 * sgi + lane;
-                float w[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (i < N) {
-                    const float4 g4 = grd[i], t4 = tq[i];
-                    w[0] = g4.x; w[1] = g4.y; w[2] = g4.z;
-                    w[3] = t4.x; w[4] = t4.y; w[5] = t4.z;
-                }
-#pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-                    for (int c = 0; c < 6; c++) {
-                        const float y = __shfl_up_sync(0xffffffffu, w[c], off);
-                        if (lane >= off) w[c] += y;
-                    }
-                }
-                if (i < N) {
-                    grd[i] = make_float4(w[0], w[1], w[2], 0.f);
-                    tq[i] = make_float4(w[3], w[4], w[5], 0.f);
-                }
-                if (lane == 31) {
-#pragma unroll
-                    for (int c = 0; c < 6; c++) seg[8 * sgi + c] = w[c];
-                }
-            }
+            // one atom per lane of the group's first warp: each torsion's lane
+            // sums its moving atoms (one contiguous range [s, e) of the
+            // depth-first order) with the lever arm from the bond's atom b,
+            // a . sum (x - x_b) x g, from the shared coordinates and gradients
+            if (rounds && gt < N) grd[gt] = make_float4(go.x, go.y, go.z, 0.f);
             group_sync<TPP>(group);
             for (int k = gt; k < T; k += TPP) {
                 const int4 ta = s_tat[k];
                 float gk = 0.f;
                 if (ta.w > ta.z) {
-                    float sm6[6];
-                    const int hi = ta.w - 1, lo = ta.z - 1;
-                    const float4 gh = grd[hi], th = tq[hi];
-                    sm6[0] = gh.x; sm6[1] = gh.y; sm6[2] = gh.z;
-                    sm6[3] = th.x; sm6[4] = th.y; sm6[5] = th.z;
-                    for (int s2 = 0; s2 < (hi >> 5); s2++)
-                        for (int c = 0; c < 6; c++) sm6[c] += seg[8 * s2 + c];
-                    if (lo >= 0) {
-                        const float4 gl = grd[lo], tl = tq[lo];
-                        sm6[0] -= gl.x; sm6[1] -= gl.y; sm6[2] -= gl.z;
-                        sm6[3] -= tl.x; sm6[4] -= tl.y; sm6[5] -= tl.z;
-                        for (int s2 = 0; s2 < (lo >> 5); s2++)
-                            for (int c = 0; c < 6; c++) sm6[c] -= seg[8 * s2 + c];
-                    }
                     const float4 xa = xyz[ta.x], xb = xyz[ta.y];
+                    float3 acc = make_float3(0.f, 0.f, 0.f);
+                    for (int i = ta.z; i < ta.w; i++) {
+                        const float4 g = grd[i], x = xyz[i];
+                        const float3 d = make_float3(x.x - xb.x, x.y - xb.y, x.z - xb.z);
+                        acc.x += d.y * g.z - d.z * g.y;
+                        acc.y += d.z * g.x - d.x * g.z;
+                        acc.z += d.x * g.y - d.y * g.x;
+                    }
                     const float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
                     const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
-                    const float3 bt = make_float3(xb.x - tr.x, xb.y - tr.y, xb.z - tr.z);
-                    const float3 acc = make_float3(sm6[3] - (bt.y * sm6[2] - bt.z * sm6[1]),
-                                                   sm6[4] - (bt.z * sm6[0] - bt.x * sm6[2]),
-                                                   sm6[5] - (bt.x * sm6[1] - bt.y * sm6[0]));
                     gk = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
                 }
                 ggrad[6 + k] = gk;
+            }
+        } else {
+            // any N: each torsion's gradient as a direct sum over its moving
+            // atoms (one contiguous range of the depth-first order) with the
+            // lever arm from the bond's atom b, a . sum (x - x_b) x g: warp w of
+            // the pose takes torsions w, w + W, ...; its lanes stride the
+            // range, then a butterfly sums the lanes (a fixed order).  (A
+            // difference of prefix sums over the whole order would cancel
+            // every atom before the range: for large forces far more rounding
+            // error than the torsion's own terms carry.)
+            group_sync<TPP>(group);
+            constexpr int W = TPP / 32;
+            const int lane = gt & 31;
+            for (int k0 = 0; k0 < T; k0 += W) {
+                const int k = k0 + (gt >> 5);   // warp-uniform
+                float3 acc = make_float3(0.f, 0.f, 0.f);
+                int4 ta = make_int4(0, 0, 0, 0);
+                float4 xb = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (k < T) {
+                    ta = s_tat[k];
+                    xb = xyz[ta.y];
+                    for (int i = ta.z + lane; i < ta.w; i += 32) {
+                        const float4 g = grd[i], x = xyz[i];
+                        const float3 d = make_float3(x.x - xb.x, x.y - xb.y, x.z - xb.z);
+                        acc.x += d.y * g.z - d.z * g.y;
+                        acc.y += d.z * g.x - d.x * g.z;
+                        acc.z += d.x * g.y - d.y * g.x;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+                    acc.z += __shfl_xor_sync(0xffffffffu, acc.z, off);
+                }
+                if (k < T && lane == 0) {
+                    float gk = 0.f;
+                    if (ta.w > ta.z) {
+                        const float4 xa = xyz[ta.x];
+                        const float3 ax = make_float3(xb.x - xa.x, xb.y - xa.y, xb.z - xa.z);
+                        const float il = rsqrtf(ax.x * ax.x + ax.y * ax.y + ax.z * ax.z);
+                        gk = (ax.x * acc.x + ax.y * acc.y + ax.z * acc.z) * il;
+                    }
+                    ggrad[6 + k] = gk;
+                }
             }
         }
 

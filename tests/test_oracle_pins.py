@@ -442,3 +442,60 @@ def test_tcu_reduction_layout_of_section_4_2():
             k = comp[sym.split("_")[1]]
             assert np.allclose(W[r], u[:, k].sum())
     assert np.allclose(W[:4, 0], u.sum(axis=0))
+
+
+# ------------------------------------------- gradient magnitudes (conditioning)
+def test_gradient_magnitude_closed_form_constant_maps(oracle_mod):
+    # one atom at the rotation centre in constant maps: the gradient is zero
+    # and each axis' magnitude is the corner shares' absolute sum,
+    # 2 (|c_t| + |q c_e| + |q| |c_d|) / h (the eight y-z weights sum to 2)
+    ct, ce, cd, h = 1.5, -0.7, 0.4, 0.5
+    vals = {0: ct, 1: ce, 2: cd}
+    rec = tiny_receptor(n=10, spacing=h, n_type_maps=1,
+                        fill=lambda m, X, Y, Z: vals[m] + 0 * X)
+    q = -0.35
+    lig = dict(n_atoms=1, n_types=1, n_tors=0, type=np.array([0], np.int32),
+               charge=np.array([q], np.float32), xyz=np.zeros((1, 3)),
+               tors_bond=np.zeros((0, 2), np.int32), mov_off=np.zeros(1, np.int32),
+               mov_atoms=np.zeros(0, np.int32), pairs=np.zeros((0, 2), np.int32),
+               R=np.ones(1, np.float32), eps=np.ones(1, np.float32),
+               vol=np.ones(1, np.float32), solpar=np.ones(1, np.float32),
+               hb_role=np.zeros(1, np.int32), hb_R=np.float32(1.9), hb_eps=np.float32(5.0))
+    qf = float(np.float32(q))
+    want = 2.0 * (abs(ct) + abs(qf * ce) + abs(qf) * abs(cd)) / h
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        genes = np.concatenate([rng.uniform(-1.5, 1.5, 3), rng.uniform(0, 3, 3)])
+        _, g, _, _ = oracle_mod.score(rec, lig, genes)
+        m = oracle_mod.score_magnitude(rec, lig, genes)
+        assert np.allclose(g, 0.0, atol=1e-9)
+        assert m[:3] == pytest.approx([want] * 3, rel=1e-5)   # maps hold float32 values
+        assert np.all(m[3:] == 0.0)                            # no lever arm
+        # coordinate rounding: no pairs, so nothing for the translation; the
+        # rotation genes' lever x - t is zero but computed from coordinates of
+        # size |x|_inf, so each takes sum_d |g|_d |x|_inf = 3 want |x|_inf
+        _, pm = oracle_mod.score_magnitude(rec, lig, genes, with_positions=True)
+        assert np.all(pm[:3] == 0.0)
+        assert pm[3:] == pytest.approx([3 * want * np.max(np.abs(genes[:3]))] * 3, rel=1e-5)
+    # outside the grid along x: only the wall's gradient, 2 W_OUT d
+    hi = float(rec["origin"][0]) + 9 * h
+    genes = np.array([hi + 0.6, 0.0, 0.0, 0.0, 0.0, 0.0])
+    m = oracle_mod.score_magnitude(rec, lig, genes)
+    assert m[0] == pytest.approx(2 * 10.0 * 0.6, rel=1e-9)
+
+
+@pytest.mark.parametrize("which", ["cfg0", "cfg1"])
+def test_gradient_magnitude_bounds_the_gradient(oracle_mod, which, request):
+    # triangle inequality: the absolute sum of the contributions bounds the sum
+    w = request.getfixturevalue(which)
+    R, L = oracle_mod.Receptor(w["receptor"]), oracle_mod.Ligand(w["ligand"])
+    for p in range(min(12, w["genes"].shape[0])):
+        _, g, _, _ = oracle_mod.score(R, L, w["genes"][p])
+        m = oracle_mod.score_magnitude(R, L, w["genes"][p])
+        assert np.all(m >= np.abs(g) * (1 - 1e-12) - 1e-12), (p, m, g)
+        assert np.all(np.isfinite(m))
+        # coordinate rounding: a pair force enters a gene through the difference
+        # of its atoms' velocities, which is zero for the translation genes
+        m2, pm = oracle_mod.score_magnitude(R, L, w["genes"][p], with_positions=True)
+        assert np.array_equal(m2, m)
+        assert np.all(pm[:3] == 0.0) and np.all(pm >= 0.0) and np.all(np.isfinite(pm))
