@@ -23,7 +23,8 @@ STEPS = {0: "whole evaluation", 1: "pair rounds", 2: "grid terms",
          12: "reduce-and-broadcast + torsion moving-set sums", 8: "torsion moving-set sums (shuffle)",
          16: "torsion-tree walk", 32: "gene-gradient formulas", 64: "sines and cosines",
          3: "pair rounds + grid terms", 128: "pair-term arithmetic (exchanges kept)",
-         256: "pair-round shuffles (arithmetic kept)"}
+         256: "pair-round shuffles (arithmetic kept)",
+         512: "one tcgen05 MMA a block instead of one a warp (design, not a step)"}
 
 
 def main(argv=None):
@@ -51,8 +52,8 @@ def main(argv=None):
     for v in map(int, a.variants.split(",")):
         row = {}
         for mask, name in STEPS.items():
-            if mask == 8 and v == 3:
-                continue   # the tensor-core form computes the moving-set sums in its MMA
+            if (mask == 8 and v == 3) or (mask == 512 and v != 3):
+                continue   # tensor-core form: moving-set sums in its MMA; 512 is its design
             ms = []
             for _ in range(a.reps + 1):
                 g.copy_(g0)
@@ -68,7 +69,9 @@ def main(argv=None):
         res["variant%d" % v] = out
         print("%s variant %d: whole %.3f ms" % (a.workload, v, base))
         for m, t in row.items():
-            if m:
+            if m == 512:
+                print("  design: %-48s %.3f ms  (%+.1f%% time)" % (STEPS[m], t, 100 * (t - base) / base))
+            elif m:
                 print("  without %-48s %.3f ms  share %5.1f%%" % (STEPS[m], t, 100 * (base - t) / base))
     ctx.close()
     print(json.dumps(res))

@@ -572,7 +572,11 @@ int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, 
  * of the shuffle form), 16 (the torsion-tree walk of the coordinates), 32
  * (the gene-gradient formulas), 64 (sines and cosines: zero angles), 3
  * (pairs and grid), 128 (the pair terms' arithmetic, the exchanges kept),
- * 256 (the pair rounds' shuffles, the arithmetic kept).
+ * 256 (the pair rounds' shuffles, the arithmetic kept); 512 (nothing left
+ * out: the tcgen05 variant with ONE tensor-core product a block over all its
+ * warps' partials, after a block barrier, instead of one a warp - the other
+ * design of the reduction on tensor cores, kept for measurement; needs n a
+ * multiple of the genotypes a block).
  * variant: ADGB_REDUCE_SHFL or ADGB_REDUCE_TCGEN05.  genes_dev [n][6+T]
  * in/out, best_energy_dev [n] out, on `stream`.  The ligand must run two
  * genotypes a warp (at most 32 atoms with matching rounds, at most 26

@@ -60,6 +60,10 @@ enum {
     SK_SINCOS = 64,  // the sines and cosines of the angles (zero angles instead)
     SK_PAIRMATH = 128,  // the pair terms' arithmetic (the exchanges kept)
     SK_PAIRXCHG = 256,  // the pair rounds' shuffles (the arithmetic kept)
+    // not a step left out but the other tensor-core design, measured through
+    // the same entry: ONE MMA a block (N = 32 x warps, after a block barrier)
+    // instead of one a warp; needs full blocks and equal iteration counts
+    SK_BLOCKMMA = 512,
 };
 
 // ------------------------------------------------------- packed FP32x2
@@ -342,28 +346,39 @@ __device__ __forceinline__ void tc2_write_pattern(unsigned char *R, const int4 *
 
 // Stages the lane's 16 partials (8 a genotype) as TF32 hi and lo terms into
 // this warp's B operand and has one lane issue D = P . B^T (M = 128, N = 32,
-// K = 32 lanes in four K = 8 MMAs) committed to the warp's mbarrier.
+// K = 32 lanes in four K = 8 MMAs) committed to the warp's mbarrier.  BLK
+// (measurement form): after a block barrier that every warp takes each
+// evaluation (also after a failed wait), thread 0 issues one product over
+// all warps' B operands (contiguous: N = 32 x warps) into the same D
+// columns, committed to warp 0's mbarrier, which every warp then waits on.
+template <bool BLK = false>
 __device__ __forceinline__ void tc2_issue(const float2 v[8], Tc2 &t) {
-    if (!t.ok) return;
+    if (!BLK && !t.ok) return;
     const int lane = threadIdx.x & 31, cq = lane >> 2;
-    unsigned char *mine = t.b + (lane & 3) * 4;
+    if (t.ok) {
+        unsigned char *mine = t.b + (lane & 3) * 4;
 #pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const uint32_t ha = to_tf32(v[c].x), hb = to_tf32(v[c].y);
-        const uint32_t la = to_tf32(v[c].x - __uint_as_float(ha));
-        const uint32_t lb = to_tf32(v[c].y - __uint_as_float(hb));
-        const int off = c * 128 + ((cq ^ c) << 4);
-        *reinterpret_cast<uint32_t *>(mine + off) = ha;          // row c
-        *reinterpret_cast<uint32_t *>(mine + 1024 + off) = la;   // row 8 + c
-        *reinterpret_cast<uint32_t *>(mine + 2048 + off) = hb;   // row 16 + c
-        *reinterpret_cast<uint32_t *>(mine + 3072 + off) = lb;   // row 24 + c
+        for (int c = 0; c < 8; c++) {
+            const uint32_t ha = to_tf32(v[c].x), hb = to_tf32(v[c].y);
+            const uint32_t la = to_tf32(v[c].x - __uint_as_float(ha));
+            const uint32_t lb = to_tf32(v[c].y - __uint_as_float(hb));
+            const int off = c * 128 + ((cq ^ c) << 4);
+            *reinterpret_cast<uint32_t *>(mine + off) = ha;          // row c
+            *reinterpret_cast<uint32_t *>(mine + 1024 + off) = la;   // row 8 + c
+            *reinterpret_cast<uint32_t *>(mine + 2048 + off) = hb;   // row 16 + c
+            *reinterpret_cast<uint32_t *>(mine + 3072 + off) = lb;   // row 24 + c
+        }
+        tc05::fence_proxy_async_smem();
     }
-    tc05::fence_proxy_async_smem();
     tc05::fence_before();
-    __syncwarp();
-    if (lane == 0) {
+    if constexpr (BLK) {
+        asm volatile("bar.sync 1, %0;" ::"r"(blockDim.x) : "memory");
+    } else {
+        __syncwarp();
+    }
+    if (BLK ? (threadIdx.x == 0 && t.ok) : lane == 0) {
         tc05::fence_after();
-        constexpr uint32_t idesc = tc05::idesc_tf32(128, 32);
+        const uint32_t idesc = tc05::idesc_tf32(128, BLK ? 32 * (blockDim.x >> 5) : 32);
 #pragma unroll
         for (int s = 0; s < 4; s++)
             tc05::mma_tf32_ss(t.d_col, tc05::desc_sw128(t.a_s + 32u * s, 1024),
@@ -722,7 +737,7 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
             Ts = {v[4], v[5], v[6]};
         } else if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
             float2 S[8];
-            tc2_issue(v, tw);
+            tc2_issue<(SKIP & SK_BLOCKMMA) != 0>(v, tw);
             tc2_finish(S, tw, fail);
             E = shfl2(S[0], 0);   // lane 0's pattern row is all ones
             Gs = {S[1], S[2], S[3]};
@@ -926,6 +941,7 @@ __global__ void __launch_bounds__(64, 5) eval_pair_kernel(const PairArgs a) {
     if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
         tc2_write_pattern(smem_raw, a.lig.tatoms, a.lig.n_tors);
         tc2_begin(smem_raw, tw);
+        if constexpr ((SKIP & SK_BLOCKMMA) != 0) tw.mbar -= warp;   // warp 0's barrier for all
     }
     __syncthreads();
     const int b0 = blockIdx.x * a.ppb;
@@ -1147,6 +1163,12 @@ static cudaError_t launch_ablation_t(const PairArgs &a, int smem, cudaStream_t s
         case SK_PAIRS | SK_GRID: return launch_pair_t<VAR, SK_PAIRS | SK_GRID>(a, smem, s);
         case SK_PAIRMATH: return launch_pair_t<VAR, SK_PAIRMATH>(a, smem, s);
         case SK_PAIRXCHG: return launch_pair_t<VAR, SK_PAIRXCHG>(a, smem, s);
+        case SK_BLOCKMMA:
+            // every warp of every block must take the block barrier of each
+            // evaluation: full blocks only (the iteration count is uniform here)
+            if (VAR != ADGB_REDUCE_TCGEN05 || a.n % a.ppb != 0 || a.ppb % 2 != 0 || a.iters_pp)
+                return cudaErrorInvalidValue;
+            return launch_pair_t<VAR, SK_BLOCKMMA>(a, smem, s);
     }
     return cudaErrorInvalidValue;
 }
