@@ -562,6 +562,23 @@ int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, 
                   adgb_stream stream);
 
 /*
+ * device_status - tensor-core failure report (no counterpart in the paper).
+ * Every wait of the tcgen05 local-search kernels for the tensor core is
+ * bounded; a wait that gives up makes that warp's sums NaN for the rest of
+ * its launch, frees its tensor memory and is counted on the device.  The
+ * synchronous calls (score_poses, local_search, local_search_sw, dock)
+ * return ADGB_EDEVICE when the count grew during the call or since the last
+ * report; the asynchronous *_dev calls cannot, and device_status reports it
+ * for them: it waits for the context's stream and returns ADGB_EDEVICE
+ * (once) if any wait gave up on ctx's device since the context last
+ * reported one, else ADGB_OK.  The count is device-wide: a give-up in any
+ * caller's kernels on the device is reported.  (A served job is failed with
+ * ADGB_EDEVICE by the same rule, between its first and last launch.)
+ * Errors: EINVAL, EDEVICE.
+ */
+int device_status(adgb_ctx *ctx);
+
+/*
  * ls_ablation_dev - measurement aid with no counterpart in the paper: the
  * two-genotypes-a-warp local search of local_search_dev with some of its
  * steps left out at compile time, so that a step's share of the time is the
@@ -576,7 +593,11 @@ int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, 
  * out: the tcgen05 variant with ONE tensor-core product a block over all its
  * warps' partials, after a block barrier, instead of one a warp - the other
  * design of the reduction on tensor cores, kept for measurement; needs n a
- * multiple of the genotypes a block).
+ * multiple of the genotypes a block); 1024 (a test of the failure path: the
+ * tcgen05 variant with nothing issued to the tensor core, so that every
+ * warp's first completion wait gives up after a short bounded wait; its sums
+ * are NaN, its tensor memory is released, the give-up is counted and the
+ * next synchronous call or device_status reports ADGB_EDEVICE once).
  * variant: ADGB_REDUCE_SHFL or ADGB_REDUCE_TCGEN05.  genes_dev [n][6+T]
  * in/out, best_energy_dev [n] out, on `stream`.  The ligand must run two
  * genotypes a warp (at most 32 atoms with matching rounds, at most 26

@@ -39,7 +39,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget",
-           "philox4x32_10_dev", "ls_ablation_dev"]
+           "philox4x32_10_dev", "ls_ablation_dev", "device_status"]
 MAX_GENES = 46
 
 
@@ -203,6 +203,7 @@ def load(build: bool = False):
     L.ga_converged_dev.argtypes = [vp, C.POINTER(_DockParams), vp, vp, vp]
     L.alu_bench_dev.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.philox4x32_10_dev.argtypes = [vp, vp, C.c_int, vp, vp]
+    L.device_status.argtypes = [vp]
     L.ls_ablation_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                   vp, vp]
     _lib = L
@@ -368,6 +369,14 @@ class Context:
         self._chk(self.lib.ls_ablation_dev(self.h, rid, lid, _ptr(genes), genes.shape[0],
                                            int(iters), int(variant), int(skip_mask),
                                            _ptr(best_energy), _stream()))
+
+    def device_status(self):
+        """Raises AdgbError (EDEVICE) once if a tensor-core completion wait gave
+        up on the context's device since the last report (after the context's
+        stream and torch's current stream have finished)."""
+        import torch
+        torch.cuda.current_stream().synchronize()
+        self._chk(self.lib.device_status(self.h))
 
     def reduce4_bench_dev(self, variant, x, threads, reps=1, out=None):
         import torch

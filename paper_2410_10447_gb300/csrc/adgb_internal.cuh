@@ -259,12 +259,12 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
                         int iters, float rho, float eps, int resume, float *energy,
                         float *grad, float *state, cudaStream_t s,
                         const int *iters_per_pose = nullptr);
-// Two genotypes a warp (pair_eligible ligands only; EvalCfg::paired); fail
-// (may be null) is set to 1 if a tensor-core completion wait gave up.
+// Two genotypes a warp (pair_eligible ligands only; EvalCfg::paired).  A
+// tensor-core completion wait that gives up is counted (tc_gave_up_async).
 cudaError_t launch_eval_pair(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, int mode,
                              const float *genes_in, float *genes_out, int n, int iters, float rho,
                              float eps, int resume, float *energy, float *grad, float *state,
-                             cudaStream_t s, const int *iters_per_pose, int *fail);
+                             cudaStream_t s, const int *iters_per_pose);
 int pair_smem_bytes(int layout_bytes, int warps, int variant, int device);
 // Measurement-only paired local search without the steps in `skip`
 // (ls_ablation_dev); cudaErrorInvalidValue for masks or variants not built.
@@ -272,10 +272,15 @@ cudaError_t launch_pair_ablation(const RecDev &rec, const LigDev &lig, const Eva
                                  float *genes, int n, int iters, float *energy, cudaStream_t s,
                                  int skip);
 int pair_layout_bytes(int n_atoms, int n_tors, int ppb, int variant);
+// Queues copies of the tensor-core give-up counts of the local-search kernels
+// on the current device (dst[0]: one genotype a warp and Solis-Wets, dst[1]:
+// two genotypes a warp; monotonic) into host memory dst.
+cudaError_t tc_gave_up_async(unsigned int dst[2], cudaStream_t s);
+cudaError_t pair_tc_gave_up_async(unsigned int *dst, cudaStream_t s);
 int pair_items_grid(const EvalCfg &cfg, int budget, int device);
 cudaError_t launch_eval_pair_items(const WorkItem *items, int n_items, const LigDev *ligs,
                                    const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
-                                   int grid, cudaStream_t s, int *fail);
+                                   int grid, cudaStream_t s);
 // Shared-memory bytes of one ligand's layout in a multi-ligand launch of
 // shape cfg (the launch's budget is the largest over its ligands).
 int items_layout_bytes(const EvalCfg &cfg, int n_atoms, int n_tors, int n_pairs);

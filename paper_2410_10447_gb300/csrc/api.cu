@@ -68,6 +68,7 @@ struct adgb_ctx {
     cudaStream_t stream = nullptr;  // used by the host-pointer calls
     void *stage = nullptr;          // device staging for host-pointer calls
     size_t stage_bytes = 0;
+    unsigned int tc_seen = 0;       // tensor-core give-up count already reported (device-wide)
 };
 
 namespace {
@@ -98,6 +99,36 @@ int ferr(std::string *err, int code, const char *fmt, ...) {
 
 int cuda_fail(adgb_ctx *c, cudaError_t e, const char *what) {
     return fail(c, ADGB_EDEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// The device's tensor-core give-up count (both local-search modules), read
+// after everything queued on the context's stream.
+cudaError_t tc_count(adgb_ctx *c, unsigned int *count) {
+    unsigned int h[2] = {0, 0};
+    cudaError_t e = tc_gave_up_async(h, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    *count = h[0] + h[1];
+    return e;
+}
+
+// ADGB_EDEVICE if a tensor-core completion wait gave up (in any kernel on
+// the device) since the context last reported one, else ADGB_OK.
+int tc_report(adgb_ctx *c, const char *what) {
+    unsigned int n = 0;
+    const cudaError_t e = tc_count(c, &n);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    if (n == c->tc_seen) return ADGB_OK;
+    c->tc_seen = n;
+    return fail(c, ADGB_EDEVICE,
+                "%s: a tensor-core completion wait gave up; the results of this call and of "
+                "asynchronous calls since the last report are not valid", what);
+}
+
+// End of a synchronous call: its CUDA status, then the tensor-core report.
+int sync_done(adgb_ctx *c, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    return tc_report(c, what);
 }
 
 // Makes ctx's device current for the duration of a call.
@@ -931,7 +962,9 @@ int adgb_create(adgb_ctx **ctx, int device, const adgb_options *opts) {
         return ADGB_EINVAL;
     }
     DeviceGuard g(device);
-    if (!g.ok || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (!g.ok || cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        tc_count(c, &c->tc_seen) != cudaSuccess) {
+        if (c->stream) cudaStreamDestroy(c->stream);
         delete c;
         return ADGB_EDEVICE;
     }
@@ -1159,8 +1192,7 @@ int score_poses(adgb_ctx *c, int receptor_id, int ligand_id, const float *genes,
                         0.f, 0.f, 0, de, grad ? dgr : nullptr, nullptr, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, dgr, 4 * G * n, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "score_poses");
+    return sync_done(c, e, "score_poses");
 }
 
 static int check_ls(adgb_ctx *c, const adgb_ls_params *p, int &variant) {
@@ -1216,8 +1248,7 @@ int local_search(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, int 
     if (e == cudaSuccess) e = cudaMemcpyAsync(genes, dg, 4 * G * n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(best_energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && state) e = cudaMemcpyAsync(state, ds, 4 * 3 * G * n, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search");
+    return sync_done(c, e, "local_search");
 }
 
 static int check_sw(adgb_ctx *c, const adgb_sw_params *p, int &variant, SwCfg &w) {
@@ -1290,8 +1321,7 @@ int local_search_sw(adgb_ctx *c, int receptor_id, int ligand_id, float *genes, i
     if (e == cudaSuccess) e = cudaMemcpyAsync(energy, de, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && evals) e = cudaMemcpyAsync(evals, dv, 4 * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && state) e = cudaMemcpyAsync(state, ds, 4 * SW * n, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "local_search_sw");
+    return sync_done(c, e, "local_search_sw");
 }
 
 static int check_dock(adgb_ctx *c, const adgb_dock_params *p, int &variant, DockCfg &d) {
@@ -1369,8 +1399,7 @@ int dock(adgb_ctx *c, int receptor_id, int ligand_id, const adgb_dock_params *p,
     if (e == cudaSuccess) e = cudaMemcpyAsync(best_genes, dg, 4 * (size_t)d.n_runs * G, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(best_energy, de, 8 * (size_t)d.n_runs, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess && evals) e = cudaMemcpyAsync(evals, dv, 8 * (size_t)d.n_runs, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "dock");
+    return sync_done(c, e, "dock");
 }
 
 int ga_init_population_dev(adgb_ctx *c, int receptor_id, int ligand_id, unsigned long long seed,
@@ -1484,6 +1513,12 @@ int ls_ablation_dev(adgb_ctx *c, int receptor_id, int ligand_id, float *genes_de
                                          (cudaStream_t)stream, skip_mask);
     if (e == cudaErrorInvalidValue) return fail(c, ADGB_EINVAL, "ls_ablation: mask %d not built", skip_mask);
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "ls_ablation");
+}
+
+int device_status(adgb_ctx *c) {
+    if (!c) return ADGB_EINVAL;
+    DeviceGuard g(c->device);
+    return tc_report(c, "device_status");
 }
 
 int philox4x32_10_dev(adgb_ctx *c, const unsigned int *in_dev, int n, unsigned int *out_dev,

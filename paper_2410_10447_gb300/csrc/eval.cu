@@ -1280,8 +1280,7 @@ cudaError_t launch_eval_items(const WorkItem *items, int n_items, const LigDev *
                               const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
                               int grid, cudaStream_t s) {
     if (cfg.paired)
-        return launch_eval_pair_items(items, n_items, ligs, recs, counter, cfg, budget, grid, s,
-                                      nullptr);
+        return launch_eval_pair_items(items, n_items, ligs, recs, counter, cfg, budget, grid, s);
     ItemsArgs a;
     a.items = items;
     a.ligs = ligs;
@@ -1387,7 +1386,7 @@ cudaError_t launch_eval(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg
     if (cfg.paired &&
         pair_eligible(lig.n_atoms, lig.n_tors, lig.n_pairs, lig.n_rounds, lig.r_lanes, cfg.tpp))
         return launch_eval_pair(rec, lig, cfg, mode, genes_in, genes_out, n, iters, rho, eps,
-                                resume, energy, grad, state, s, iters_per_pose, nullptr);
+                                resume, energy, grad, state, s, iters_per_pose);
     EvalArgs a;
     a.iters_pp = iters_per_pose;
     a.rec = rec;
@@ -1554,6 +1553,13 @@ cudaError_t launch_pack_grid(const float *maps, int nx, int ny, int nz, int M, f
                              cudaStream_t s) {
     pack_grid_kernel<<<152 * 8, 256, 0, s>>>(maps, nx, ny, nz, M, cells);
     return cudaGetLastError();
+}
+
+cudaError_t tc_gave_up_async(unsigned int dst[2], cudaStream_t s) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(dst, g_tc_gave_up, sizeof(unsigned int), 0,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = pair_tc_gave_up_async(dst + 1, s);
+    return e;
 }
 
 }  // namespace adgb

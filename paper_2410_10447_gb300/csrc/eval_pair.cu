@@ -64,7 +64,12 @@ enum {
     // the same entry: ONE MMA a block (N = 32 x warps, after a block barrier)
     // instead of one a warp; needs full blocks and equal iteration counts
     SK_BLOCKMMA = 512,
+    // test form of the tcgen05 variant: the MMAs are not issued, so the first
+    // completion wait of every warp gives up after a short limit (the failure
+    // path: NaN sums, the give-up count, TMEM still freed)
+    SK_NOISSUE = 1024,
 };
+constexpr int TC2_TEST_LIMIT = 64;   // mbarrier probes of SK_NOISSUE's waits
 
 // ------------------------------------------------------- packed FP32x2
 __device__ __forceinline__ float2 bc(float a) { return make_float2(a, a); }
@@ -351,7 +356,7 @@ __device__ __forceinline__ void tc2_write_pattern(unsigned char *R, const int4 *
 // evaluation (also after a failed wait), thread 0 issues one product over
 // all warps' B operands (contiguous: N = 32 x warps) into the same D
 // columns, committed to warp 0's mbarrier, which every warp then waits on.
-template <bool BLK = false>
+template <bool BLK = false, bool ISSUE = true>
 __device__ __forceinline__ void tc2_issue(const float2 v[8], Tc2 &t) {
     if (!BLK && !t.ok) return;
     const int lane = threadIdx.x & 31, cq = lane >> 2;
@@ -376,7 +381,7 @@ __device__ __forceinline__ void tc2_issue(const float2 v[8], Tc2 &t) {
     } else {
         __syncwarp();
     }
-    if (BLK ? (threadIdx.x == 0 && t.ok) : lane == 0) {
+    if (ISSUE && (BLK ? (threadIdx.x == 0 && t.ok) : lane == 0)) {
         tc05::fence_after();
         const uint32_t idesc = tc05::idesc_tf32(128, BLK ? 32 * (blockDim.x >> 5) : 32);
 #pragma unroll
@@ -408,10 +413,11 @@ __device__ __forceinline__ void ld32_wait(uint32_t taddr, float v[32]) {
 
 // Waits (bounded) for the warp's MMAs and reads row `lane` of D: s[c] = the
 // pattern row's sums of component c for both genotypes.  A wait that gives
-// up makes the sums NaN and records the failure.
-__device__ __forceinline__ void tc2_finish(float2 s[8], Tc2 &t, int *fail) {
+// up makes the sums NaN from then on (tc2_end counts it).
+template <int LIMIT = TC05_WAIT_LIMIT>
+__device__ __forceinline__ void tc2_finish(float2 s[8], Tc2 &t) {
     if (t.ok) {
-        const bool done = __all_sync(FULL, tc05::mbar_wait(t.mbar, t.phase & 1, TC05_WAIT_LIMIT));
+        const bool done = __all_sync(FULL, tc05::mbar_wait(t.mbar, t.phase & 1, LIMIT));
         t.phase++;
         if (done) {
             tc05::fence_after();
@@ -423,15 +429,18 @@ __device__ __forceinline__ void tc2_finish(float2 s[8], Tc2 &t, int *fail) {
             return;
         }
         t.ok = 0;
-        if (fail && (threadIdx.x & 31) == 0) atomicOr(fail, 1);
     }
 #pragma unroll
     for (int c = 0; c < 8; c++) s[c] = bc(__int_as_float(0x7fc00000));
 }
 
-// Releases the block's tensor memory once every warp's MMAs are complete.
+// Releases the block's tensor memory once every warp's MMAs are complete;
+// counts a warp whose waits gave up (or that never had a usable operand
+// region) in the module's give-up count.
+template <int LIMIT = TC05_WAIT_LIMIT>
 __device__ __forceinline__ void tc2_end(Tc2 &t) {
-    if (!t.ok && t.phase > 0) (void)tc05::mbar_wait(t.mbar, (t.phase - 1) & 1, TC05_WAIT_LIMIT);
+    if (!t.ok && t.phase > 0) (void)tc05::mbar_wait(t.mbar, (t.phase - 1) & 1, LIMIT);
+    if (!t.ok && (threadIdx.x & 31) == 0) atomicAdd(&g_tc_gave_up, 1u);
     tc05::fence_before();
     __syncthreads();
     tc05::fence_after();
@@ -475,7 +484,6 @@ struct PairArgs {
     float *grad;
     float *state;
     const int *iters_pp;
-    int *fail;          // set to 1 if a tensor-core wait gave up (may be null)
     int n, iters, resume, mode, ppb;
     float rho, eps;
 };
@@ -522,7 +530,7 @@ __device__ __forceinline__ void stage_pair_ligand(unsigned char *sm, const PairS
 template <int VAR, int SKIP = 0>
 __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L,
                                             const LigDev &lig, const RecDev &rec, const int warp,
-                                            const PairIO &io, Tc2 &tw, int *fail) {
+                                            const PairIO &io, Tc2 &tw) {
     const int lane = threadIdx.x & 31;
     const int N = lig.n_atoms, T = lig.n_tors, G = 6 + T;
     const float4 *s_ref = reinterpret_cast<const float4 *>(sm + L.ref);
@@ -737,8 +745,8 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
             Ts = {v[4], v[5], v[6]};
         } else if constexpr (VAR == ADGB_REDUCE_TCGEN05) {
             float2 S[8];
-            tc2_issue<(SKIP & SK_BLOCKMMA) != 0>(v, tw);
-            tc2_finish(S, tw, fail);
+            tc2_issue<(SKIP & SK_BLOCKMMA) != 0, (SKIP & SK_NOISSUE) == 0>(v, tw);
+            tc2_finish<(SKIP & SK_NOISSUE) ? TC2_TEST_LIMIT : TC05_WAIT_LIMIT>(S, tw);
             E = shfl2(S[0], 0);   // lane 0's pattern row is all ones
             Gs = {S[1], S[2], S[3]};
             Ts = {S[4], S[5], S[6]};
@@ -948,8 +956,9 @@ __global__ void __launch_bounds__(64, 5) eval_pair_kernel(const PairArgs a) {
     const int count = min(a.ppb, a.n - b0);
     const int p0 = b0 + 2 * warp, nvalid = min(2, count - 2 * warp);
     if (nvalid > 0)
-        search_pair<VAR, SKIP>(sm, a.L, a.lig, a.rec, warp, pair_io(a, p0, nvalid), tw, a.fail);
-    if constexpr (VAR == ADGB_REDUCE_TCGEN05) tc2_end(tw);
+        search_pair<VAR, SKIP>(sm, a.L, a.lig, a.rec, warp, pair_io(a, p0, nvalid), tw);
+    if constexpr (VAR == ADGB_REDUCE_TCGEN05)
+        tc2_end<(SKIP & SK_NOISSUE) ? TC2_TEST_LIMIT : TC05_WAIT_LIMIT>(tw);
 }
 
 // Persistent multi-ligand form (batches and serving): blocks take work items
@@ -966,7 +975,6 @@ struct PairItemsArgs {
     const LigDev *ligs;
     const RecDev *recs;
     int *counter;
-    int *fail;
     int n_items, ppb;
 };
 
@@ -1015,7 +1023,7 @@ __global__ void __launch_bounds__(64, 5) eval_pair_items_kernel(const PairItemsA
             io.resume = 0;
             io.rho = w.rho;
             io.eps = w.eps;
-            search_pair<VAR>(sm, L, lg, a.recs[w.rec], warp, io, tw, a.fail);
+            search_pair<VAR>(sm, L, lg, a.recs[w.rec], warp, io, tw);
         }
         __syncthreads();   // the item is done before shared memory or s_item change
     }
@@ -1080,13 +1088,12 @@ int pair_layout_bytes(int n_atoms, int n_tors, int ppb, int variant) {
 
 cudaError_t launch_eval_pair_items(const WorkItem *items, int n_items, const LigDev *ligs,
                                    const RecDev *recs, int *counter, const EvalCfg &cfg, int budget,
-                                   int grid, cudaStream_t s, int *fail) {
+                                   int grid, cudaStream_t s) {
     PairItemsArgs a;
     a.items = items;
     a.ligs = ligs;
     a.recs = recs;
     a.counter = counter;
-    a.fail = fail;
     a.n_items = n_items;
     a.ppb = cfg.ppb < 1 ? 1 : (cfg.ppb > 4 ? 4 : cfg.ppb);
     int dev = 0;
@@ -1169,6 +1176,9 @@ static cudaError_t launch_ablation_t(const PairArgs &a, int smem, cudaStream_t s
             if (VAR != ADGB_REDUCE_TCGEN05 || a.n % a.ppb != 0 || a.ppb % 2 != 0 || a.iters_pp)
                 return cudaErrorInvalidValue;
             return launch_pair_t<VAR, SK_BLOCKMMA>(a, smem, s);
+        case SK_NOISSUE:
+            if (VAR != ADGB_REDUCE_TCGEN05) return cudaErrorInvalidValue;
+            return launch_pair_t<VAR, SK_NOISSUE>(a, smem, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -1179,7 +1189,7 @@ static cudaError_t launch_pair_any(const RecDev &rec, const LigDev &lig, const E
                                    int mode, const float *genes_in, float *genes_out, int n,
                                    int iters, float rho, float eps, int resume, float *energy,
                                    float *grad, float *state, cudaStream_t s,
-                                   const int *iters_per_pose, int *fail, int skip) {
+                                   const int *iters_per_pose, int skip) {
     if (n == 0) return cudaSuccess;
     if (!pair_eligible(lig.n_atoms, lig.n_tors, lig.n_pairs, lig.n_rounds, lig.r_lanes, cfg.tpp))
         return cudaErrorInvalidValue;
@@ -1196,7 +1206,6 @@ static cudaError_t launch_pair_any(const RecDev &rec, const LigDev &lig, const E
     a.grad = grad;
     a.state = state;
     a.iters_pp = iters_per_pose;
-    a.fail = fail;
     a.n = n;
     a.iters = iters;
     a.resume = resume;
@@ -1227,9 +1236,9 @@ static cudaError_t launch_pair_any(const RecDev &rec, const LigDev &lig, const E
 cudaError_t launch_eval_pair(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg, int mode,
                              const float *genes_in, float *genes_out, int n, int iters, float rho,
                              float eps, int resume, float *energy, float *grad, float *state,
-                             cudaStream_t s, const int *iters_per_pose, int *fail) {
+                             cudaStream_t s, const int *iters_per_pose) {
     return launch_pair_any(rec, lig, cfg, mode, genes_in, genes_out, n, iters, rho, eps, resume,
-                           energy, grad, state, s, iters_per_pose, fail, -1);
+                           energy, grad, state, s, iters_per_pose, -1);
 }
 
 cudaError_t launch_pair_ablation(const RecDev &rec, const LigDev &lig, const EvalCfg &cfg,
@@ -1237,7 +1246,12 @@ cudaError_t launch_pair_ablation(const RecDev &rec, const LigDev &lig, const Eva
                                  int skip) {
     if (skip < 0) return cudaErrorInvalidValue;
     return launch_pair_any(rec, lig, cfg, MODE_LS, genes, genes, n, iters, 0.8f, 1e-2f, 0, energy,
-                           nullptr, nullptr, s, nullptr, nullptr, skip);
+                           nullptr, nullptr, s, nullptr, skip);
+}
+
+cudaError_t pair_tc_gave_up_async(unsigned int *dst, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(dst, g_tc_gave_up, sizeof(unsigned int), 0,
+                                     cudaMemcpyDeviceToHost, s);
 }
 
 }  // namespace adgb

@@ -209,6 +209,11 @@ struct Tc05Warp {
 
 constexpr int TC05_WAIT_LIMIT = 1 << 16;   // mbarrier probes, each suspending up to a time limit
 
+// Tensor-core completion waits that gave up in this translation unit's
+// kernels on the current device (monotonic, one count a warp; the host reads
+// it after a call and reports ADGB_EDEVICE when it grew).
+static __device__ unsigned int g_tc_gave_up;
+
 // The tcgen05 reduction in two halves, so that independent work can run
 // while the MMAs are in flight: tc05_issue stages the warp's partials (TF32
 // hi and lo terms) and has one lane issue the MMAs and commit them to the
@@ -249,6 +254,7 @@ __device__ __forceinline__ void tc05_finish(float v[8], Tc05Warp &t) {
     t.phase++;
     if (!done) {
         t.ok = 0;
+        if ((threadIdx.x & 31) == 0) atomicAdd(&g_tc_gave_up, 1u);
 #pragma unroll
         for (int c = 0; c < 8; c++) v[c] = __int_as_float(0x7fc00000);
         return;

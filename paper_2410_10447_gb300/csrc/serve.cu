@@ -74,12 +74,14 @@ struct Job {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev[IN_FLIGHT] = {}, ev_fin = nullptr;
     Pinned cnt;        // [IN_FLIGHT][runs] evaluation counts, [IN_FLIGHT][runs] stop flags, blob
-    Pinned res;        // results: [runs][G] genes, [runs] FP64 energies, [runs] counts
+    Pinned res;        // results: [runs][G] genes, [runs] FP64 energies, [runs] counts,
+                       // tensor-core give-up counts [2] at the start and [2] at the end
     int launched = 0;  // generations queued (0 = the initial population)
     int processed = 0; // generations whose counters have been read
     int cur = 0;       // population buffer of the last queued generation
     int gen_done = 0;  // generation at which the job is complete
     bool stop_launch = false, finishing = false, failed = false;
+    bool tc_failed = false;   // a tensor-core wait gave up while the job ran (results not valid)
     // published under the server lock
     int gen_pub = 0;
     std::vector<float> best_genes;
@@ -209,6 +211,14 @@ void release_job(adgb_server *s, Job *j) {
     }
 }
 
+// The job's tensor-core give-up snapshots (pinned): [0..1] when its first
+// launch starts, [2..3] after its last.  The counts are device-wide, so a
+// give-up in another job's kernels while this job ran fails this one too.
+unsigned int *tc_counts(const Job *j) {
+    return (unsigned int *)((char *)j->res.p + al256(4 * (size_t)j->d.n_runs * j->G) +
+                            16 * (size_t)j->d.n_runs);
+}
+
 // Device state of a newly admitted job: stream, events, memory, pinned
 // buffers, ligand blob, initial population.
 cudaError_t setup_job(adgb_server *s, Job *j) {
@@ -221,12 +231,13 @@ cudaError_t setup_job(adgb_server *s, Job *j) {
     job_layout(*j, j->mem);
     const int runs = j->d.n_runs;
     j->cnt = pinned_take(s, IN_FLIGHT * (size_t)runs * 12 + j->blob.bytes.size());
-    j->res = pinned_take(s, al256(4 * (size_t)runs * j->G) + 16 * (size_t)runs);
+    j->res = pinned_take(s, al256(4 * (size_t)runs * j->G) + 16 * (size_t)runs + 16);
     if (!j->cnt.p || !j->res.p) return cudaErrorMemoryAllocation;
     // the ligand blob through pinned memory (an asynchronous copy)
     unsigned char *stage = (unsigned char *)j->cnt.p + IN_FLIGHT * (size_t)runs * 12;
     std::copy(j->blob.bytes.begin(), j->blob.bytes.end(), stage);
     e = cudaMemcpyAsync(j->mem, stage, j->blob.bytes.size(), cudaMemcpyHostToDevice, j->stream);
+    if (e == cudaSuccess) e = tc_gave_up_async(tc_counts(j), j->stream);
     if (e == cudaSuccess) e = launch_job_start(j->rec, j->lig.n_tors, j->d, j->w, j->stream);
     return e;
 }
@@ -336,6 +347,7 @@ bool service(adgb_server *s, Job *j, bool *complete) {
             e = cudaMemcpyAsync(h_g, j->d_best_genes, 4 * (size_t)runs * j->G, cudaMemcpyDeviceToHost, j->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_e, j->d_best_e, 8 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_v, j->w.evals, 8 * (size_t)runs, cudaMemcpyDeviceToHost, j->stream);
+        if (e == cudaSuccess) e = tc_gave_up_async(tc_counts(j) + 2, j->stream);
         if (e == cudaSuccess) e = cudaEventRecord(j->ev_fin, j->stream);
         if (e != cudaSuccess) {
             job_error(s, j, e);
@@ -349,6 +361,9 @@ bool service(adgb_server *s, Job *j, bool *complete) {
     if (q == cudaErrorNotReady) return progress;
     if (q != cudaSuccess) {
         job_error(s, j, q);
+    } else if (const unsigned int *tc = tc_counts(j); tc[0] + tc[1] != tc[2] + tc[3]) {
+        j->tc_failed = true;
+        s->err = "serving: a tensor-core completion wait gave up while the job ran";
     } else {
         j->best_genes.assign(h_g, h_g + (size_t)runs * j->G);
         j->best_e.assign(h_e, h_e + runs);
@@ -415,8 +430,9 @@ void server_loop(adgb_server *s) {
         }
         lk.lock();
         for (Job *j : complete) {
-            j->status = j->failed ? (int)ADGB_EDEVICE
-                                  : (j->cancel ? (int)ADGB_ECANCELLED : (int)JOB_DONE);
+            j->status = (j->failed || j->tc_failed)
+                            ? (int)ADGB_EDEVICE
+                            : (j->cancel ? (int)ADGB_ECANCELLED : (int)JOB_DONE);
             if (j->status == JOB_DONE) j->gen_pub = j->gen_done;
             j->t_finish = now_s(s->t0);
             s->used -= j->bytes;

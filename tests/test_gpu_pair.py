@@ -148,3 +148,33 @@ def test_mixed_iteration_counts_in_a_warp(pkg, torch):
     (g0, e0, v0), (g1, e1, v1) = res
     assert np.array_equal(v0, v1)
     assert np.all(np.abs(e0 - e1) <= np.maximum(E_REL * np.abs(e1), E_ABS)), (e0, e1)
+
+
+def test_tcgen05_wait_give_up_is_reported(pkg, torch, cfg1):
+    """The failure path of the tensor-core waits, without a GPU fault: the
+    test form of the tcgen05 kernel issues nothing to the tensor core, so
+    every warp's first completion wait gives up after a short bounded wait.
+    The give-up is reported once (device_status for the asynchronous call,
+    the next synchronous call otherwise), and the context keeps working with
+    the same bits as before."""
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(cfg1["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(cfg1["ligand"])
+    genes = cfg1["genes"][:12]
+    e0, g0 = ctx.score_poses(rid, lid, genes, variant=3)
+    ctx.device_status()                                  # nothing to report
+    g = torch.from_numpy(genes.copy()).cuda()
+    best = torch.empty(genes.shape[0], device="cuda")
+    ctx.ls_ablation_dev(rid, lid, g, best, 5, 3, 1024)
+    with pytest.raises(pkg.adgb.AdgbError) as ei:
+        ctx.device_status()
+    assert ei.value.code == -4
+    ctx.device_status()                                  # reported once
+    ctx.ls_ablation_dev(rid, lid, g, best, 5, 3, 1024)
+    torch.cuda.synchronize()                             # (the call ran on torch's stream)
+    with pytest.raises(pkg.adgb.AdgbError) as ei:        # the next synchronous call reports it
+        ctx.score_poses(rid, lid, genes, variant=3)
+    assert ei.value.code == -4
+    e1, g1 = ctx.score_poses(rid, lid, genes, variant=3)
+    assert np.array_equal(e0, e1) and np.array_equal(g0, g1)
+    ctx.close()
