@@ -703,6 +703,9 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
             settle(wa, fa);
             settle(wb, fb);
         };
+        // unrolled twice: four rounds' chains for the scheduler to interleave
+        // (measured +1.6% shuffle, +2.8% tcgen05 form on the 32-atom ligand)
+#pragma unroll 2
         for (; r + 1 < R; r += 2) two_rounds(r);
         if (r < R) {
             const uint32_t w = __ldg(rw + 32 * r);
