@@ -78,6 +78,7 @@ LAUNCHES_PER_DOCK = 4 + 3 * GENS + 1
 FLOP_GRID, FLOP_PAIR, FLOP_POSE_MOV, FLOP_POSE_ATOM = 110, 40, 20, 30
 FLOP_GGRAD_MOV, FLOP_RED_THREAD, FLOP_GENE = 12, 8, 15
 RSQ_PAIR, EX2_PAIR, SQRT_GENE = 1, 2, 2
+GRID_BYTES_ATOM = 96   # type map 32 B + e map 32 B + d map 32 B of the atom's cell
 SM_COUNT, FP32_LANES, SM_MHZ_MAX = 152, 128, 2070.0
 # special-function results an SM completes a clock, by operation (from the
 # ALU probe on GB300: ex2 10.0 T/s and rsqrt 5.0 T/s at 2070 MHz over 152 SMs)
@@ -119,6 +120,41 @@ def alu_roofline(lig, evals_per_s, probe=None, sm_mhz=SM_MHZ_MAX):
                                                       + ex2 / (probe["ex2_gops"] * 1e9))
         out["measured_probe"] = probe
     return out
+
+
+def l2_probe(ctx, torch, mb=64, waves=8, threads=256):
+    """Measured L2 read bandwidth over the whole GPU (l2_bench_dev) on a
+    buffer of `mb` MB that stays resident in L2: streaming (16-byte coalesced
+    reads) and the scoring kernels' 96-byte cell gathers, GB/s."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    nb = props.multi_processor_count * waves
+    buf = torch.ones(mb * (1 << 20) // 4, device="cuda")
+    out = torch.empty(nb * threads, device="cuda")
+    res = {"buffer_mb": mb}
+    for kind, name, reps, per in ((0, "stream", 2000, 16), (1, "gather96", 400, 96)):
+        ctx.l2_bench_dev(kind, buf, nb, threads, 20, out)
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.l2_bench_dev(kind, buf, nb, threads, reps, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name + "_gbs"] = nb * threads * reps * per / (min(ms) / 1e3) / 1e9
+    return res
+
+
+def grid_roofline(lig, evals_per_s, l2):
+    """The grid gathers' L2 roofline: their algorithmic bytes (96 a ligand
+    atom and evaluation) at the local search's rate, against the measured L2
+    streaming and gather bandwidths."""
+    gbs = evals_per_s * lig["n_atoms"] * GRID_BYTES_ATOM / 1e9
+    return {"bound": "l2", "achieved": gbs, "peak": l2["stream_gbs"], "unit": "GB/s",
+            "frac": gbs / l2["stream_gbs"], "frac_of_gather_probe": gbs / l2["gather96_gbs"],
+            "bytes_per_eval": lig["n_atoms"] * GRID_BYTES_ATOM,
+            "peak_basis": "measured: l2_bench_dev streaming reads of a %d MB L2-resident "
+                          "buffer (gathers of 96 B: %.0f GB/s)" % (l2["buffer_mb"], l2["gather96_gbs"])}
 
 
 def alu_probe(ctx, torch, waves=8, threads=256, reps=2000):
@@ -659,6 +695,7 @@ def main():
         extra["serving"] = serving_phase(pkg, window=args.serve_window)
     # measured FP32 FMA and special-function throughput (after the timed region)
     probe = alu_probe(ctx, torch)
+    l2bw = l2_probe(ctx, torch)
 
     if rank != 0:
         if dist:
@@ -670,6 +707,7 @@ def main():
     roof["traffic"] = profile_traffic(kernel_sha())
     roof["kernel"] = ("eval_pair_kernel (local search, two genotypes a warp, 3000 genotypes x 300 "
                       "evaluations)")
+    roof_grid = grid_roofline(lig, n * ITERS / launch_s, l2bw)
     cpu = None
     if not args.no_cpu_baseline:
         import oracle
@@ -703,6 +741,7 @@ def main():
                 "d2h_bytes_per_step": RUNS * (G * 4 + 8 + 8)},
         "gpu_launches": args.steps * LAUNCHES_PER_DOCK,
         "roofline": roof,
+        "roofline_grid_l2": roof_grid,
         "clocks": clocks,
         "cpu_baseline": cpu,
     }

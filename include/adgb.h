@@ -562,6 +562,24 @@ int alu_bench_dev(adgb_ctx *ctx, int kind, int n_blocks, int threads, int reps, 
                   adgb_stream stream);
 
 /*
+ * l2_bench_dev - read-bandwidth probe of the L2 cache (no counterpart in the
+ * paper; it measures the denominator of the grid gathers' roofline, whose
+ * maps stay resident in L2 for grids up to ~100 MB).  buf_dev [n_float4]
+ * float4 (16-byte aligned; the caller sizes it to stay resident in L2 and
+ * reads it once before timing) is read by n_blocks x threads threads, reps
+ * times each.  kind 0: coalesced streaming reads, 16 bytes a thread and
+ * repetition.  kind 1: the scoring kernels' gathers - per repetition a
+ * pseudo-random cell of cell_float4 float4 (even, >= 6; the grid's cells are
+ * maps x 2 float4) and 96 bytes of it: two float4 of one leading map and the
+ * four trailing float4.  out_dev [n_blocks * threads] float32 receives each
+ * thread's sum of the x components read (with a buffer of ones: 1 a float4
+ * read).  threads: 32..256, a multiple of 32.  Errors: EINVAL, EDEVICE.
+ */
+int l2_bench_dev(adgb_ctx *ctx, int kind, const float *buf_dev, long long n_float4,
+                 int cell_float4, int n_blocks, int threads, int reps, float *out_dev,
+                 adgb_stream stream);
+
+/*
  * device_status - tensor-core failure report (no counterpart in the paper).
  * Every wait of the tcgen05 local-search kernels for the tensor core is
  * bounded; a wait that gives up makes that warp's sums NaN for the rest of

@@ -39,7 +39,7 @@ EXPORTS = ["adgb_create", "adgb_destroy", "adgb_last_error", "upload_receptor_gr
            "dock_noalloc_dev", "batch_create", "batch_autotune", "batch_local_search_dev",
            "batch_release", "serve_start", "serve_stop", "serve_last_error", "serve_stats",
            "dock_submit", "dock_poll", "dock_wait", "dock_result", "dock_cancel", "dock_forget",
-           "philox4x32_10_dev", "ls_ablation_dev", "device_status"]
+           "philox4x32_10_dev", "ls_ablation_dev", "device_status", "l2_bench_dev"]
 MAX_GENES = 46
 
 
@@ -204,6 +204,8 @@ def load(build: bool = False):
     L.alu_bench_dev.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
     L.philox4x32_10_dev.argtypes = [vp, vp, C.c_int, vp, vp]
     L.device_status.argtypes = [vp]
+    L.l2_bench_dev.argtypes = [vp, C.c_int, vp, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_int,
+                               vp, vp]
     L.ls_ablation_dev.argtypes = [vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                   vp, vp]
     _lib = L
@@ -438,6 +440,15 @@ class Context:
         self._chk(self.lib.ga_generation_dev(self.h, lid, C.byref(params), gen, _ptr(genes),
                                              _ptr(energy), _ptr(genes_out), _ptr(iters_out),
                                              _stream()))
+
+    def l2_bench_dev(self, kind, buf, n_blocks, threads, reps, out, cell_float4=20):
+        """L2 read probe over float32 buf (kind 0 streaming, 1 the grid's 96-byte
+        gathers from cells of cell_float4 float4)."""
+        _check_dev(buf, "buf")
+        _check_dev(out, "out")
+        self._chk(self.lib.l2_bench_dev(self.h, int(kind), _ptr(buf), buf.numel() // 4,
+                                        int(cell_float4), int(n_blocks), int(threads), int(reps),
+                                        _ptr(out), _stream()))
 
     def alu_bench_dev(self, kind, n_blocks, threads, reps, out):
         """ALU throughput probe (kind 0 FFMA, 1 ex2.approx, 2 rsqrt.approx, 3 packed FFMA2)."""

@@ -315,6 +315,8 @@ cudaError_t launch_ga_converged(int n_runs, int pop, int top, float tol, const f
 cudaError_t launch_philox(const uint32_t *in, int n, uint32_t *out, cudaStream_t s);
 cudaError_t launch_alu_bench(int kind, int n_blocks, int threads, int reps, float *out,
                              cudaStream_t s);
+cudaError_t launch_l2_bench(int kind, const float *buf, long long n4, int cell4, int n_blocks,
+                            int threads, int reps, float *out, cudaStream_t s);
 cudaError_t launch_coords(const LigDev &lig, const float *genes, int n, float *xyz,
                           cudaStream_t s);
 // Persistent multi-ligand local search over a device table of work items

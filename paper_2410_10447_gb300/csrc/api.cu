@@ -1494,6 +1494,22 @@ int alu_bench_dev(adgb_ctx *c, int kind, int n_blocks, int threads, int reps, fl
     return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "alu_bench");
 }
 
+int l2_bench_dev(adgb_ctx *c, int kind, const float *buf_dev, long long n_float4, int cell_float4,
+                 int n_blocks, int threads, int reps, float *out_dev, adgb_stream stream) {
+    if (!c) return ADGB_EINVAL;
+    if ((kind != 0 && kind != 1) || !buf_dev || !out_dev || n_float4 < 1 || n_blocks < 1 ||
+        threads < 32 || threads > 256 || threads % 32 || reps < 1 ||
+        (reinterpret_cast<uintptr_t>(buf_dev) & 15))
+        return fail(c, ADGB_EINVAL, "l2_bench: bad arguments");
+    if (kind == 1 && (cell_float4 < 6 || cell_float4 % 2 || n_float4 < cell_float4 ||
+                      n_float4 / cell_float4 > 0xffffffffLL))
+        return fail(c, ADGB_EINVAL, "l2_bench: bad cell size");
+    DeviceGuard g(c->device);
+    cudaError_t e = launch_l2_bench(kind, buf_dev, n_float4, cell_float4, n_blocks, threads, reps,
+                                    out_dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? ADGB_OK : cuda_fail(c, e, "l2_bench");
+}
+
 int ls_ablation_dev(adgb_ctx *c, int receptor_id, int ligand_id, float *genes_dev, int n, int iters,
                     int variant, int skip_mask, float *best_energy_dev, adgb_stream stream) {
     if (!c) return ADGB_EINVAL;

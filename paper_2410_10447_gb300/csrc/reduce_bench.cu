@@ -407,6 +407,56 @@ cudaError_t launch_alu_bench(int kind, int n_blocks, int threads, int reps, floa
     return cudaGetLastError();
 }
 
+// L2 read probe.  KIND 0: coalesced streaming reads (thread t reads float4
+// t, t + T, ... modulo n4, T the threads of the launch).  KIND 1: the scoring
+// kernels' gather pattern: per repetition a pseudo-random cell of cell4
+// float4 (an integer hash of thread and repetition) and 96 bytes of it - two
+// float4 of one of its leading maps and the four trailing float4 (the grid's
+// type map and its e and d maps).  Each thread writes the sum of the x
+// components it read.
+template <int KIND>
+__global__ void __launch_bounds__(256) l2_kernel(const float4 *buf, long long n4, int cell4,
+                                                 int reps, float *out) {
+    const long long T = (long long)gridDim.x * blockDim.x;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float acc = 0.f;
+    if constexpr (KIND == 0) {
+        long long i = t % n4;
+        const long long step = T % n4;
+#pragma unroll 8
+        for (int r = 0; r < reps; r++) {
+            acc += __ldg(buf + i).x;
+            i += step;
+            if (i >= n4) i -= n4;
+        }
+    } else {
+        const uint32_t n_cells = (uint32_t)(n4 / cell4);
+        const int m = (int)(t % (cell4 / 2 - 2));
+#pragma unroll 4
+        for (int r = 0; r < reps; r++) {
+            uint32_t h = (uint32_t)t * 0x9E3779B1u ^ (uint32_t)r * 0x85EBCA77u;
+            h ^= h >> 15;
+            h *= 0x2C1B3C6Du;
+            h ^= h >> 12;
+            const float4 *cp = buf + (size_t)__umulhi(h, n_cells) * cell4;
+            acc += __ldg(cp + 2 * m).x + __ldg(cp + 2 * m + 1).x + __ldg(cp + cell4 - 4).x +
+                   __ldg(cp + cell4 - 3).x + __ldg(cp + cell4 - 2).x + __ldg(cp + cell4 - 1).x;
+        }
+    }
+    out[t] = acc;
+}
+
+cudaError_t launch_l2_bench(int kind, const float *buf, long long n4, int cell4, int n_blocks,
+                            int threads, int reps, float *out, cudaStream_t s) {
+    const float4 *b = reinterpret_cast<const float4 *>(buf);
+    switch (kind) {
+        case 0: l2_kernel<0><<<n_blocks, threads, 0, s>>>(b, n4, cell4, reps, out); break;
+        case 1: l2_kernel<1><<<n_blocks, threads, 0, s>>>(b, n4, cell4, reps, out); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_reduce4_bench(int variant, const float *in, int threads, int n_blocks,
                                  int reps, float *out, cudaStream_t s) {
     switch (variant) {

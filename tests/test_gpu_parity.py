@@ -425,6 +425,28 @@ def test_alu_probe(pkg, torch):
     ctx.close()
 
 
+def test_l2_probe(pkg, torch):
+    """The L2 read probe reads what it says: over a buffer of ones every
+    thread's sum is the number of float4 it read (reps streaming, 6 a
+    repetition gathering; the buffer holds 50 cells of 20 float4 and a ragged
+    tail), and it refuses bad shapes and cell sizes."""
+    ctx = make_ctx(pkg)
+    buf = torch.ones(4 * (50 * 20 + 7), device="cuda")
+    out = torch.empty(3 * 64, device="cuda")
+    ctx.l2_bench_dev(0, buf, 3, 64, 5, out)
+    assert torch.equal(out, torch.full_like(out, 5.0))
+    ctx.l2_bench_dev(1, buf, 3, 64, 5, out, cell_float4=20)
+    assert torch.equal(out, torch.full_like(out, 30.0))
+    for bad in ((2, buf, 3, 64, 5, out), (0, buf, 3, 48, 5, out), (0, buf, 0, 64, 5, out),
+                (0, buf, 3, 64, 0, out)):
+        with pytest.raises(pkg.AdgbError):
+            ctx.l2_bench_dev(*bad)
+    for cell in (5, 7, 50 * 20 + 8):
+        with pytest.raises(pkg.AdgbError):
+            ctx.l2_bench_dev(1, buf, 3, 64, 5, out, cell_float4=cell)
+    ctx.close()
+
+
 def test_tcgen05_wait_gives_up_cleanly(pkg, torch):
     """Failure path of the bounded tensor-core completion wait: with nothing
     committed every wait gives up (after a short bounded wait), the outputs
