@@ -280,8 +280,9 @@ def profile_traffic(kernel_sha):
 
 
 def kernel_sha():
+    """Digest of the sources the profiled kernel (eval_pair_kernel) is built from."""
     h = hashlib.sha1()
-    for f in ("eval_pair.cu", "eval.cu", "reduce.cuh", "tcgen05.cuh", "adgb_internal.cuh"):
+    for f in ("eval_pair.cu", "reduce.cuh", "tcgen05.cuh", "adgb_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2410_10447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
