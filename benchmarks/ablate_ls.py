@@ -2,7 +2,7 @@
 most 32 atoms): times ls_ablation_dev launches with one step left out at
 compile time and reports each step's share as the time saved.
 
-    python -m benchmarks.ablate_ls [--workload lga_n32] [--iters 300] [--variants 0,3]
+    python -m benchmarks.ablate_ls [--workload lga_n32] [--iters 300] [--variants 0,3] [--n 0]
 
 The launches are the local-search launch of the workload (its genotypes, one
 launch of `iters` evaluations each), best of `reps` after one warm-up; the
@@ -38,9 +38,12 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--variants", default="0,3")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--n", type=int, default=0,
+                    help="genotypes (0 = the workload's own); few genotypes (1-2 warps an SM) "
+                         "give each step's share of one warp's dependency chain")
     a = ap.parse_args(argv)
     P.load(build=True)
-    w = synth.workload(a.workload)
+    w = synth.workload(a.workload, n_poses=a.n or None)
     g0 = torch.from_numpy(w["genes"]).cuda()
     n = g0.shape[0]
     ctx = P.Context(0)
