@@ -1068,29 +1068,6 @@ cudaError_t pair_items_occupancy(int threads, int smem, int device, int *per_sm)
     return cudaSuccess;
 }
 
-// Carveout hint for a kernel of the shuffle and mma.sync forms: the
-// smallest shared-memory share of the SM's unified L1 / shared memory that
-// still holds as many blocks as the registers allow; the rest stays L1 for
-// the grid gathers and the round tables (measured on the 32-atom ligand's
-// local search: 505 -> 516M evaluations/s, L1 hit rate 69 -> 74%).  The
-// tcgen05 form keeps the default: its blocks need ~42 KB each.
-template <typename K>
-cudaError_t prefer_l1(K k, int smem, int threads) {
-    int dev = 0, per_sm = 0, reserved = 0, regs_sm = 0;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
-    if (e != cudaSuccess || per_sm <= 0) return e;
-    const int regs_block = ((fa.numRegs * 32 + 255) / 256) * 256 * (threads / 32);
-    const int blocks = regs_block > 0 ? max(1, regs_sm / regs_block) : 1;
-    const long need = (long)blocks * (smem + (long)fa.sharedSizeBytes + reserved);
-    const int pct = (int)max(1L, min(100L, (need * 100 + per_sm - 1) / per_sm));
-    return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-}
-
 template <int VAR>
 cudaError_t launch_pair_items_t(const PairItemsArgs &a, int smem, int grid, cudaStream_t s) {
     auto k = eval_pair_items_kernel<VAR>;
