@@ -178,3 +178,28 @@ def test_tcgen05_wait_give_up_is_reported(pkg, torch, cfg1):
     e1, g1 = ctx.score_poses(rid, lid, genes, variant=3)
     assert np.array_equal(e0, e1) and np.array_equal(g0, g1)
     ctx.close()
+
+
+def test_block_mma_design_equals_warp_mma(pkg, torch, cfg1):
+    """The other tensor-core design (one tcgen05 MMA a block over both warps'
+    partials, measurement form 512 of ls_ablation_dev) computes every column
+    of D as one MMA a warp does: the searched genotypes and energies are the
+    same bits; it refuses launches whose last block is not full."""
+    ctx = pkg.Context(0)
+    rid = ctx.upload_receptor_grids(cfg1["receptor"])
+    lid = ctx.upload_ligand_torsion_tree(cfg1["ligand"])
+    genes = cfg1["genes"][:36]                 # 9 blocks of 4 genotypes
+    out = []
+    for mask in (0, 512):
+        g = torch.from_numpy(genes.copy()).cuda()
+        best = torch.empty(genes.shape[0], device="cuda")
+        ctx.ls_ablation_dev(rid, lid, g, best, 25, 3, mask)
+        torch.cuda.synchronize()
+        out.append((g.cpu().numpy(), best.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    g = torch.from_numpy(cfg1["genes"][:37].copy()).cuda()
+    best = torch.empty(37, device="cuda")
+    with pytest.raises(pkg.adgb.AdgbError):
+        ctx.ls_ablation_dev(rid, lid, g, best, 25, 3, 512)
+    ctx.device_status()
+    ctx.close()
