@@ -311,9 +311,13 @@ void build_rounds(HostLigand &h) {
                 const int p = via[x];
                 const int t = tail[p];
                 std::swap(tail[p], head[p]);
+                // p now leaves head: move it between the two out-lists, each
+                // kept in edge order (as rebuild_out leaves them)
+                std::vector<int> &from = outs[t], &to = outs[tail[p]];
+                from.erase(std::lower_bound(from.begin(), from.end(), p));
+                to.insert(std::lower_bound(to.begin(), to.end(), p), p);
                 x = t;
             }
-            rebuild_out();
         }
     }
     // receive slots: slot 2v + k, k = 0, 1; an atom's in-edges split in halves
@@ -563,37 +567,47 @@ int build_ligand(std::string *err, const adgb_ligand_desc *d, HostLigand &h) {
     // parameter loads) conflict when two lanes read different atoms (type
     // pairs) in the same bank group.  A greedy pass appends, from the next 64
     // pairs in line, the one that adds the fewest such collisions.
+    // A candidate's collisions are counted from the pairs already placed in
+    // its quarter-warp (16-byte atom coordinates: bank group = atom & 7) and
+    // half-warp (8-byte atom parameters and type-pair terms: & 15): for each
+    // index, the placed entries in its bank group less those of the same atom
+    // (or type pair), kept as running counts that restart at every quarter /
+    // half-warp boundary.
     for (int p0 = 0; p0 < NP; p0 += PAIR_CHUNK) {
         const int p1 = std::min(NP, p0 + PAIR_CHUNK);
         std::vector<uint32_t> rem(h.pairs.begin() + p0, h.pairs.begin() + p1), out;
         out.reserve(rem.size());
         constexpr int WIN = 64;
+        int qi[8], qj[8], hi[16], hj[16], ht[16];          // placed entries a bank group
+        int qsi[256], qsj[256], hsi[256], hsj[256], hst[256];   // placed entries an atom / type pair
         while (!rem.empty()) {
             const int pos = (int)out.size();
-            const int q0 = pos - pos % 8, hw0 = pos - pos % 16;
+            if (pos % 16 == 0) {
+                std::fill(hi, hi + 16, 0); std::fill(hj, hj + 16, 0); std::fill(ht, ht + 16, 0);
+                std::fill(hsi, hsi + 256, 0); std::fill(hsj, hsj + 256, 0); std::fill(hst, hst + 256, 0);
+            }
+            if (pos % 8 == 0) {
+                std::fill(qi, qi + 8, 0); std::fill(qj, qj + 8, 0);
+                std::fill(qsi, qsi + 256, 0); std::fill(qsj, qsj + 256, 0);
+            }
             int best = 0, best_c = INT32_MAX;
             const int lim = std::min<int>(WIN, (int)rem.size());
             for (int t = 0; t < lim && best_c > 0; t++) {
                 const uint32_t c = rem[t];
                 const int i = c & 255, j = (c >> 8) & 255, tp = (c >> 16) & 255;
-                int cost = 0;
-                for (int r = hw0; r < pos; r++) {
-                    const uint32_t o = out[r];
-                    const int oi = o & 255, oj = (o >> 8) & 255, otp = (o >> 16) & 255;
-                    if (r >= q0) {   // same quarter-warp: 16-byte atom coordinates
-                        cost += 2 * (oi != i && (oi & 7) == (i & 7));
-                        cost += 2 * (oj != j && (oj & 7) == (j & 7));
-                    }
-                    cost += (oi != i && (oi & 15) == (i & 15));    // 8-byte atom parameters
-                    cost += (oj != j && (oj & 15) == (j & 15));
-                    cost += (otp != tp && (otp & 15) == (tp & 15));  // 8-byte type-pair terms
-                }
+                const int cost = 2 * (qi[i & 7] - qsi[i]) + 2 * (qj[j & 7] - qsj[j]) +
+                                 (hi[i & 15] - hsi[i]) + (hj[j & 15] - hsj[j]) +
+                                 (ht[tp & 15] - hst[tp]);
                 if (cost < best_c) {
                     best_c = cost;
                     best = t;
                 }
             }
-            out.push_back(rem[best]);
+            const uint32_t c = rem[best];
+            const int i = c & 255, j = (c >> 8) & 255, tp = (c >> 16) & 255;
+            qi[i & 7]++; qj[j & 7]++; qsi[i]++; qsj[j]++;
+            hi[i & 15]++; hj[j & 15]++; ht[tp & 15]++; hsi[i]++; hsj[j]++; hst[tp]++;
+            out.push_back(c);
             rem.erase(rem.begin() + best);
         }
         std::copy(out.begin(), out.end(), h.pairs.begin() + p0);
