@@ -172,20 +172,19 @@ struct SmemLayout {
 // most 32 atoms): the ligand's constants once, then per warp the two
 // genotypes' coordinates (atom i: [2i] genotype A, [2i+1] genotype B), genes
 // (float2 per gene) and sin / (1 - cos) of every angle (float4: A's pair,
-// B's pair), a staging tile, and the lanes' grid-cell corner copies.  All offsets in
-// bytes from the layout's base, 16-byte aligned.
+// B's pair) and a staging tile.  All offsets in bytes from the layout's base,
+// 16-byte aligned.
 struct PairSmem {
     int ref, type, frag, tparent, tatoms, taxis, tbref;
     int warp0, warp_stride;
-    int w_xyz, w_genes, w_sc, w_stage, w_grid;
+    int w_xyz, w_genes, w_sc, w_stage;
     int total;
 
     static __host__ __device__ inline int al16(int x) { return (x + 15) & ~15; }
 
     // stage: room for the warp's 32 x 12-float staging tile (the mma.sync
-    // reductions and the shuffle form's torsion sums; not the tcgen05 form);
-    // grid: room for the lanes' grid-corner copies (the tcgen05 form)
-    __host__ __device__ inline void make(int N, int T, int warps, bool stage, bool grid) {
+    // reductions and the shuffle form's torsion sums; not the tcgen05 form)
+    __host__ __device__ inline void make(int N, int T, int warps, bool stage) {
         const int Tn = T > 0 ? T : 1;
         int o = 0;
         ref = o;     o = al16(o + 16 * N);
@@ -201,7 +200,6 @@ struct PairSmem {
         w_genes = q; q = al16(q + 8 * MAX_GENES);
         w_sc = q;    q = al16(q + 16 * (ADGB_MAX_TORS + 4));
         w_stage = q; q = al16(q + (stage ? 4 * 32 * 12 : 0));
-        w_grid = q;  q = al16(q + (grid ? 2 * 6 * 32 * 16 : 0));
         warp_stride = q;
         total = warp0 + warps * warp_stride;
     }

@@ -116,55 +116,15 @@ __device__ __forceinline__ void rotate2(V2 &p, float4 k, float4 b, float4 c) {
     p.z = fma2(s, kv.z, fma2(o, kkv.z, p.z));
 }
 
-// Intermolecular term of one atom in one genotype, in two halves so that
-// the gathers' L2 latency is hidden behind the pair rounds.  grid_issue
-// clamps the point onto the grid, finds its cell and starts the copies of
-// the cell's corners of the type map and of the e and d maps (cell-major
-// corner-packed: three 32-byte runs, six 16-byte copies) into the lane's
-// shared-memory slots (slot k of the lane at dst + 512 k); grid_finish, once
-// the copies have landed, interpolates map + q e + |q| d trilinearly, with
-// its gradient, and adds W_OUT times the squared distance outside the grid.
+// Intermolecular term of one atom in one genotype: the point clamped onto
+// the grid, its cell's corners of the type map and of the e and d maps
+// (cell-major corner-packed: three 32-byte runs) loaded, map + q e + |q| d
+// interpolated trilinearly with its gradient, plus W_OUT times the squared
+// distance outside the grid.
 struct GridAt {
     float f0, f1, f2;   // position inside the cell (fractions)
     float o0, o1, o2;   // distance outside the grid per axis (0 inside)
 };
-
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
-__device__ __forceinline__ GridAt grid_issue(const RecDev &R, int t, float x0, float x1, float x2,
-                                             uint32_t dst) {
-    const float xs[3] = {x0, x1, x2};
-    const int n[3] = {R.nx, R.ny, R.nz};
-    float f[3], o[3];
-    int i0[3];
-#pragma unroll
-    for (int d = 0; d < 3; d++) {
-        const float xc = fminf(fmaxf(xs[d], R.lo[d]), R.hi[d]);
-        o[d] = xs[d] - xc;
-        const float u = (xc - R.lo[d]) * R.inv_h;
-        int k = (int)u;   // u >= 0
-        k = k > n[d] - 2 ? n[d] - 2 : k;
-        i0[d] = k;
-        f[d] = u - (float)k;
-    }
-    const size_t cell = ((size_t)i0[2] * (R.ny - 1) + i0[1]) * (R.nx - 1) + i0[0];
-    const float4 *cp = reinterpret_cast<const float4 *>(R.cells + cell * (size_t)R.M * 8);
-    cp_async16(dst, cp + 2 * t);
-    cp_async16(dst + 512, cp + 2 * t + 1);
-    cp_async16(dst + 1024, cp + 2 * (R.M - 2));
-    cp_async16(dst + 1536, cp + 2 * (R.M - 2) + 1);
-    cp_async16(dst + 2048, cp + 2 * (R.M - 1));
-    cp_async16(dst + 2560, cp + 2 * (R.M - 1) + 1);
-    return {f[0], f[1], f[2], o[0], o[1], o[2]};
-}
 
 // Trilinear value and gradient of map + q e + |q| d from the cell's corners
 // (t0/t1 type map, e0/e1 e map, d0/d1 d map; corner c = cx + 2 cy + 4 cz),
@@ -196,15 +156,7 @@ __device__ __forceinline__ float grid_interp(const RecDev &R, float q, const Gri
     return val + ADGB_W_OUT * pen;
 }
 
-// Prefetched form: the corners copied by grid_issue (lane's slots 32 float4
-// apart).
-__device__ __forceinline__ float grid_finish(const RecDev &R, float q, const GridAt &a,
-                                             const float4 *slot, float &g0, float &g1, float &g2) {
-    return grid_interp(R, q, a, slot[0], slot[32], slot[64], slot[96], slot[128], slot[160], g0,
-                       g1, g2);
-}
-
-// Direct form: the same cell and corners, loaded into registers.
+// The atom's cell and corners, loaded into registers.
 __device__ __forceinline__ float grid_direct(const RecDev &R, int t, float q, float x0, float x1,
                                              float x2, float &g0, float &g1, float &g2) {
     const float xs[3] = {x0, x1, x2};
@@ -545,8 +497,6 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
     float2 *genes_s = reinterpret_cast<float2 *>(W + L.w_genes);
     float4 *sc = reinterpret_cast<float4 *>(W + L.w_sc);
     float *stage = reinterpret_cast<float *>(W + L.w_stage);
-    // the lane's grid-corner slots: [genotype][6 copies][32 lanes] x 16 bytes
-    const uint32_t grid_s = tc05::smem_u32(W + L.w_grid) + 16u * (threadIdx.x & 31);
 
     // the lane's gene (j = lane) of both genotypes, and ADADELTA state
     const int j = lane;
@@ -584,7 +534,6 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
     const uint32_t *rw = lig.rword + lane;
     const float4 *rcs = lig.rconst + lane;
     const int iters = max(io.iters[0], io.iters[1]);
-    constexpr bool PREFETCH = VAR == ADGB_REDUCE_TCGEN05;
 
     for (int it = 0; it < iters; it++) {
         // 1. genes and sin / (1 - cos) of every angle (half-angle form: exact
@@ -624,13 +573,9 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
         const float2 m02 = fma2(s, u.y, oxz), m20 = fma2(bc(-1.f), mul2(s, u.y), oxz);
         const float2 m12 = fma2(bc(-1.f), mul2(s, u.x), oyz), m21 = fma2(s, u.x, oyz);
 
-        // 2. the lane's atom in both genotypes and its grid terms: loaded and
-        //    interpolated here, or (tcgen05 form, measured faster there) the
-        //    copies of the two cells' corners start here and are used after
-        //    the pair rounds
+        // 2. the lane's atom in both genotypes and its grid terms
         V2 xo = {bc(0.f), bc(0.f), bc(0.f)}, go = xo;
         float2 e_acc = bc(0.f);
-        GridAt at_a{}, at_b{};
         if (has_atom) {
             V2 p = {bc(r4.x), bc(r4.y), bc(r4.z)};
             if constexpr (!(SKIP & SK_WALK))
@@ -638,11 +583,7 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
             xo.x = add2(add2(p.x, fma2(m02, p.z, fma2(m01, p.y, mul2(m00, p.x)))), tr.x);
             xo.y = add2(add2(p.y, fma2(m12, p.z, fma2(m11, p.y, mul2(m10, p.x)))), tr.y);
             xo.z = add2(add2(p.z, fma2(m22, p.z, fma2(m21, p.y, mul2(m20, p.x)))), tr.z);
-            if constexpr (!(SKIP & SK_GRID) && PREFETCH) {
-                at_a = grid_issue(rec, a_type, xo.x.x, xo.y.x, xo.z.x, grid_s);
-                at_b = grid_issue(rec, a_type, xo.x.y, xo.y.y, xo.z.y, grid_s + 3072);
-                cp_async_commit();
-            } else if constexpr (!(SKIP & SK_GRID)) {
+            if constexpr (!(SKIP & SK_GRID)) {
                 float ga0, ga1, ga2, gb0, gb1, gb2;
                 const float ea = grid_direct(rec, a_type, r4.w, xo.x.x, xo.y.x, xo.z.x, ga0, ga1, ga2);
                 const float eb = grid_direct(rec, a_type, r4.w, xo.x.y, xo.y.y, xo.z.y, gb0, gb1, gb2);
@@ -716,20 +657,6 @@ __device__ __forceinline__ void search_pair(unsigned char *sm, const PairSmem &L
             V2 f;
             e_acc = add2(e_acc, pterm(d, pc, (w >> 24) & 1, f));
             settle(w, f);
-        }
-
-        // grid terms, the copies landed meanwhile (each lane reads only the
-        // slots it filled)
-        if (PREFETCH && has_atom && !(SKIP & SK_GRID)) {
-            cp_async_wait_all();
-            const float4 *slot = reinterpret_cast<const float4 *>(W + L.w_grid) + lane;
-            float ga0, ga1, ga2, gb0, gb1, gb2;
-            const float ea = grid_finish(rec, r4.w, at_a, slot, ga0, ga1, ga2);
-            const float eb = grid_finish(rec, r4.w, at_b, slot + 192, gb0, gb1, gb2);
-            e_acc = add2(e_acc, make_float2(ea, eb));
-            go.x = add2(go.x, make_float2(ga0, gb0));
-            go.y = add2(go.y, make_float2(ga1, gb1));
-            go.z = add2(go.z, make_float2(ga2, gb2));
         }
 
         // 4. partials (E, g, (x - t) x g) of both genotypes
@@ -1001,7 +928,7 @@ __global__ void __launch_bounds__(64, 5) eval_pair_items_kernel(const PairItemsA
         const LigDev &lg = a.ligs[w.lig];
         if (w.lig != cur_lig) {
             if (threadIdx.x == 0)
-                L.make(lg.n_atoms, lg.n_tors, W, VAR != ADGB_REDUCE_TCGEN05, VAR == ADGB_REDUCE_TCGEN05);
+                L.make(lg.n_atoms, lg.n_tors, W, VAR != ADGB_REDUCE_TCGEN05);
             __syncthreads();
             stage_pair_ligand(sm, L, lg);
             if constexpr (VAR == ADGB_REDUCE_TCGEN05) tc2_write_pattern(smem_raw, lg.tatoms, lg.n_tors);
@@ -1085,8 +1012,7 @@ cudaError_t launch_pair_items_t(const PairItemsArgs &a, int smem, int grid, cuda
 int pair_layout_bytes(int n_atoms, int n_tors, int ppb, int variant) {
     PairSmem L;
     ppb = ppb < 1 ? 1 : (ppb > 4 ? 4 : ppb);
-    L.make(n_atoms, n_tors, (ppb + 1) / 2, variant != ADGB_REDUCE_TCGEN05,
-           variant == ADGB_REDUCE_TCGEN05);
+    L.make(n_atoms, n_tors, (ppb + 1) / 2, variant != ADGB_REDUCE_TCGEN05);
     return L.total + PAIR_HDR;
 }
 
@@ -1203,8 +1129,7 @@ static cudaError_t launch_pair_any(const RecDev &rec, const LigDev &lig, const E
     a.lig = lig;
     a.ppb = cfg.ppb < 1 ? 1 : (cfg.ppb > 4 ? 4 : cfg.ppb);
     const int warps = (a.ppb + 1) / 2;
-    a.L.make(lig.n_atoms, lig.n_tors, warps, cfg.variant != ADGB_REDUCE_TCGEN05,
-             cfg.variant == ADGB_REDUCE_TCGEN05);
+    a.L.make(lig.n_atoms, lig.n_tors, warps, cfg.variant != ADGB_REDUCE_TCGEN05);
     a.genes_in = genes_in;
     a.genes_out = genes_out;
     a.energy = energy;
