@@ -257,8 +257,8 @@ struct EvalCfg {
 // rest stays L1 for the grid gathers and the round tables (measured on the
 // 32-atom ligand's local search: 505 -> 516M evaluations/s, L1 hit rate 69
 // -> 74%; on the one-genotype and Solis-Wets kernels 1-2% slower, so they
-// keep the default).  The tcgen05 form keeps the default too: its operand
-// regions take ~42 KB a block.
+// keep the default).  The tcgen05 form keeps the default too (no gain
+// measured: its P and B operands take 30 KB a block).
 template <typename K>
 inline cudaError_t prefer_l1(K k, int smem, int threads) {
     int dev = 0, per_sm = 0, reserved = 0, regs_sm = 0;
